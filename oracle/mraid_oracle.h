@@ -1,0 +1,105 @@
+/* mraid_oracle.h - plain, slow CPU oracle of the eigenvalue RFI flagger.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may call this code; the library's product
+ * path never does. It shares no source with the CUDA path.
+ *
+ * Method (mRAID, arXiv 2512.16278):
+ *   Section 3.2, Eq. 1: per (channel j, sub-integration k) the N_beam x N_beam
+ *     cross-correlation matrix of the beams' total power; read here as the
+ *     Pearson correlation (mean-subtracted, unit diagonal) of the N_s samples.
+ *   Section 3.3, Eq. 2: eigendecomposition C = Q Lambda Q^-1; eigenvalues
+ *     ordered largest first, normalised as lambda_i^2 / sum_j lambda_j^2.
+ *   Section 3.3 (masking paragraph) and Section 4.5: iterative Gaussian fit
+ *     to the dominant normalised eigenvalue over all cells; cells above
+ *     mean + k * sigma (k = 3) are masked; repeat until the mask is stable.
+ *   Section 4.3: user-preserved frequency ranges are never masked.
+ * Everything is FP64 except the Gram sums, which are exact int64.
+ */
+#ifndef MRAID_ORACLE_H
+#define MRAID_ORACLE_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  double mu;          /* mean of the statistic over the last unmasked set */
+  double sigma;       /* population standard deviation of that set */
+  double thresh;      /* mu + k * sigma */
+  int32_t iterations; /* statistic evaluations made */
+  int32_t converged;  /* 1 if the mask stopped changing */
+  int64_t n_flagged;
+  int64_t n_used;     /* cells in the last unmasked, non-preserved set */
+} orc_flag_info;
+
+/* Exact augmented Gram of one cell (Eq. 1 before normalisation). G is the
+ * full (N+1)x(N+1) row-major matrix of X~ X~^T with X~ = [X; 1]:
+ * G[a][b] = sum_t x_a(t) x_b(t), G[a][N] = sum_t x_a(t), G[N][N] = N_s.
+ * data is uint8 [beam][time][chan], beam b at data + b*beam_stride, time
+ * stride n_chan. Returns 0, or -1 on bad arguments. */
+int orc_cell_gram_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
+                     int32_t n_chan, int32_t n_samp_sub, int32_t sub,
+                     int32_t chan, int64_t* G);
+
+/* Same for float32 samples: G is not exact here, so the oracle forms the
+ * mean-subtracted covariance directly in FP64 (cov[a][b], N x N). */
+int orc_cell_cov_f32(const float* data, int32_t n_beam, int64_t beam_stride,
+                     int32_t n_chan, int32_t n_samp_sub, int32_t sub,
+                     int32_t chan, double* cov);
+
+/* Pearson correlation r (N x N) from the augmented Gram:
+ * r_ab = (n S_ab - S_a S_b) / sqrt((n S_aa - S_a^2)(n S_bb - S_b^2)),
+ * numerators exact in int64. A beam of zero variance gets r_aa = 1 and
+ * r_ab = 0. Returns the number of zero-variance beams. */
+int orc_corr_from_gram(const int64_t* G, int32_t n_beam, double* r);
+
+/* Correlation from an FP64 covariance (same zero-variance rule). */
+int orc_corr_from_cov(const double* cov, int32_t n_beam, double* r);
+
+/* Cyclic (row-by-row) two-sided Jacobi in FP64 on a symmetric n x n matrix.
+ * evals: n eigenvalues, largest first. q1: the unit eigenvector of evals[0],
+ * sign chosen so its largest-magnitude element is positive (lowest index on
+ * ties); may be NULL. sweeps: sweeps used; may be NULL. Stops when the
+ * off-diagonal Frobenius norm is <= 1e-14 of the matrix norm, or after 100
+ * sweeps. Returns 0, or -1 on bad arguments / no convergence. */
+int orc_jacobi(const double* a, int32_t n, double* evals, double* q1,
+               int32_t* sweeps);
+
+/* Normalised dominant eigenvalue s = lambda_1^2 / sum_i lambda_i^2. */
+double orc_stat(const double* evals, int32_t n);
+
+/* Whole path for one cell: Gram, correlation, eigenvalues, q1, statistic.
+ * Any output pointer may be NULL. Returns zero-variance beam count or -1. */
+int orc_cell_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
+                int32_t n_chan, int32_t n_samp_sub, int32_t sub, int32_t chan,
+                int64_t* G, double* r, double* evals, double* q1, double* stat);
+
+/* All cells (cell index = sub * n_chan + chan) with n_threads host threads.
+ * evals [cell][N], q1 [cell][N] may be NULL; stat [cell] required.
+ * Returns 0 or -1. */
+int orc_block_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
+                 int32_t n_chan, int32_t n_samp_sub, int32_t n_sub,
+                 int32_t n_threads, double* evals, double* q1, double* stat);
+
+/* Same for a list of cells (sub[i], chan[i]); outputs indexed by i. */
+int orc_cells_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
+                 int32_t n_chan, int32_t n_samp_sub, int64_t n_list,
+                 const int32_t* subs, const int32_t* chans, int32_t n_threads,
+                 int64_t* G, double* evals, double* q1, double* stat);
+
+/* Iterative clipping of the statistic (cells [sub][chan], n_cells a multiple
+ * of n_chan). keep: n_chan bytes, nonzero = preserved channel (never flagged,
+ * not in the statistics); may be NULL. Starting from an empty mask: mean and
+ * population sigma of the statistic over unmasked, unpreserved cells,
+ * threshold mu + k_sigma*sigma, add every unpreserved cell with s > threshold
+ * to the mask; stop when nothing was added or after max_iter evaluations.
+ * flags: n_cells bytes, 1 = RFI. Returns 0 or -1. */
+int orc_flag(const double* stat, int64_t n_cells, int32_t n_chan,
+             const uint8_t* keep, double k_sigma, int32_t max_iter,
+             uint8_t* flags, orc_flag_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
