@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Benchmark of the eigenvalue RFI flagger on a FAST-shaped block.
+
+Workload (default): 19 beams x 4096 channels x 200 sub-integrations x 1024
+samples of 8-bit data (a 10.07 s block at 49.152 us; 819200 cells of 19x19
+correlation matrices), synthetic (seeded generator, noise + beam-common RFI
++ single-beam pulses). One step = mraid_run on the block resident in HBM:
+Gram sums, correlation, Jacobi eigenvalues, q1, statistic and the
+iterative mask. Inputs (15.9 GB) are far larger than L2 (129 MB).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mraid|reference]
+
+Under torchrun every rank processes its own block (different seed); there is
+no data-path collective (weak scaling). Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("CCM+eig cells/s & HBM GB/s %peak (19-beam×4096-ch); "
+          "served p50/p99 block latency")
+UNIT = "cells/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["mraid", "reference"], default="mraid")
+    ap.add_argument("--workload", choices=["fast_block", "small"], default="fast_block")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="budget of the oracle CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name, rank):
+    import synth
+    base = synth.FAST_BLOCK if name == "fast_block" else synth.SMALL
+    cfg = base.replace(seed=base.seed + 7919 * rank)
+    desc = (f"FAST-shaped block: {cfg.n_beam} beams x {cfg.n_chan} channels x {cfg.n_sub} "
+            f"sub-integrations x {cfg.n_samp_sub} samples, uint8 ({cfg.n_cells} cells, "
+            f"{cfg.nbytes / 1e9:.2f} GB)")
+    return cfg, desc
+
+
+def config_dict(cfg, desc, world):
+    return {
+        "workload": desc,
+        "n_beam": cfg.n_beam, "n_chan": cfg.n_chan, "n_sub": cfg.n_sub,
+        "n_samp_sub": cfg.n_samp_sub, "cells_per_gpu": cfg.n_cells,
+        "bytes_per_gpu": cfg.nbytes, "rfi": {"narrowband_channels": cfg.n_narrow,
+                                           "broadband_bursts": cfg.n_burst,
+                                           "single_beam_pulses": cfg.n_spike},
+        "l2": "inputs larger than L2 (no flush needed)",
+        "parallelism": f"dp{world} (one independent block per GPU)",
+    }
+
+
+# ------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [x for x in vis.split(",") if x.strip()]
+        if local_rank < len(ids) and ids[local_rank].strip().isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+# ------------------------------------------------------------- peaks
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def kernel_traffic(name):
+    """dram bytes per launch from a committed ncu summary, if it was taken
+    on the current source of that kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    rec = d.get(name)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec.get("source", ""))
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if h != rec.get("source_sha256_16"):
+        return None
+    return rec.get("bytes_per_launch_full_size")
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def cpu_baseline(cfg, h_ptr, seconds):
+    """The oracle as it stands, on the host's cores, on a random sample of
+    the workload's cells (same bytes the GPU processed)."""
+    import numpy as np
+    import oracle
+    import synth
+    threads = synth.default_threads()
+    rng = np.random.default_rng(12345)
+    shape = (cfg.n_beam, cfg.n_time, cfg.n_chan)
+
+    def run(n):
+        idx = rng.integers(0, cfg.n_cells, size=n)
+        subs = (idx // cfg.n_chan).astype(np.int32)
+        chans = (idx % cfg.n_chan).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.cells(None, cfg.n_samp_sub, subs, chans, n_threads=threads, data_ptr=h_ptr,
+                     shape=shape)
+        return time.perf_counter() - t0
+
+    n = threads * 4
+    t = run(n)
+    n2 = max(threads, int(n * max(seconds - t, 0.5) / max(t, 1e-6)))
+    t2 = run(n2)
+    return {"value": n2 / t2, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n2} random cells of the same block (per-cell Gram, FP64 Jacobi, "
+                      f"statistic; {t2:.1f} s on {threads} threads); the mask pass is "
+                      "excluded (it is O(cells) and negligible)"}
+
+
+# ------------------------------------------------------------- main arms
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return 0
+    import torch
+    cfg, desc = workload(args.workload, 0)
+    import synth
+    h = torch.empty(cfg.nbytes, dtype=torch.uint8)
+    synth.generate(cfg, out_ptr=h.data_ptr())
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(cfg, h.data_ptr(), per_step)
+        if i >= args.warmup:
+            vals.append(r["value"])
+    v = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * cfg.n_cells / v, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8->i64 Gram, f64 Jacobi", "data": "synthetic",
+        "config": config_dict(cfg, desc, 1),
+        "cpu_baseline": {"kind": "oracle", "cores": r["cores"], "sample": r["sample"],
+                         "value": v, "unit": UNIT},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_mraid(args):
+    world, rank, local = dist_setup(args)
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: a CUDA device is required (no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2512_16278_gb300 as m
+    from paper_2512_16278_gb300 import build as mbuild
+    mbuild.build()
+    import synth
+
+    cfg, desc = workload(args.workload, rank)
+    h = torch.empty(cfg.nbytes, dtype=torch.uint8, pin_memory=True)
+    synth.generate(cfg, out_ptr=h.data_ptr())
+    d = h.to("cuda")
+    stream = torch.cuda.Stream()
+    N, cells = cfg.n_beam, cfg.n_cells
+    with torch.cuda.stream(stream):
+        plan = m.Plan(N, cfg.n_chan, cfg.n_samp_sub, cfg.n_sub, stream=stream)
+        evals = torch.empty(cells, N, dtype=torch.float32, device="cuda")
+        q1 = torch.empty(cells, N, dtype=torch.float32, device="cuda")
+        stat = torch.empty(cells, dtype=torch.float32, device="cuda")
+        flags = torch.empty(cells, dtype=torch.uint8, device="cuda")
+    info = m.FlagInfo()
+
+    def step():
+        m.mraid_run(plan.handle, d, evals, q1, stat, flags, info)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    m.mraid_sync(plan.handle)
+    m.mraid_profile_reset(plan.handle)
+    m.mraid_profile_enable(plan.handle, True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(gpu_index(local))
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    m.mraid_sync(plan.handle)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    m.mraid_profile_enable(plan.handle, False)
+    prof = m.mraid_profile_read(plan.handle)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * cells / (ms / 1000.0)
+
+    # roofline of the dominant kernel (per-launch averages from the events
+    # the plan recorded around each launch inside the timed region)
+    kt = {k: (n, tot / n) for k, (n, tot) in prof.items() if n > 0}
+    launches = sum(n for (n, _) in prof.values())
+    dom = max(kt, key=lambda k: kt[k][0] * kt[k][1])
+    peaks = measured_peaks()
+    in_bytes = cfg.n_beam * cfg.n_samp_sub * cells          # samples read once
+    out_bytes = cells * (4 + 1 + 8 * N)                     # stat, flag, evals, q1
+    np_, psum = N * (N + 1) // 2, (N + 1) * (N + 2) // 2
+    alg = {  # algorithmic bytes per launch of each kernel
+        "gram_u8": in_bytes,
+        "corr_from_sums": cells * (8 * psum + 4 * np_),
+        "eig_jacobi": cells * (4 * np_ + 4 + 8 * N),
+        "flag_clip": cells * 5,
+    }
+    dom_ms = kt[dom][1]
+    achieved = alg.get(dom, in_bytes) / (dom_ms / 1000.0) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+            "traffic": kernel_traffic(dom), "peak_source": peaks["source"] + " (burst copy)",
+            "ms_per_launch": dom_ms}
+    path_gbs = (in_bytes + out_bytes) / (ms / 1000.0) / 1e9
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    e2e = None
+    if args.e2e_steps > 0:
+        h_flags = torch.empty(cells, dtype=torch.uint8, pin_memory=True)
+        h_stat = torch.empty(cells, dtype=torch.float32, pin_memory=True)
+        hinfo = m.FlagInfo()
+        m.mraid_run_host(plan.handle, h, h_stat, h_flags, hinfo)
+        m.mraid_sync(plan.handle)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            m.mraid_run_host(plan.handle, h, h_stat, h_flags, hinfo)
+            m.mraid_sync(plan.handle)
+        te = (time.perf_counter() - t0) / args.e2e_steps
+        if dist:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * cells / te, "unit": UNIT, "h2d_bytes_per_step": cfg.nbytes,
+               "d2h_bytes_per_step": cells * 5, "ms_per_step": te * 1000.0,
+               "api": "mraid_run_host (pinned host input, stat + flags copied back)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(cfg, h.data_ptr(), args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8->i32/i64 Gram, f32 Jacobi", "data": "synthetic",
+            "config": config_dict(cfg, desc, world),
+            "hbm": {"path_bytes_per_step": in_bytes + out_bytes, "achieved_gbs": path_gbs,
+                    "frac_of_measured": path_gbs / peaks["hbm_gbs"],
+                    "frac_of_8tbs_nominal": path_gbs / 8000.0},
+            "roofline": roof,
+            "kernels_ms_per_launch": {k: v[1] for k, v in kt.items()},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "mask": {"flagged_fraction": info.n_flagged / cells, "iterations": info.iterations,
+                     "threshold": info.thresh, "n_near": info.n_near},
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mraid(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

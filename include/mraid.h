@@ -1,0 +1,182 @@
+/* mraid.h - C ABI of the GB300 eigenvalue RFI flagger.
+ *
+ * Method: mRAID (arXiv 2512.16278). For every cell (channel j,
+ * sub-integration k) of multi-beam search-mode data:
+ *   1. the N_beam x N_beam cross-correlation matrix of the beams' total
+ *      power (Section 3.2, Eq. 1), read as the Pearson correlation of the
+ *      N_s = T_k / t_s samples: r_ab = cov_ab / sqrt(cov_aa cov_bb);
+ *   2. its eigendecomposition (Section 3.3, Eq. 2), eigenvalues ordered
+ *      largest first, and the normalised dominant eigenvalue
+ *      s = lambda_1^2 / sum_i lambda_i^2 (Section 3.3);
+ *   3. iterative masking: a Gaussian (mean, sigma) fit to s over the cells
+ *      not yet masked, mask s > mean + k sigma, repeat until the mask is
+ *      stable (Section 3.3 masking paragraph; k = 3 in Section 4.5), never
+ *      masking preserved channels (Section 4.3).
+ *
+ * Conventions for every call below:
+ *   - Data layout: samples [beam][time][chan], channel fastest (as recorded),
+ *     beam b starting beam_stride elements after beam b-1. 8-bit unsigned
+ *     (bit_depth 8) or float32 (bit_depth 32) samples.
+ *   - Cell index = sub * n_chan + chan. All per-cell outputs are dense in
+ *     that order.
+ *   - Pointers named d_* are device pointers allocated and owned by the
+ *     caller; h_* are host pointers owned by the caller (pinned memory makes
+ *     host transfers asynchronous and faster, pageable memory also works).
+ *   - All device work is enqueued on the plan's stream and is asynchronous;
+ *     outputs are valid after mraid_sync (or any later work on that stream).
+ *   - Argument errors are reported synchronously and enqueue nothing. Device
+ *     errors and expired bounded waits surface at the next call or at
+ *     mraid_sync. There is no CPU fallback: without a usable CUDA device
+ *     mraid_plan fails with MRAID_ERR_CUDA.
+ */
+#ifndef MRAID_H
+#define MRAID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MRAID_ABI_VERSION 1
+
+typedef enum {
+  MRAID_OK = 0,
+  MRAID_ERR_INVALID_ARG = 1, /* NULL pointer, size out of range, bad layout */
+  MRAID_ERR_UNSUPPORTED = 2, /* valid but not built: bit depth, N_beam > 128 */
+  MRAID_ERR_OOM = 3,         /* device or pinned host allocation failed */
+  MRAID_ERR_CUDA = 4,        /* a CUDA call failed (message: mraid_last_error) */
+  MRAID_ERR_TIMEOUT = 5,     /* a bounded device wait expired */
+  MRAID_ERR_NOT_READY = 6    /* mraid_query: work still in flight */
+} mraid_status;
+
+/* Problem statement (Section 3.2 and Section 4.5). */
+typedef struct {
+  int32_t n_beam;        /* N_beam, 2..128 (Eq. 1) */
+  int32_t n_chan;        /* frequency channels, >= 1 */
+  int32_t n_samp_sub;    /* N_s = T_k / t_s, samples per sub-integration, 2..2^20 */
+  int32_t n_sub;         /* sub-integrations in one block, >= 1 */
+  int32_t bit_depth;     /* 8: uint8 samples; 32: float32 samples */
+  int64_t beam_stride;   /* elements between beams; 0 = dense (n_sub*n_samp_sub*n_chan) */
+  double eig_k;          /* eigenvalue threshold multiple k (Section 4.5), > 0; 3 */
+  double vec_t;          /* eigenvector threshold multiple (Section 4.5), >= 0; 1 */
+  int32_t max_clip_iter; /* bound on masking iterations, 1..1000; 64 */
+  int32_t reserved;      /* must be 0 */
+  const uint8_t* keep;   /* host, n_chan bytes, nonzero = preserved channel
+                            (Section 4.3); NULL = none. Copied by mraid_plan. */
+} mraid_params;
+
+/* Result of the masking step (Section 3.3). */
+typedef struct {
+  double mu;             /* mean of s over the final unmasked, unpreserved cells */
+  double sigma;          /* population standard deviation of that set */
+  double thresh;         /* mu + k * sigma: the converged dynamic threshold */
+  int32_t iterations;    /* Gaussian fits made */
+  int32_t converged;     /* 1 if the mask stopped changing within max_clip_iter */
+  int64_t n_flagged;     /* cells masked */
+  int64_t n_used;        /* cells in the final fit */
+  int64_t n_near;        /* unpreserved cells with |s - thresh| <= 2e-4 * s */
+  int64_t n_degenerate;  /* (beam, cell) pairs with zero variance (mraid_run) */
+  int32_t timed_out;     /* 1 if a bounded device wait expired */
+  int32_t reserved;
+} mraid_flag_info;
+
+typedef struct mraid_plan_s* mraid_plan_t;
+
+/* Fill p with the paper's defaults (eig_k 3, vec_t 1, max_clip_iter 64,
+ * bit_depth 8, dense layout) for the given sizes. Host only. */
+void mraid_default_params(mraid_params* p, int32_t n_beam, int32_t n_chan,
+                          int32_t n_samp_sub, int32_t n_sub);
+
+/* Check p without touching the GPU. MRAID_OK, MRAID_ERR_INVALID_ARG or
+ * MRAID_ERR_UNSUPPORTED. */
+mraid_status mraid_validate(const mraid_params* p);
+
+/* Validate p, bind the plan to the current CUDA device and to stream
+ * (a cudaStream_t; NULL = the legacy default stream), allocate the plan's
+ * small device state and copy keep[]. Large work buffers are allocated on
+ * first use and kept until mraid_destroy. *out receives the plan. */
+mraid_status mraid_plan(const mraid_params* p, void* stream, mraid_plan_t* out);
+
+/* Section 3.2, Eq. 1: per cell, the exact augmented Gram sums and/or the
+ * Pearson correlation.
+ *   d_data: samples, layout above (bit_depth 8 only for d_sums).
+ *   d_sums: int64 [cell][P], P = (N+1)(N+2)/2, the upper triangle (a <= b,
+ *           row-major) of G = X~ X~^T with X~ = [X; 1]: G[a][b] = sum x_a x_b,
+ *           G[a][N] = sum x_a, G[N][N] = N_s. Exact. May be NULL.
+ *   d_corr: float32 [cell][N(N+1)/2], upper triangle (a <= b, row-major) of r,
+ *           r_aa = 1; a zero-variance beam has r_ab = 0 (a != b). May be NULL.
+ * At least one of d_sums, d_corr must be non-NULL. */
+mraid_status mraid_ccm(mraid_plan_t plan, const void* d_data, int64_t* d_sums,
+                       float* d_corr);
+
+/* Section 3.3, Eq. 2: eigenvalues of every cell's correlation (parallel
+ * cyclic Jacobi in FP32), its dominant eigenvector and statistic.
+ *   d_corr:  float32 [cell][N(N+1)/2] as written by mraid_ccm.
+ *   d_evals: float32 [cell][N], largest first. May be NULL.
+ *   d_q1:    float32 [cell][N], unit eigenvector of evals[0] with its
+ *            largest-magnitude element positive. May be NULL.
+ *   d_stat:  float32 [cell], s = lambda_1^2 / sum lambda_i^2. Required. */
+mraid_status mraid_eig(mraid_plan_t plan, const float* d_corr, float* d_evals,
+                       float* d_q1, float* d_stat);
+
+/* Section 3.3 masking: iterative Gaussian-fit threshold on d_stat.
+ *   d_stat:  float32 [cell].
+ *   d_flags: uint8 [cell], 1 = RFI. Required.
+ *   info:    host struct, filled by the next mraid_sync; may be NULL. */
+mraid_status mraid_flag(mraid_plan_t plan, const float* d_stat, uint8_t* d_flags,
+                        mraid_flag_info* info);
+
+/* The whole path (Eq. 1, Eq. 2, masking) on one block already in device
+ * memory. d_evals and d_q1 may be NULL; d_stat and d_flags are required;
+ * info as in mraid_flag. */
+mraid_status mraid_run(mraid_plan_t plan, const void* d_data, float* d_evals,
+                       float* d_q1, float* d_stat, uint8_t* d_flags,
+                       mraid_flag_info* info);
+
+/* The whole path on one block in HOST memory: copies h_data to the device in
+ * pieces overlapped with the computation, then copies the statistic and the
+ * flags back. h_stat (float32 [cell]) may be NULL; h_flags (uint8 [cell]) is
+ * required. Outputs are valid after mraid_sync. */
+mraid_status mraid_run_host(mraid_plan_t plan, const void* h_data, float* h_stat,
+                            uint8_t* h_flags, mraid_flag_info* info);
+
+/* Wait for the plan's stream, then deliver pending mraid_flag_info. Returns
+ * the first device error seen (MRAID_ERR_TIMEOUT, MRAID_ERR_CUDA) or OK. */
+mraid_status mraid_sync(mraid_plan_t plan);
+
+/* Non-blocking: MRAID_OK if the plan's stream is idle (info delivered),
+ * MRAID_ERR_NOT_READY if work is in flight, or an error. */
+mraid_status mraid_query(mraid_plan_t plan);
+
+/* Free everything the plan owns (waits for its stream first). NULL is a
+ * no-op. */
+void mraid_destroy(mraid_plan_t plan);
+
+/* Per-kernel timing. While enabled, the plan brackets every kernel it
+ * launches with a pair of CUDA events on its stream; mraid_sync folds the
+ * elapsed times into per-kernel totals. mraid_profile_read copies up to max
+ * records (name, launches, total milliseconds) into out and sets *n to the
+ * number of kernels seen; mraid_profile_reset clears the totals. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+} mraid_kernel_time;
+
+mraid_status mraid_profile_enable(mraid_plan_t plan, int32_t enable);
+mraid_status mraid_profile_read(mraid_plan_t plan, mraid_kernel_time* out, int32_t max,
+                                int32_t* n);
+mraid_status mraid_profile_reset(mraid_plan_t plan);
+
+/* Static strings. mraid_last_error describes the last failure in this
+ * thread (empty if none). */
+const char* mraid_status_string(mraid_status s);
+const char* mraid_last_error(void);
+int32_t mraid_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRAID_H */

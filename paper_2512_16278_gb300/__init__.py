@@ -1,0 +1,317 @@
+"""Python binding of libmraid (include/mraid.h): argument marshalling only.
+
+Every step of the eigenvalue RFI flagger (mRAID, arXiv 2512.16278: Eq. 1
+cross-correlation matrices, Eq. 2 eigendecomposition, Section 3.3 iterative
+masking) runs in the CUDA kernels of libmraid.so. PyTorch supplies device
+memory and streams. There is no CPU fallback: if the library or a CUDA
+device is missing, the calls raise.
+
+The functions mraid_* mirror the C ABI one to one and take raw pointers
+(int) or torch tensors; `Plan` is a small convenience wrapper that
+allocates the outputs as torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+__all__ = [
+    "MraidError", "Params", "FlagInfo", "Plan", "load", "library_path",
+    "mraid_default_params", "mraid_validate", "mraid_plan", "mraid_ccm", "mraid_eig",
+    "mraid_flag", "mraid_run", "mraid_run_host", "mraid_sync", "mraid_query",
+    "mraid_destroy", "mraid_status_string", "mraid_last_error", "mraid_abi_version",
+    "mraid_profile_enable", "mraid_profile_read", "mraid_profile_reset", "STATUS",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+STATUS = {0: "MRAID_OK", 1: "MRAID_ERR_INVALID_ARG", 2: "MRAID_ERR_UNSUPPORTED",
+          3: "MRAID_ERR_OOM", 4: "MRAID_ERR_CUDA", 5: "MRAID_ERR_TIMEOUT",
+          6: "MRAID_ERR_NOT_READY"}
+
+
+class MraidError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({detail})")
+
+
+class Params(ctypes.Structure):
+    """mraid_params (Section 3.2 problem statement, Section 4.5 thresholds)."""
+    _fields_ = [
+        ("n_beam", ctypes.c_int32), ("n_chan", ctypes.c_int32),
+        ("n_samp_sub", ctypes.c_int32), ("n_sub", ctypes.c_int32),
+        ("bit_depth", ctypes.c_int32), ("beam_stride", ctypes.c_int64),
+        ("eig_k", ctypes.c_double), ("vec_t", ctypes.c_double),
+        ("max_clip_iter", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("keep", ctypes.c_void_p),
+    ]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double)]
+
+
+class FlagInfo(ctypes.Structure):
+    """mraid_flag_info: result of the Section 3.3 masking."""
+    _fields_ = [
+        ("mu", ctypes.c_double), ("sigma", ctypes.c_double), ("thresh", ctypes.c_double),
+        ("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+        ("n_flagged", ctypes.c_int64), ("n_used", ctypes.c_int64),
+        ("n_near", ctypes.c_int64), ("n_degenerate", ctypes.c_int64),
+        ("timed_out", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "libmraid.so")
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def load():
+    """Load libmraid.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{path} is missing: build it with `python -m paper_2512_16278_gb300.build` "
+            "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    i32, vp = ctypes.c_int32, ctypes.c_void_p
+    sig = {
+        "mraid_default_params": (None, [ctypes.POINTER(Params), i32, i32, i32, i32]),
+        "mraid_validate": (ctypes.c_int, [ctypes.POINTER(Params)]),
+        "mraid_plan": (ctypes.c_int, [ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]),
+        "mraid_ccm": (ctypes.c_int, [vp, vp, vp, vp]),
+        "mraid_eig": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "mraid_flag": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(FlagInfo)]),
+        "mraid_run": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, ctypes.POINTER(FlagInfo)]),
+        "mraid_run_host": (ctypes.c_int, [vp, vp, vp, vp, ctypes.POINTER(FlagInfo)]),
+        "mraid_sync": (ctypes.c_int, [vp]),
+        "mraid_query": (ctypes.c_int, [vp]),
+        "mraid_destroy": (None, [vp]),
+        "mraid_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "mraid_last_error": (ctypes.c_char_p, []),
+        "mraid_abi_version": (ctypes.c_int32, []),
+        "mraid_profile_enable": (ctypes.c_int, [vp, i32]),
+        "mraid_profile_read": (ctypes.c_int, [vp, ctypes.POINTER(KernelTime), i32,
+                                              ctypes.POINTER(i32)]),
+        "mraid_profile_reset": (ctypes.c_int, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(x) -> Optional[int]:
+    """Device/host address of a torch tensor, an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise MraidError(status, where, mraid_last_error())
+
+
+# ---------------------------------------------------------------- raw ABI
+
+def mraid_default_params(n_beam: int, n_chan: int, n_samp_sub: int, n_sub: int) -> Params:
+    p = Params()
+    load().mraid_default_params(ctypes.byref(p), n_beam, n_chan, n_samp_sub, n_sub)
+    return p
+
+
+def mraid_validate(p: Params) -> int:
+    return load().mraid_validate(ctypes.byref(p))
+
+
+def mraid_plan(p: Params, stream: int = 0) -> int:
+    out = ctypes.c_void_p()
+    _check(load().mraid_plan(ctypes.byref(p), stream or None, ctypes.byref(out)), "mraid_plan")
+    return out.value
+
+
+def mraid_ccm(plan: int, d_data, d_sums=None, d_corr=None):
+    _check(load().mraid_ccm(plan, _ptr(d_data), _ptr(d_sums), _ptr(d_corr)), "mraid_ccm")
+
+
+def mraid_eig(plan: int, d_corr, d_evals=None, d_q1=None, d_stat=None):
+    _check(load().mraid_eig(plan, _ptr(d_corr), _ptr(d_evals), _ptr(d_q1), _ptr(d_stat)),
+           "mraid_eig")
+
+
+def mraid_flag(plan: int, d_stat, d_flags, info: Optional[FlagInfo] = None):
+    _check(load().mraid_flag(plan, _ptr(d_stat), _ptr(d_flags),
+                             ctypes.byref(info) if info is not None else None), "mraid_flag")
+
+
+def mraid_run(plan: int, d_data, d_evals, d_q1, d_stat, d_flags,
+              info: Optional[FlagInfo] = None):
+    _check(load().mraid_run(plan, _ptr(d_data), _ptr(d_evals), _ptr(d_q1), _ptr(d_stat),
+                            _ptr(d_flags), ctypes.byref(info) if info is not None else None),
+           "mraid_run")
+
+
+def mraid_run_host(plan: int, h_data, h_stat, h_flags, info: Optional[FlagInfo] = None):
+    _check(load().mraid_run_host(plan, _ptr(h_data), _ptr(h_stat), _ptr(h_flags),
+                                 ctypes.byref(info) if info is not None else None),
+           "mraid_run_host")
+
+
+def mraid_sync(plan: int):
+    _check(load().mraid_sync(plan), "mraid_sync")
+
+
+def mraid_query(plan: int) -> int:
+    return load().mraid_query(plan)
+
+
+def mraid_destroy(plan: int):
+    load().mraid_destroy(plan)
+
+
+def mraid_status_string(s: int) -> str:
+    return load().mraid_status_string(s).decode()
+
+
+def mraid_last_error() -> str:
+    return load().mraid_last_error().decode()
+
+
+def mraid_abi_version() -> int:
+    return load().mraid_abi_version()
+
+
+def mraid_profile_enable(plan: int, enable: bool = True):
+    _check(load().mraid_profile_enable(plan, 1 if enable else 0), "mraid_profile_enable")
+
+
+def mraid_profile_read(plan: int) -> dict:
+    """{kernel name: (launches, total ms)} folded at the last mraid_sync."""
+    arr = (KernelTime * 16)()
+    n = ctypes.c_int32(0)
+    _check(load().mraid_profile_read(plan, arr, 16, ctypes.byref(n)), "mraid_profile_read")
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
+            for i in range(min(n.value, 16))}
+
+
+def mraid_profile_reset(plan: int):
+    _check(load().mraid_profile_reset(plan), "mraid_profile_reset")
+
+
+# ------------------------------------------------------------ convenience
+
+class Plan:
+    """A plan bound to the current CUDA device and a torch stream; outputs
+    are torch tensors on that device."""
+
+    def __init__(self, n_beam: int, n_chan: int, n_samp_sub: int, n_sub: int, *,
+                 eig_k: float = 3.0, vec_t: float = 1.0, max_clip_iter: int = 64,
+                 keep=None, beam_stride: int = 0, stream=None):
+        import numpy as np
+        import torch
+        self.torch = torch
+        self.p = mraid_default_params(n_beam, n_chan, n_samp_sub, n_sub)
+        self.p.eig_k = eig_k
+        self.p.vec_t = vec_t
+        self.p.max_clip_iter = max_clip_iter
+        self.p.beam_stride = beam_stride
+        self._keep = None
+        if keep is not None:
+            self._keep = np.ascontiguousarray(np.asarray(keep, dtype=np.uint8))
+            if self._keep.shape != (n_chan,):
+                raise ValueError("keep must have n_chan entries")
+            self.p.keep = self._keep.ctypes.data
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.handle = mraid_plan(self.p, self.stream.cuda_stream)
+        self.n_beam, self.n_chan, self.n_sub = n_beam, n_chan, n_sub
+        self.n_cells = n_chan * n_sub
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mraid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _empty(self, *shape, dtype):
+        return self.torch.empty(*shape, dtype=dtype, device=self.device)
+
+    def ccm(self, data, sums: bool = True, corr: bool = True):
+        N = self.n_beam
+        s = self._empty(self.n_cells, (N + 1) * (N + 2) // 2, dtype=self.torch.int64) if sums else None
+        c = self._empty(self.n_cells, N * (N + 1) // 2, dtype=self.torch.float32) if corr else None
+        mraid_ccm(self.handle, data, s, c)
+        return s, c
+
+    def eig(self, corr, evals: bool = True, q1: bool = True):
+        N = self.n_beam
+        e = self._empty(self.n_cells, N, dtype=self.torch.float32) if evals else None
+        q = self._empty(self.n_cells, N, dtype=self.torch.float32) if q1 else None
+        st = self._empty(self.n_cells, dtype=self.torch.float32)
+        mraid_eig(self.handle, corr, e, q, st)
+        return e, q, st
+
+    def flag(self, stat):
+        f = self._empty(self.n_cells, dtype=self.torch.uint8)
+        info = FlagInfo()
+        mraid_flag(self.handle, stat, f, info)
+        mraid_sync(self.handle)
+        return f, info.as_dict()
+
+    def run(self, data, evals: bool = True, q1: bool = True, sync: bool = True):
+        N = self.n_beam
+        out = {
+            "evals": self._empty(self.n_cells, N, dtype=self.torch.float32) if evals else None,
+            "q1": self._empty(self.n_cells, N, dtype=self.torch.float32) if q1 else None,
+            "stat": self._empty(self.n_cells, dtype=self.torch.float32),
+            "flags": self._empty(self.n_cells, dtype=self.torch.uint8),
+        }
+        info = FlagInfo()
+        mraid_run(self.handle, data, out["evals"], out["q1"], out["stat"], out["flags"], info)
+        out["_info"] = info
+        if sync:
+            mraid_sync(self.handle)
+            out["info"] = info.as_dict()
+        return out
+
+    def run_host(self, h_data, h_stat=None, h_flags=None):
+        """Whole path from a host block (pinned torch tensor or address)."""
+        torch = self.torch
+        if h_flags is None:
+            h_flags = torch.empty(self.n_cells, dtype=torch.uint8, pin_memory=True)
+        info = FlagInfo()
+        mraid_run_host(self.handle, h_data, h_stat, h_flags, info)
+        mraid_sync(self.handle)
+        return h_flags, info.as_dict()
+
+    def sync(self):
+        mraid_sync(self.handle)

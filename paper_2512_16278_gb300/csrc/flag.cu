@@ -1,0 +1,184 @@
+// flag.cu - iterative Gaussian-fit masking of the normalised dominant
+// eigenvalue (Section 3.3 masking paragraph; threshold multiple k from
+// Section 4.5; preserved channels from Section 4.3).
+//
+// One cooperative launch runs the whole iteration on the device: every pass
+// masks the cells above the previous threshold, reduces (count, sum s,
+// sum s^2) over the cells still unmasked and unpreserved in FP64, and
+// derives mu, sigma (population) and mu + k sigma. The fit stops when a
+// pass masks nothing new (the unmasked count is unchanged) or after
+// max_clip_iter fits. Block partial sums are combined in a fixed order by
+// every block, so the result is deterministic.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace mraid {
+namespace {
+
+constexpr int kFlagThreads = 256;
+
+struct FlagArgs {
+  const float* stat;
+  int64_t n_cells;
+  int n_chan;
+  const uint8_t* keep;  // device [n_chan] or nullptr
+  double k_sigma;
+  int max_iter;
+  uint8_t* flags;
+  double* partials;     // [2][gridDim.x][3]
+  mraid_flag_info* info;
+};
+
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  const int w = threadIdx.x / 32, nw = blockDim.x / 32;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    red[3 * w] = a;
+    red[3 * w + 1] = b;
+    red[3 * w + 2] = c;
+  }
+  __syncthreads();
+  a = b = c = 0.0;
+  for (int i = 0; i < nw; ++i) {  // fixed order
+    a += red[3 * i];
+    b += red[3 * i + 1];
+    c += red[3 * i + 2];
+  }
+}
+
+__global__ void __launch_bounds__(kFlagThreads) flag_kernel(FlagArgs f) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double red[3 * (kFlagThreads / 32)];
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = tid; i < f.n_cells; i += nthr) f.flags[i] = 0;
+
+  double thresh = INFINITY, mu = 0.0, sigma = 0.0;
+  double prev_count = -1.0, used = 0.0;
+  int fits = 0, converged = 0;
+  for (int pass = 0;; ++pass) {
+    double cnt = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int64_t i = tid; i < f.n_cells; i += nthr) {
+      if (f.keep && f.keep[i % f.n_chan]) continue;
+      const double v = (double)f.stat[i];
+      uint8_t m = f.flags[i];
+      if (!m && v > thresh) {
+        m = 1;
+        f.flags[i] = 1;
+      }
+      if (!m) {
+        cnt += 1.0;
+        s1 += v;
+        s2 = fma(v, v, s2);
+      }
+    }
+    block_sum3(cnt, s1, s2, red);
+    double* part = f.partials + (size_t)(pass & 1) * gridDim.x * 3;
+    if (threadIdx.x == 0) {
+      part[3 * blockIdx.x] = cnt;
+      part[3 * blockIdx.x + 1] = s1;
+      part[3 * blockIdx.x + 2] = s2;
+    }
+    grid.sync();
+    cnt = s1 = s2 = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) {  // same order in every block
+      cnt += part[3 * b];
+      s1 += part[3 * b + 1];
+      s2 += part[3 * b + 2];
+    }
+    if (pass >= 1 && cnt == prev_count) {  // the last threshold masked nothing
+      converged = 1;
+      break;
+    }
+    if (fits == f.max_iter) break;  // mask already holds max_iter markings
+    if (cnt == 0.0) {               // nothing left to fit
+      mu = sigma = 0.0;
+      thresh = INFINITY;
+      used = 0.0;
+      ++fits;
+      converged = 1;
+      break;
+    }
+    mu = s1 / cnt;
+    sigma = sqrt(fmax(s2 / cnt - mu * mu, 0.0));
+    thresh = mu + f.k_sigma * sigma;
+    used = cnt;
+    prev_count = cnt;
+    ++fits;
+  }
+  // totals for the report
+  double nflag = 0.0, nnear = 0.0, dummy = 0.0;
+  for (int64_t i = tid; i < f.n_cells; i += nthr) {
+    nflag += f.flags[i];
+    if (f.keep && f.keep[i % f.n_chan]) continue;
+    const double v = (double)f.stat[i];
+    if (fabs(v - thresh) <= 2e-4 * v) nnear += 1.0;
+  }
+  block_sum3(nflag, nnear, dummy, red);
+  grid.sync();  // everyone has read this pass's partials before they are reused
+  double* part = f.partials;
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = nflag;
+    part[3 * blockIdx.x + 1] = nnear;
+  }
+  grid.sync();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double tf = 0.0, tn = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) {
+      tf += part[3 * b];
+      tn += part[3 * b + 1];
+    }
+    mraid_flag_info* o = f.info;
+    o->mu = mu;
+    o->sigma = sigma;
+    o->thresh = thresh;
+    o->iterations = fits;
+    o->converged = converged;
+    o->n_flagged = (int64_t)tf;
+    o->n_used = (int64_t)used;
+    o->n_near = (int64_t)tn;
+    o->timed_out = 0;
+  }
+}
+
+}  // namespace
+
+int flag_grid_blocks(int device, int sm_count) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, flag_kernel, kFlagThreads, 0) !=
+          cudaSuccess ||
+      per_sm < 1)
+    return 0;
+  (void)device;
+  return sm_count * (per_sm < 2 ? per_sm : 2);
+}
+
+cudaError_t launch_flag(mraid_plan_s* pl, const float* d_stat, uint8_t* d_flags) {
+  FlagArgs f;
+  f.stat = d_stat;
+  f.n_cells = pl->n_cells;
+  f.n_chan = pl->p.n_chan;
+  f.keep = pl->d_keep;
+  f.k_sigma = pl->p.eig_k;
+  f.max_iter = pl->p.max_clip_iter;
+  f.flags = d_flags;
+  f.partials = pl->d_partials;
+  f.info = pl->d_info;
+  void* args[] = {&f};
+  return cudaLaunchCooperativeKernel((const void*)flag_kernel, dim3(pl->flag_blocks),
+                                    dim3(kFlagThreads), args, 0, pl->stream);
+}
+
+}  // namespace mraid

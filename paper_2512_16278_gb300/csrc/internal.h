@@ -1,0 +1,100 @@
+// internal.h - plan state and kernel launchers shared by the library's
+// translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "mraid.h"
+
+namespace mraid {
+
+constexpr int kMaxBeam = 128;
+constexpr int kMaxSampSub = 1 << 20;
+constexpr int kMaxClipIter = 1000;
+// Samples per int32 accumulation segment: 32768 * 255^2 < 2^32 (unsigned).
+constexpr int kGramSegment = 32768;
+
+struct FlagDev {  // device image of mraid_flag_info
+  mraid_flag_info info;
+};
+
+enum KernelId { K_GRAM = 0, K_CORR, K_EIG, K_FLAG, K_COUNT };
+const char* kernel_name(int id);
+
+struct Profiler {
+  bool on = false;
+  struct Rec {
+    int id;
+    cudaEvent_t start, stop;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  int64_t launches[K_COUNT] = {};
+  double total_ms[K_COUNT] = {};
+};
+
+struct Workspace {
+  int64_t* sums = nullptr;  // [cell][P] (staged Gram for mraid_run)
+  float* corr = nullptr;    // [cell][NP]
+  size_t cells = 0;
+};
+
+}  // namespace mraid
+
+struct mraid_plan_s {
+  mraid_params p{};
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  int64_t n_cells = 0;
+  int64_t beam_stride = 0;
+  int np = 0;    // N(N+1)/2
+  int psum = 0;  // (N+1)(N+2)/2
+  uint8_t* d_keep = nullptr;          // [n_chan]
+  double* d_partials = nullptr;       // flag partial sums [2][blocks][3]
+  int flag_blocks = 0;
+  mraid_flag_info* d_info = nullptr;  // device flag info
+  unsigned long long* d_degenerate = nullptr;
+  unsigned* d_error = nullptr;        // device error word (bounded waits)
+  mraid_flag_info* h_info = nullptr;  // pinned staging
+  mraid_flag_info* pending_info = nullptr;  // user pointer to fill at sync
+  mraid::Workspace ws;
+  // host-buffer path (mraid_run_host)
+  uint8_t* d_chunk[2] = {nullptr, nullptr};
+  size_t chunk_bytes = 0;
+  int chunk_subs = 0;
+  float* d_stat_full = nullptr;
+  uint8_t* d_flags_full = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+  cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
+  mraid::Profiler prof;
+};
+
+namespace mraid {
+
+void set_error(const char* fmt, ...);
+// Bracket a kernel launch with profiling events (no-ops unless enabled).
+void prof_begin(mraid_plan_s* pl, int id, cudaEvent_t* start);
+void prof_end(mraid_plan_s* pl, int id, cudaEvent_t start);
+mraid_status cuda_fail(cudaError_t e, const char* what);
+
+// gram.cu
+// sums of sub-integrations [sub0, sub0 + n_sub) of d_data; d_sums is indexed
+// by cell relative to sub0 (cell = (sub - sub0) * n_chan + chan).
+cudaError_t launch_gram_u8(const mraid_plan_s* pl, const uint8_t* d_data,
+                           int sub0, int n_sub, int64_t* d_sums);
+cudaError_t launch_corr_from_sums(const mraid_plan_s* pl, const int64_t* d_sums,
+                                  int64_t n_cells, float* d_corr);
+// eig.cu
+cudaError_t launch_eig(const mraid_plan_s* pl, const float* d_corr, int64_t n_cells,
+                       float* d_evals, float* d_q1, float* d_stat);
+bool eig_supported(int n_beam);
+// flag.cu
+cudaError_t launch_flag(mraid_plan_s* pl, const float* d_stat, uint8_t* d_flags);
+int flag_grid_blocks(int device, int sm_count);
+
+}  // namespace mraid

@@ -1,0 +1,539 @@
+// plan.cu - the C ABI (include/mraid.h): validation, plans, launches of the
+// per-stage kernels and the host-buffer path.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "internal.h"
+
+namespace mraid {
+
+static thread_local char g_err[512];
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+mraid_status cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  if (e == cudaErrorMemoryAllocation) return MRAID_ERR_OOM;
+  return MRAID_ERR_CUDA;
+}
+
+const char* kernel_name(int id) {
+  switch (id) {
+    case K_GRAM: return "gram_u8";
+    case K_CORR: return "corr_from_sums";
+    case K_EIG: return "eig_jacobi";
+    case K_FLAG: return "flag_clip";
+  }
+  return "unknown";
+}
+
+static cudaEvent_t take_event(mraid_plan_s* pl) {
+  if (!pl->prof.pool.empty()) {
+    cudaEvent_t e = pl->prof.pool.back();
+    pl->prof.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+void prof_begin(mraid_plan_s* pl, int id, cudaEvent_t* start) {
+  (void)id;
+  *start = nullptr;
+  if (!pl->prof.on) return;
+  *start = take_event(pl);
+  if (*start) cudaEventRecord(*start, pl->stream);
+}
+
+void prof_end(mraid_plan_s* pl, int id, cudaEvent_t start) {
+  if (!pl->prof.on || !start) return;
+  cudaEvent_t stop = take_event(pl);
+  if (!stop) return;
+  cudaEventRecord(stop, pl->stream);
+  pl->prof.pending.push_back({id, start, stop});
+}
+
+// Fold recorded event pairs into the totals (the stream has been synced).
+static void prof_fold(mraid_plan_s* pl) {
+  for (auto& r : pl->prof.pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.start, r.stop) == cudaSuccess) {
+      pl->prof.total_ms[r.id] += ms;
+      pl->prof.launches[r.id] += 1;
+    }
+    pl->prof.pool.push_back(r.start);
+    pl->prof.pool.push_back(r.stop);
+  }
+  pl->prof.pending.clear();
+}
+
+#define MRAID_PROF(pl, id, expr)          \
+  ([&]() {                                \
+    cudaEvent_t s_;                       \
+    prof_begin((pl), (id), &s_);          \
+    cudaError_t e_ = (expr);              \
+    prof_end((pl), (id), s_);             \
+    return e_;                            \
+  }())
+
+namespace {
+
+// Sub-integrations per gram launch (grid.y bound) and per host-path chunk.
+constexpr int kMaxSubPerLaunch = 32768;
+
+mraid_status ensure_workspace(mraid_plan_s* pl, size_t cells) {
+  if (pl->ws.cells >= cells) return MRAID_OK;
+  cudaFree(pl->ws.sums);
+  cudaFree(pl->ws.corr);
+  pl->ws.sums = nullptr;
+  pl->ws.corr = nullptr;
+  pl->ws.cells = 0;
+  cudaError_t e = cudaMalloc(&pl->ws.sums, cells * (size_t)pl->psum * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&pl->ws.corr, cells * (size_t)pl->np * sizeof(float));
+  if (e != cudaSuccess) {
+    cudaFree(pl->ws.sums);
+    pl->ws.sums = nullptr;
+    pl->ws.corr = nullptr;
+    cudaGetLastError();
+    return cuda_fail(e, "workspace allocation");
+  }
+  pl->ws.cells = cells;
+  return MRAID_OK;
+}
+
+mraid_status check_plan(mraid_plan_t pl) {
+  if (!pl) {
+    set_error("plan is NULL");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != pl->device) {
+    e = cudaSetDevice(pl->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  }
+  return MRAID_OK;
+}
+
+// Gram sums + correlation of sub-integrations [sub0, sub0+n_sub) of d_data;
+// d_sums / d_corr are indexed by cell relative to sub0.
+mraid_status ccm_range(mraid_plan_s* pl, const void* d_data, int sub0, int n_sub, int64_t* d_sums,
+                       float* d_corr) {
+  const int64_t cells = (int64_t)n_sub * pl->p.n_chan;
+  int64_t* sums = d_sums;
+  if (!sums) {
+    mraid_status st = ensure_workspace(pl, (size_t)cells);
+    if (st != MRAID_OK) return st;
+    sums = pl->ws.sums;
+  }
+  for (int s = 0; s < n_sub; s += kMaxSubPerLaunch) {
+    const int ns = (n_sub - s) < kMaxSubPerLaunch ? (n_sub - s) : kMaxSubPerLaunch;
+    cudaError_t e = MRAID_PROF(pl, K_GRAM,
+                               launch_gram_u8(pl, static_cast<const uint8_t*>(d_data), sub0 + s, ns,
+                                              sums + (int64_t)s * pl->p.n_chan * pl->psum));
+    if (e != cudaSuccess) return cuda_fail(e, "gram launch");
+  }
+  if (d_corr) {
+    cudaError_t e = MRAID_PROF(pl, K_CORR, launch_corr_from_sums(pl, sums, cells, d_corr));
+    if (e != cudaSuccess) return cuda_fail(e, "corr launch");
+  }
+  return MRAID_OK;
+}
+
+mraid_status enqueue_info_copy(mraid_plan_s* pl, mraid_flag_info* info) {
+  cudaError_t e = cudaMemcpyAsync(pl->h_info, pl->d_info, sizeof(mraid_flag_info),
+                                  cudaMemcpyDeviceToHost, pl->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "info copy");
+  pl->pending_info = info;
+  return MRAID_OK;
+}
+
+}  // namespace
+}  // namespace mraid
+
+using namespace mraid;
+
+extern "C" {
+
+int32_t mraid_abi_version(void) { return MRAID_ABI_VERSION; }
+
+const char* mraid_last_error(void) { return g_err; }
+
+const char* mraid_status_string(mraid_status s) {
+  switch (s) {
+    case MRAID_OK: return "ok";
+    case MRAID_ERR_INVALID_ARG: return "invalid argument";
+    case MRAID_ERR_UNSUPPORTED: return "unsupported";
+    case MRAID_ERR_OOM: return "out of memory";
+    case MRAID_ERR_CUDA: return "CUDA error";
+    case MRAID_ERR_TIMEOUT: return "device wait timed out";
+    case MRAID_ERR_NOT_READY: return "not ready";
+  }
+  return "unknown status";
+}
+
+void mraid_default_params(mraid_params* p, int32_t n_beam, int32_t n_chan, int32_t n_samp_sub,
+                          int32_t n_sub) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->n_beam = n_beam;
+  p->n_chan = n_chan;
+  p->n_samp_sub = n_samp_sub;
+  p->n_sub = n_sub;
+  p->bit_depth = 8;
+  p->beam_stride = 0;
+  p->eig_k = 3.0;
+  p->vec_t = 1.0;
+  p->max_clip_iter = 64;
+  p->keep = nullptr;
+}
+
+mraid_status mraid_validate(const mraid_params* p) {
+  g_err[0] = 0;
+  if (!p) {
+    set_error("params is NULL");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  if (p->n_beam < 2) {
+    set_error("n_beam %d < 2", p->n_beam);
+    return MRAID_ERR_INVALID_ARG;
+  }
+  if (p->n_beam > kMaxBeam) {
+    set_error("n_beam %d > %d", p->n_beam, kMaxBeam);
+    return MRAID_ERR_UNSUPPORTED;
+  }
+  if (p->n_chan < 1 || p->n_sub < 1) {
+    set_error("n_chan %d and n_sub %d must be >= 1", p->n_chan, p->n_sub);
+    return MRAID_ERR_INVALID_ARG;
+  }
+  if (p->n_samp_sub < 2 || p->n_samp_sub > kMaxSampSub) {
+    set_error("n_samp_sub %d outside [2, %d]", p->n_samp_sub, kMaxSampSub);
+    return MRAID_ERR_INVALID_ARG;
+  }
+  if (p->bit_depth != 8) {
+    set_error("bit_depth %d: only 8-bit samples are built", p->bit_depth);
+    return MRAID_ERR_UNSUPPORTED;
+  }
+  const int64_t dense = (int64_t)p->n_sub * p->n_samp_sub * p->n_chan;
+  if (p->beam_stride != 0 && p->beam_stride < dense) {
+    set_error("beam_stride %lld smaller than one beam's block (%lld)", (long long)p->beam_stride,
+              (long long)dense);
+    return MRAID_ERR_INVALID_ARG;
+  }
+  if (!(p->eig_k > 0.0) || !(p->vec_t >= 0.0) || p->eig_k > 1e6) {
+    set_error("eig_k must be > 0 and vec_t >= 0");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  if (p->max_clip_iter < 1 || p->max_clip_iter > kMaxClipIter) {
+    set_error("max_clip_iter %d outside [1, %d]", p->max_clip_iter, kMaxClipIter);
+    return MRAID_ERR_INVALID_ARG;
+  }
+  if (p->reserved != 0) {
+    set_error("reserved field must be 0");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  return MRAID_OK;
+}
+
+mraid_status mraid_plan(const mraid_params* p, void* stream, mraid_plan_t* out) {
+  if (!out) {
+    set_error("out is NULL");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  mraid_status st = mraid_validate(p);
+  if (st != MRAID_OK) return st;
+  mraid_plan_s* pl = new (std::nothrow) mraid_plan_s();
+  if (!pl) {
+    set_error("host allocation failed");
+    return MRAID_ERR_OOM;
+  }
+  pl->p = *p;
+  pl->p.keep = nullptr;
+  pl->stream = static_cast<cudaStream_t>(stream);
+  pl->n_cells = (int64_t)p->n_sub * p->n_chan;
+  pl->beam_stride = p->beam_stride ? p->beam_stride : (int64_t)p->n_sub * p->n_samp_sub * p->n_chan;
+  pl->np = p->n_beam * (p->n_beam + 1) / 2;
+  pl->psum = (p->n_beam + 1) * (p->n_beam + 2) / 2;
+  cudaError_t e = cudaGetDevice(&pl->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, pl->device);
+  if (e == cudaSuccess) {
+    pl->flag_blocks = flag_grid_blocks(pl->device, pl->sm_count);
+    if (pl->flag_blocks < 1) e = cudaErrorLaunchOutOfResources;
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&pl->d_partials, sizeof(double) * 6 * (size_t)pl->flag_blocks);
+  if (e == cudaSuccess) e = cudaMalloc(&pl->d_info, sizeof(mraid_flag_info));
+  if (e == cudaSuccess) e = cudaMalloc(&pl->d_degenerate, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&pl->d_error, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMallocHost(&pl->h_info, sizeof(mraid_flag_info));
+  if (e == cudaSuccess && p->keep) {
+    e = cudaMalloc(&pl->d_keep, (size_t)p->n_chan);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->d_keep, p->keep, (size_t)p->n_chan, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_error, 0, sizeof(unsigned), pl->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_info, 0, sizeof(mraid_flag_info), pl->stream);
+  if (e != cudaSuccess) {
+    st = cuda_fail(e, "mraid_plan");
+    mraid_destroy(pl);
+    return st;
+  }
+  *out = pl;
+  return MRAID_OK;
+}
+
+mraid_status mraid_ccm(mraid_plan_t pl, const void* d_data, int64_t* d_sums, float* d_corr) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  if (!d_data || (!d_sums && !d_corr)) {
+    set_error("mraid_ccm: d_data and one of d_sums / d_corr are required");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  if (d_sums && pl->p.bit_depth != 8) {
+    set_error("mraid_ccm: exact sums exist for 8-bit data only");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  return ccm_range(pl, d_data, 0, pl->p.n_sub, d_sums, d_corr);
+}
+
+mraid_status mraid_eig(mraid_plan_t pl, const float* d_corr, float* d_evals, float* d_q1,
+                       float* d_stat) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  if (!d_corr || !d_stat) {
+    set_error("mraid_eig: d_corr and d_stat are required");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  cudaError_t e = MRAID_PROF(pl, K_EIG, launch_eig(pl, d_corr, pl->n_cells, d_evals, d_q1, d_stat));
+  return e == cudaSuccess ? MRAID_OK : cuda_fail(e, "eig launch");
+}
+
+mraid_status mraid_flag(mraid_plan_t pl, const float* d_stat, uint8_t* d_flags,
+                        mraid_flag_info* info) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  if (!d_stat || !d_flags) {
+    set_error("mraid_flag: d_stat and d_flags are required");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  cudaError_t e = MRAID_PROF(pl, K_FLAG, launch_flag(pl, d_stat, d_flags));
+  if (e != cudaSuccess) return cuda_fail(e, "flag launch");
+  return enqueue_info_copy(pl, info);
+}
+
+mraid_status mraid_run(mraid_plan_t pl, const void* d_data, float* d_evals, float* d_q1,
+                       float* d_stat, uint8_t* d_flags, mraid_flag_info* info) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  if (!d_data || !d_stat || !d_flags) {
+    set_error("mraid_run: d_data, d_stat and d_flags are required");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  st = ensure_workspace(pl, (size_t)pl->n_cells);
+  if (st != MRAID_OK) return st;
+  cudaError_t e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "memset");
+  st = ccm_range(pl, d_data, 0, pl->p.n_sub, pl->ws.sums, pl->ws.corr);
+  if (st != MRAID_OK) return st;
+  e = MRAID_PROF(pl, K_EIG, launch_eig(pl, pl->ws.corr, pl->n_cells, d_evals, d_q1, d_stat));
+  if (e != cudaSuccess) return cuda_fail(e, "eig launch");
+  e = MRAID_PROF(pl, K_FLAG, launch_flag(pl, d_stat, d_flags));
+  if (e != cudaSuccess) return cuda_fail(e, "flag launch");
+  e = cudaMemcpyAsync(&pl->d_info->n_degenerate, pl->d_degenerate, sizeof(int64_t),
+                      cudaMemcpyDeviceToDevice, pl->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "degenerate copy");
+  return enqueue_info_copy(pl, info);
+}
+
+mraid_status mraid_run_host(mraid_plan_t pl, const void* h_data, float* h_stat, uint8_t* h_flags,
+                            mraid_flag_info* info) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  if (!h_data || !h_flags) {
+    set_error("mraid_run_host: h_data and h_flags are required");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  if (pl->beam_stride != (int64_t)pl->p.n_sub * pl->p.n_samp_sub * pl->p.n_chan) {
+    set_error("mraid_run_host: host blocks must be dense (beam_stride 0)");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  const size_t esz = pl->p.bit_depth == 8 ? 1 : 4;
+  const int64_t sub_bytes = (int64_t)pl->p.n_samp_sub * pl->p.n_chan * (int64_t)esz;  // per beam
+  cudaError_t e = cudaSuccess;
+  if (!pl->copy_stream) {
+    // chunk: ~256 MiB of samples across all beams, whole sub-integrations
+    int64_t per_sub = sub_bytes * pl->p.n_beam;
+    int chunk = (int)((256ll << 20) / (per_sub > 0 ? per_sub : 1));
+    chunk = chunk < 1 ? 1 : (chunk > pl->p.n_sub ? pl->p.n_sub : chunk);
+    pl->chunk_subs = chunk;
+    pl->chunk_bytes = (size_t)per_sub * chunk;
+    e = cudaStreamCreateWithFlags(&pl->copy_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      e = cudaMalloc(&pl->d_chunk[i], pl->chunk_bytes);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_copied[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_consumed[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_stat_full, sizeof(float) * (size_t)pl->n_cells);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_flags_full, (size_t)pl->n_cells);
+    if (e != cudaSuccess) return cuda_fail(e, "host-path buffers");
+  }
+  const int chunk = pl->chunk_subs;
+  st = ensure_workspace(pl, (size_t)chunk * pl->p.n_chan);
+  if (st != MRAID_OK) return st;
+  e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
+  // The chunk buffer holds [beam][chunk subs * n_samp_sub][chan]; the kernels
+  // see it as a block of `chunk` sub-integrations with beam stride
+  // chunk * n_samp_sub * n_chan.
+  const int64_t saved_stride = pl->beam_stride;
+  const int32_t saved_nsub = pl->p.n_sub;
+  const int64_t saved_cells = pl->n_cells;
+  int k = 0;
+  for (int s0 = 0; s0 < saved_nsub && e == cudaSuccess; s0 += chunk, ++k) {
+    const int ns = (saved_nsub - s0) < chunk ? (saved_nsub - s0) : chunk;
+    const int slot = k & 1;
+    e = cudaStreamWaitEvent(pl->copy_stream, pl->ev_consumed[slot], 0);
+    for (int b = 0; b < pl->p.n_beam && e == cudaSuccess; ++b) {
+      const char* src = static_cast<const char*>(h_data) + (size_t)b * saved_stride * esz +
+                        (size_t)s0 * sub_bytes;
+      char* dst = reinterpret_cast<char*>(pl->d_chunk[slot]) + (size_t)b * chunk * sub_bytes;
+      e = cudaMemcpyAsync(dst, src, (size_t)ns * sub_bytes, cudaMemcpyHostToDevice, pl->copy_stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(pl->ev_copied[slot], pl->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(pl->stream, pl->ev_copied[slot], 0);
+    if (e != cudaSuccess) break;
+    pl->beam_stride = (int64_t)chunk * pl->p.n_samp_sub * pl->p.n_chan;
+    pl->p.n_sub = ns;
+    pl->n_cells = (int64_t)ns * pl->p.n_chan;
+    st = ccm_range(pl, pl->d_chunk[slot], 0, ns, pl->ws.sums, pl->ws.corr);
+    if (st == MRAID_OK) {
+      e = MRAID_PROF(pl, K_EIG, launch_eig(pl, pl->ws.corr, pl->n_cells, nullptr, nullptr,
+                                           pl->d_stat_full + (int64_t)s0 * pl->p.n_chan));
+    }
+    pl->beam_stride = saved_stride;
+    pl->p.n_sub = saved_nsub;
+    pl->n_cells = saved_cells;
+    if (st != MRAID_OK) return st;
+    if (e == cudaSuccess) e = cudaEventRecord(pl->ev_consumed[slot], pl->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "mraid_run_host");
+  e = MRAID_PROF(pl, K_FLAG, launch_flag(pl, pl->d_stat_full, pl->d_flags_full));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&pl->d_info->n_degenerate, pl->d_degenerate, sizeof(int64_t),
+                        cudaMemcpyDeviceToDevice, pl->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h_flags, pl->d_flags_full, (size_t)pl->n_cells, cudaMemcpyDeviceToHost, pl->stream);
+  if (e == cudaSuccess && h_stat)
+    e = cudaMemcpyAsync(h_stat, pl->d_stat_full, sizeof(float) * (size_t)pl->n_cells,
+                        cudaMemcpyDeviceToHost, pl->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "mraid_run_host");
+  return enqueue_info_copy(pl, info);
+}
+
+mraid_status mraid_sync(mraid_plan_t pl) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  cudaError_t e = cudaStreamSynchronize(pl->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "mraid_sync");
+  prof_fold(pl);
+  if (pl->pending_info) {
+    *pl->pending_info = *pl->h_info;
+    pl->pending_info = nullptr;
+  }
+  if (pl->h_info->timed_out) {
+    set_error("a bounded device wait expired");
+    return MRAID_ERR_TIMEOUT;
+  }
+  return MRAID_OK;
+}
+
+mraid_status mraid_query(mraid_plan_t pl) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  cudaError_t e = cudaStreamQuery(pl->stream);
+  if (e == cudaErrorNotReady) return MRAID_ERR_NOT_READY;
+  if (e != cudaSuccess) return cuda_fail(e, "mraid_query");
+  return mraid_sync(pl);
+}
+
+mraid_status mraid_profile_enable(mraid_plan_t pl, int32_t enable) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  pl->prof.on = enable != 0;
+  return MRAID_OK;
+}
+
+mraid_status mraid_profile_read(mraid_plan_t pl, mraid_kernel_time* out, int32_t max, int32_t* n) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  if (!n || (max > 0 && !out) || max < 0) {
+    set_error("mraid_profile_read: bad arguments");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  int32_t k = 0;
+  for (int id = 0; id < K_COUNT; ++id) {
+    if (pl->prof.launches[id] == 0) continue;
+    if (k < max) {
+      memset(&out[k], 0, sizeof(out[k]));
+      strncpy(out[k].name, kernel_name(id), sizeof(out[k].name) - 1);
+      out[k].launches = pl->prof.launches[id];
+      out[k].total_ms = pl->prof.total_ms[id];
+    }
+    ++k;
+  }
+  *n = k;
+  return MRAID_OK;
+}
+
+mraid_status mraid_profile_reset(mraid_plan_t pl) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  for (int id = 0; id < K_COUNT; ++id) {
+    pl->prof.launches[id] = 0;
+    pl->prof.total_ms[id] = 0.0;
+  }
+  return MRAID_OK;
+}
+
+void mraid_destroy(mraid_plan_t pl) {
+  if (!pl) return;
+  int dev = -1;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev != pl->device) cudaSetDevice(pl->device);
+  if (pl->stream || pl->d_info) cudaStreamSynchronize(pl->stream);
+  if (pl->copy_stream) {
+    cudaStreamSynchronize(pl->copy_stream);
+    cudaStreamDestroy(pl->copy_stream);
+  }
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(pl->d_chunk[i]);
+    if (pl->ev_copied[i]) cudaEventDestroy(pl->ev_copied[i]);
+    if (pl->ev_consumed[i]) cudaEventDestroy(pl->ev_consumed[i]);
+  }
+  prof_fold(pl);
+  for (cudaEvent_t ev : pl->prof.pool) cudaEventDestroy(ev);
+  cudaFree(pl->d_stat_full);
+  cudaFree(pl->d_flags_full);
+  cudaFree(pl->ws.sums);
+  cudaFree(pl->ws.corr);
+  cudaFree(pl->d_keep);
+  cudaFree(pl->d_partials);
+  cudaFree(pl->d_info);
+  cudaFree(pl->d_degenerate);
+  cudaFree(pl->d_error);
+  if (pl->h_info) cudaFreeHost(pl->h_info);
+  if (dev >= 0 && dev != pl->device) cudaSetDevice(dev);
+  delete pl;
+}
+
+}  // extern "C"

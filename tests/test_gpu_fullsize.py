@@ -1,0 +1,78 @@
+"""The FAST-shaped block at full size (19 beams x 4096 channels x 200
+sub-integrations x 1024 samples, 819200 cells) through mraid_run, the
+launch the benchmark times (needs a GPU and ~17 GB of device memory).
+
+The oracle checks sampled cells one by one on the same host bytes; the
+masking is checked through properties that hold at any size."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import STAT_TOL, compare_eig, compare_q1, lib
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fast_block():
+    import torch
+    cfg = synth.FAST_BLOCK
+    h = torch.empty(cfg.nbytes, dtype=torch.uint8, pin_memory=True)
+    synth.generate(cfg, out_ptr=h.data_ptr())
+    return cfg, h
+
+
+def test_fast_block_sampled_parity_and_mask_properties(fast_block):
+    import torch
+    m = lib()
+    cfg, h = fast_block
+    d = h.to("cuda", non_blocking=False)
+    with m.Plan(cfg.n_beam, cfg.n_chan, cfg.n_samp_sub, cfg.n_sub) as plan:
+        out = plan.run(d)
+        torch.cuda.synchronize()
+    stat = out["stat"].cpu().numpy()
+    evals = out["evals"].cpu().numpy()
+    q1 = out["q1"].cpu().numpy()
+    flags = out["flags"].cpu().numpy().astype(bool)
+    info = out["info"]
+    del d
+    torch.cuda.empty_cache()
+
+    # sampled cells against the oracle on the same bytes
+    rng = np.random.default_rng(2512)
+    ev = synth.events(cfg)
+    idx = set(rng.integers(0, cfg.n_cells, size=384).tolist())
+    idx |= {k * cfg.n_chan + c for (_, c, k, _) in ev["spike"][:64]}
+    idx |= {int(rng.integers(0, cfg.n_sub)) * cfg.n_chan + c for (c, _) in ev["narrow"][:32]}
+    for (_, k) in ev["burst"]:
+        idx |= {k * cfg.n_chan + int(c) for c in rng.integers(0, cfg.n_chan, size=16)}
+    idx = np.array(sorted(idx))
+    subs, chans = (idx // cfg.n_chan).astype(np.int32), (idx % cfg.n_chan).astype(np.int32)
+    o = oracle.cells(None, cfg.n_samp_sub, subs, chans, n_threads=synth.default_threads(),
+                     data_ptr=h.data_ptr(), shape=(cfg.n_beam, cfg.n_time, cfg.n_chan))
+    compare_eig(evals[idx], o["evals"], "fast block")
+    compare_q1(q1[idx], o["q1"], o["evals"])
+    s_err = np.abs(stat[idx] - o["stat"]) / o["stat"]
+    assert s_err.max() <= STAT_TOL, s_err.max()
+
+    # masking properties: the reported fit is the fit of the unmasked cells,
+    # every unmasked cell is at or below the final threshold, and the loop
+    # converged
+    assert info["converged"] == 1 and info["timed_out"] == 0
+    un = stat[~flags].astype(np.float64)
+    assert un.size == info["n_used"]
+    assert abs(un.mean() - info["mu"]) <= 1e-9 * abs(info["mu"])
+    assert abs(un.std() - info["sigma"]) <= 1e-6 * info["sigma"]
+    assert np.all(un <= info["thresh"])
+    assert abs(info["thresh"] - (info["mu"] + 3.0 * info["sigma"])) <= 1e-12
+    assert flags.sum() == info["n_flagged"]
+
+    # behaviour: beam-common RFI flagged, single-beam pulses not
+    F = flags.reshape(cfg.n_sub, cfg.n_chan)
+    for (c, _) in ev["narrow"]:
+        assert F[:, c].all(), c
+    for (_, k) in ev["burst"]:
+        assert F[k].mean() > 0.99 and F[k + 1].mean() > 0.99
+    spikes = [(k, c) for (_, c, k, _) in ev["spike"]]
+    assert np.mean([F[k, c] for (k, c) in spikes]) < 0.05
