@@ -111,6 +111,32 @@ mraid_status mraid_plan(const mraid_params* p, void* stream, mraid_plan_t* out);
 mraid_status mraid_ccm(mraid_plan_t plan, const void* d_data, int64_t* d_sums,
                        float* d_corr);
 
+/* mraid_ccm without any allocation (the paper has no counterpart; this is
+ * an interface for callers). Some callers cannot call cudaMalloc: pipelines
+ * that reserved the whole device for their own memory pool before loading
+ * this library, and real-time loops that must not make a call that can
+ * synchronise the device and stall their other streams. This entry point
+ * needs no plan and allocates nothing: its int64 Gram sums and zero-variance
+ * counter live in one fixed 8 MiB __device__ array inside the library, which
+ * every GPU that loads the library holds until the process exits.
+ *   p:        as for mraid_plan (bit_depth 8; keep is ignored).
+ *   d_data:   samples of the whole block, layout above.
+ *   sub0, n_sub: the sub-integrations [sub0, sub0 + n_sub) to process.
+ *   d_corr:   float32 [n_sub * n_chan][N(N+1)/2], cells relative to sub0,
+ *             the same values mraid_ccm writes for those cells.
+ *   stream:   cudaStream_t (NULL = legacy default stream).
+ * Limit: n_sub * n_chan * 8 * (N+1)(N+2)/2 + 256 bytes must fit the 8 MiB
+ * array (4993 cells for 19 beams); larger requests return
+ * MRAID_ERR_INVALID_ARG with a message, so split the block over calls.
+ * The first call on a device looks up the array's device address with
+ * that device current (cudaGetSymbolAddress); make that first call before
+ * any stream capture. Every call reuses the same array: calls that can
+ * overlap on the GPU (different streams, or different host threads on one
+ * device) race and corrupt each other's sums, so serialise them, e.g. on
+ * one stream. */
+mraid_status mraid_ccm_noalloc(const mraid_params* p, const void* d_data, int32_t sub0,
+                               int32_t n_sub, float* d_corr, void* stream);
+
 /* Section 3.3, Eq. 2: eigenvalues of every cell's correlation (parallel
  * cyclic Jacobi in FP32), its dominant eigenvector and statistic.
  *   d_corr:  float32 [cell][N(N+1)/2] as written by mraid_ccm.

@@ -21,7 +21,8 @@ __all__ = [
     "mraid_default_params", "mraid_validate", "mraid_plan", "mraid_ccm", "mraid_eig",
     "mraid_flag", "mraid_run", "mraid_run_host", "mraid_sync", "mraid_query",
     "mraid_destroy", "mraid_status_string", "mraid_last_error", "mraid_abi_version",
-    "mraid_profile_enable", "mraid_profile_read", "mraid_profile_reset", "STATUS",
+    "mraid_profile_enable", "mraid_profile_read", "mraid_profile_reset", "mraid_ccm_noalloc",
+    "STATUS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -107,6 +108,7 @@ def load():
         "mraid_profile_read": (ctypes.c_int, [vp, ctypes.POINTER(KernelTime), i32,
                                               ctypes.POINTER(i32)]),
         "mraid_profile_reset": (ctypes.c_int, [vp]),
+        "mraid_ccm_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), vp, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -150,6 +152,15 @@ def mraid_plan(p: Params, stream: int = 0) -> int:
 
 def mraid_ccm(plan: int, d_data, d_sums=None, d_corr=None):
     _check(load().mraid_ccm(plan, _ptr(d_data), _ptr(d_sums), _ptr(d_corr)), "mraid_ccm")
+
+
+def mraid_ccm_noalloc(p: Params, d_data, sub0: int, n_sub: int, d_corr, stream: int = 0):
+    """Correlations of sub-integrations [sub0, sub0+n_sub) without any
+    allocation: the library's fixed 8 MiB device array holds the Gram sums.
+    For callers that cannot call cudaMalloc; calls must not overlap on the
+    GPU (they share that array)."""
+    _check(load().mraid_ccm_noalloc(ctypes.byref(p), _ptr(d_data), sub0, n_sub, _ptr(d_corr),
+                                    stream or None), "mraid_ccm_noalloc")
 
 
 def mraid_eig(plan: int, d_corr, d_evals=None, d_q1=None, d_stat=None):
