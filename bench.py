@@ -44,13 +44,18 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-sub", type=int, default=0,
+                    help="shrink the block to this many sub-integrations (profiling runs)")
     return ap.parse_args()
 
 
-def workload(name, rank):
+def workload(name, rank, n_sub=0):
     import synth
     base = synth.FAST_BLOCK if name == "fast_block" else synth.SMALL
     cfg = base.replace(seed=base.seed + 7919 * rank)
+    if n_sub:
+        cfg = cfg.replace(n_sub=n_sub, n_burst=min(cfg.n_burst, max(0, n_sub - 1)),
+                          n_spike=min(cfg.n_spike, n_sub * cfg.n_chan // 1000 + 1))
     desc = (f"FAST-shaped block: {cfg.n_beam} beams x {cfg.n_chan} channels x {cfg.n_sub} "
             f"sub-integrations x {cfg.n_samp_sub} samples, uint8 ({cfg.n_cells} cells, "
             f"{cfg.nbytes / 1e9:.2f} GB)")
@@ -213,7 +218,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import torch
-    cfg, desc = workload(args.workload, 0)
+    cfg, desc = workload(args.workload, 0, args.n_sub)
     import synth
     h = torch.empty(cfg.nbytes, dtype=torch.uint8)
     synth.generate(cfg, out_ptr=h.data_ptr())
@@ -253,7 +258,7 @@ def run_mraid(args):
     mbuild.build()
     import synth
 
-    cfg, desc = workload(args.workload, rank)
+    cfg, desc = workload(args.workload, rank, args.n_sub)
     h = torch.empty(cfg.nbytes, dtype=torch.uint8, pin_memory=True)
     synth.generate(cfg, out_ptr=h.data_ptr())
     d = h.to("cuda")

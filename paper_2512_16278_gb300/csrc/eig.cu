@@ -232,7 +232,7 @@ __device__ bool dominant_vector(const float* r, float lambda1, float (&x)[N]) {
 template <int N>
 __global__ void __launch_bounds__(kEigThreads)
 eig_reg_kernel(const float* __restrict__ corr, int64_t n_cells, float* __restrict__ evals,
-               float* __restrict__ q1, float* __restrict__ stat) {
+               float* __restrict__ stat) {
   using S = Slots<N>;
   constexpr int NP = S::NP;
   constexpr int STR = NP | 1;  // odd stride: conflict-free per-thread rows
@@ -287,21 +287,40 @@ eig_reg_kernel(const float* __restrict__ corr, int64_t n_cells, float* __restric
   static_for<N>([&](auto kk) { ss = fmaf(ev[decltype(kk)::value], ev[decltype(kk)::value], ss); });
   stat[cell] = ss > 0.f ? ev[0] * ev[0] / ss : 0.f;
   if (evals) static_for<N>([&](auto kk) { evals[cell * N + decltype(kk)::value] = ev[decltype(kk)::value]; });
-  if (q1) {
-    float x[N];
-    const bool ok = dominant_vector<N>(my, ev[0], x);
-    // sign rule: largest-magnitude element positive (lowest index on ties)
-    float best = 0.f, sgn = 1.f;
-    static_for<N>([&](auto kk) {
-      const float v = x[decltype(kk)::value];
-      if (fabsf(v) > best) {
-        best = fabsf(v);
-        sgn = v < 0.f ? -1.f : 1.f;
-      }
-    });
-    if (!ok) sgn = __int_as_float(0x7fc00000);  // NaN marks a failed factor
-    static_for<N>([&](auto kk) { q1[cell * N + decltype(kk)::value] = sgn * x[decltype(kk)::value]; });
+}
+
+// q1 of every cell from its correlation and lambda_1 (evals[cell * N]): a
+// separate pass so that the Jacobi sweeps keep all registers.
+template <int N>
+__global__ void __launch_bounds__(kEigThreads)
+q1_reg_kernel(const float* __restrict__ corr, int64_t n_cells, const float* __restrict__ evals,
+              float* __restrict__ q1) {
+  constexpr int NP = Slots<N>::NP;
+  constexpr int STR = NP | 1;
+  extern __shared__ float sm[];
+  const int64_t cell0 = (int64_t)blockIdx.x * kEigThreads;
+  const int ncell = (int)min((int64_t)kEigThreads, n_cells - cell0);
+  const float* src = corr + cell0 * NP;
+  for (int i = threadIdx.x; i < ncell * NP; i += blockDim.x) {
+    const int c = i / NP;
+    sm[c * STR + (i - c * NP)] = src[i];
   }
+  __syncthreads();
+  if ((int)threadIdx.x >= ncell) return;
+  const int64_t cell = cell0 + threadIdx.x;
+  float x[N];
+  const bool ok = dominant_vector<N>(sm + threadIdx.x * STR, evals[cell * N], x);
+  // sign rule: largest-magnitude element positive (lowest index on ties)
+  float best = 0.f, sgn = 1.f;
+  static_for<N>([&](auto kk) {
+    const float v = x[decltype(kk)::value];
+    if (fabsf(v) > best) {
+      best = fabsf(v);
+      sgn = v < 0.f ? -1.f : 1.f;
+    }
+  });
+  if (!ok) sgn = __int_as_float(0x7fc00000);  // NaN marks a failed factor
+  static_for<N>([&](auto kk) { q1[cell * N + decltype(kk)::value] = sgn * x[decltype(kk)::value]; });
 }
 
 // ---------------------------------------------------------------------------
@@ -489,19 +508,30 @@ cudaError_t launch_reg(const float* d_corr, int64_t n_cells, float* d_evals, flo
                        float* d_stat, cudaStream_t stream) {
   constexpr int STR = Slots<N>::NP | 1;
   const size_t smem = (size_t)kEigThreads * STR * sizeof(float);
+  const int64_t blocks = (n_cells + kEigThreads - 1) / kEigThreads;
   cudaError_t e = cudaFuncSetAttribute(eig_reg_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = (n_cells + kEigThreads - 1) / kEigThreads;
   if (blocks > 0)
     eig_reg_kernel<N><<<(unsigned)blocks, kEigThreads, smem, stream>>>(d_corr, n_cells, d_evals,
-                                                                          d_q1, d_stat);
+                                                                          d_stat);
+  if (d_q1) {
+    e = cudaFuncSetAttribute(q1_reg_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (blocks > 0)
+      q1_reg_kernel<N><<<(unsigned)blocks, kEigThreads, smem, stream>>>(d_corr, n_cells, d_evals,
+                                                                           d_q1);
+  }
   return cudaGetLastError();
 }
 
 }  // namespace
 
 bool eig_supported(int n_beam) { return n_beam >= 2 && n_beam <= kMaxBeam; }
+
+bool eig_q1_needs_evals(int n_beam) {
+  return n_beam == 2 || n_beam == 3 || n_beam == 4 || n_beam == 13 || n_beam == 19;
+}
 
 cudaError_t launch_eig(const mraid_plan_s* pl, const float* d_corr, int64_t n_cells, float* d_evals,
                        float* d_q1, float* d_stat) {

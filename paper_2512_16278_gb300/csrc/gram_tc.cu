@@ -1,0 +1,562 @@
+// gram_tc.cu - exact augmented Gram sums of 8-bit multi-beam data on the
+// 5th-generation tensor cores (tcgen05), fused with the correlation.
+//
+// Section 3.2, Eq. 1. For a cell (channel j, sub-integration k) with
+// samples x_b(t), the kernel forms G = Y~ Y~^T with Y~ = [x - 128; 1]:
+// the centred values x - 128 are exact in f16, every product is an integer
+// of magnitude <= 2^14 and every partial sum over <= 1024 samples is an
+// integer of magnitude <= 2^24, so the FP32 tensor-core accumulation is
+// exact. From the centred sums, cov_ab = n G_ab - G_a G_b is exact in int64
+// (it does not depend on the centring) and r_ab = cov_ab / sqrt(var_a var_b)
+// is rounded to float once. The raw uint8 sums, when requested, follow from
+// S_ab = G_ab + 128 (G_a + G_b) + 128^2 n and S_a = G_a + 128 n.
+//
+// Data flow per persistent CTA (one per SM), warp-specialised:
+//   warp 0    TMA: box {16 channels, 64 samples, N beams} of u8 into a
+//             4-deep ring (cp.async.bulk.tensor, mbarrier transaction count);
+//   warps 4-7 convert each box to centred f16 operand tiles in the
+//             MN-major canonical layout (8 channels x 8 samples per core
+//             matrix), one tile per 8-channel group, into a 2-deep ring;
+//   warp 1    one thread issues tcgen05.mma (kind::f16, FP32 accumulate in
+//             TMEM): per group D1 = A(slots 0..15) x B(slots 0..N)^T and,
+//             for N >= 16, D2 = A(slots 16..31) x B(slots 16..N)^T; a slot is
+//             one beam (slot N is the row of ones) across 8 channels, so the
+//             useful entries of D are those with equal channel;
+//   warps 8-11 read TMEM (tcgen05.ld), keep each row's own-channel entries,
+//             and write the packed correlation (and optionally the sums).
+// Every wait is bounded (~2 s on the global timer); on expiry the kernel
+// records an error word, drains its in-flight copies and MMAs (again
+// bounded), frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+#include "internal.h"
+
+namespace mraid {
+namespace {
+
+constexpr int kT = 64;                 // samples per stage
+constexpr int kBoxCh = 16;             // channels per TMA box (16 bytes)
+constexpr int kGroupSlots = 24;        // slots laid out per 8-channel group
+constexpr int kSlack = 8;              // slots after group 1 (A2 rows 24..31)
+constexpr int kSlotBytes = kT * 16;    // one slot: kT samples x 8 channels x f16
+constexpr int kGroupBytes = kGroupSlots * kSlotBytes;
+constexpr int kF16StageBytes = (2 * kGroupSlots + kSlack) * kSlotBytes;
+constexpr int kNU = 4;                 // u8 ring depth
+constexpr int kNF = 2;                 // f16 ring depth
+constexpr int kThreads = 384;
+constexpr int kConvThreads = 128;
+constexpr int kEpiThreads = 128;
+constexpr uint32_t kTmemCols = 512;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+
+struct TcArgs {
+  int n_beam, n_chan, n_samp_sub, sub0, n_sub;
+  int rb;   // slots in B of the first MMA (N+1 rounded up to even)
+  int r2;   // slots in B of the second MMA (0 if N+1 <= 16), even
+  int swap_ls;  // nonzero: exchange the LBO / SBO fields of the descriptors
+  int64_t* sums;
+  float* corr;
+  unsigned long long* degenerate;
+  unsigned* error;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of `parity` to complete; false on timeout or
+// when another role already reported an error.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* error) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 255) == 255) {
+      if (*(volatile unsigned*)error) return false;
+      if (gtimer() - t0 > kWaitNs) {
+        atomicOr(error, 1u);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// tcgen05 shared-memory descriptor, no swizzle: start address, leading and
+// stride byte offsets (>> 4), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3fff) | ((uint64_t)((lbo >> 4) & 0x3fff) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3fff) << 32) | (1ull << 46);
+}
+// Instruction descriptor, kind::f16: f16 A/B, f32 D, both operands MN-major.
+__host__ __device__ constexpr uint32_t idesc_f16(int m, int n) {
+  return (1u << 4) | (0u << 7) | (0u << 10) | (1u << 15) | (1u << 16) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+// 32 consecutive TMEM columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Keep the 4 entries of a 32-column chunk whose channel equals c (columns
+// 8u + c, u = 0..3) with compile-time register indices.
+__device__ __forceinline__ void pick4(const uint32_t (&v)[32], int c, float* out) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    uint32_t x = v[8 * u];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) x = (c == k) ? v[8 * u + k] : x;
+    out[u] = __uint_as_float(x);
+  }
+}
+
+struct Smem {
+  uint64_t u8_full[kNU], u8_empty[kNU];
+  uint64_t f16_full[kNF], f16_empty[kNF];
+  uint64_t acc_full, acc_empty, drain;
+  uint32_t tmem_base;
+  int32_t s_sum[2][8][kGroupSlots];   // centred row sums G_a per group/channel/slot
+  float s_inv[2][8][kGroupSlots];     // 1/sqrt(var_a), 0 if var_a == 0
+};
+
+// dynamic shared memory for n_beam beams: f16 ring, u8 ring, barriers
+__host__ __device__ constexpr size_t smem_bytes(int n_beam) {
+  return 1024 /* alignment slack */ + (size_t)kNF * kF16StageBytes +
+         (size_t)kNU * n_beam * kT * kBoxCh + sizeof(Smem);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* f16 = base;                                   // kNF stages
+  unsigned char* u8 = f16 + (size_t)kNF * kF16StageBytes;      // kNU stages
+  const int u8_stage_bytes = g.n_beam * kT * kBoxCh;
+  Smem* s = reinterpret_cast<Smem*>(u8 + (size_t)kNU * u8_stage_bytes);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int N = g.n_beam;
+  const int chunks = g.n_chan / kBoxCh;
+  const int64_t items = (int64_t)g.n_sub * chunks;
+  const int stages = g.n_samp_sub / kT;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kNU; ++i) {
+      mbar_init(&s->u8_full[i], 1);
+      mbar_init(&s->u8_empty[i], kConvThreads);
+    }
+    for (int i = 0; i < kNF; ++i) {
+      mbar_init(&s->f16_full[i], kConvThreads);
+      mbar_init(&s->f16_empty[i], 1);
+    }
+    mbar_init(&s->acc_full, 1);
+    mbar_init(&s->acc_empty, kEpiThreads);
+    mbar_init(&s->drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // constant slots of every f16 stage: the row of ones (slot N), zero rows
+  // above it, and the slack after group 1
+  const uint32_t one2 = 0x3c003c00u;  // f16x2 (1.0, 1.0)
+  for (int st = 0; st < kNF; ++st) {
+    uint32_t* w = reinterpret_cast<uint32_t*>(f16 + (size_t)st * kF16StageBytes);
+    for (int grp = 0; grp < 2; ++grp)
+      for (int i = threadIdx.x; i < (kGroupSlots - N) * kSlotBytes / 4; i += blockDim.x) {
+        const int slot = N + i / (kSlotBytes / 4);
+        w[(grp * kGroupBytes + N * kSlotBytes) / 4 + i] = (slot == N) ? one2 : 0u;
+      }
+    for (int i = threadIdx.x; i < kSlack * kSlotBytes / 4; i += blockDim.x)
+      w[(2 * kGroupBytes) / 4 + i] = 0u;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s->tmem_base)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = s->tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA
+    if (lane == 0) {
+      uint32_t cnt = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        const int k = (int)(it / chunks), ch0 = (int)(it % chunks) * kBoxCh;
+        const int64_t t_item = (int64_t)(g.sub0 + k) * g.n_samp_sub;
+        for (int st = 0; st < stages && ok; ++st, ++cnt) {
+          const int slot = cnt % kNU;
+          ok = mbar_wait(&s->u8_empty[slot], ((cnt / kNU) & 1) ^ 1, g.error);
+          if (!ok) break;
+          mbar_expect_tx(&s->u8_full[slot], (uint32_t)u8_stage_bytes);
+          tma_load_3d(u8 + (size_t)slot * u8_stage_bytes, &tmap, ch0, (int)(t_item + st * kT), 0,
+                      &s->u8_full[slot]);
+        }
+      }
+      // drain: every issued copy has landed before the CTA may exit
+      for (uint32_t d = cnt > kNU ? cnt - kNU : 0; d < cnt; ++d)
+        mbar_wait(&s->u8_full[d % kNU], (d / kNU) & 1, g.error);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA
+    if (lane == 0) {
+      const uint32_t f16_base = smem_u32(f16);
+      const uint32_t id1 = idesc_f16(128, 8 * g.rb);
+      const uint32_t id2 = idesc_f16(128, g.r2 > 0 ? 8 * g.r2 : 16);
+      // no-swizzle canonical layout: K-adjacent core matrices 128 B apart,
+      // MN-adjacent (next slot) kSlotBytes apart
+      const uint32_t lbo = g.swap_ls ? kSlotBytes : 128, sbo = g.swap_ls ? 128 : kSlotBytes;
+      uint32_t fcnt = 0, item_iter = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x, ++item_iter) {
+        for (int st = 0; st < stages && ok; ++st, ++fcnt) {
+          const int fs = fcnt % kNF;
+          ok = mbar_wait(&s->f16_full[fs], (fcnt / kNF) & 1, g.error);
+          if (!ok) break;
+          if (st == 0 && item_iter > 0) {
+            ok = mbar_wait(&s->acc_empty, (item_iter - 1) & 1, g.error);
+            if (!ok) break;
+          }
+          fence_after();
+          const uint32_t stage_addr = f16_base + (uint32_t)(fs * kF16StageBytes);
+#pragma unroll
+          for (int grp = 0; grp < 2; ++grp) {
+            const uint32_t gaddr = stage_addr + grp * kGroupBytes;
+            const uint32_t d1 = tmem + grp * 256;
+            const uint32_t d2 = tmem + grp * 256 + 192;
+#pragma unroll
+            for (int ks = 0; ks < kT / 16; ++ks) {
+              const uint32_t koff = ks * 256;  // 16 samples = two 128-byte core matrices
+              const uint32_t acc = (st > 0 || ks > 0) ? 1u : 0u;
+              mma_f16(d1, smem_desc(gaddr + koff, lbo, sbo), smem_desc(gaddr + koff, lbo, sbo), id1,
+                      acc);
+              if (g.r2 > 0)
+                mma_f16(d2, smem_desc(gaddr + 16 * kSlotBytes + koff, lbo, sbo),
+                        smem_desc(gaddr + 16 * kSlotBytes + koff, lbo, sbo), id2, acc);
+            }
+          }
+          mma_commit(&s->f16_empty[fs]);  // stage buffer free once these MMAs finish
+          if (st == stages - 1) mma_commit(&s->acc_full);
+        }
+      }
+      mma_commit(&s->drain);
+      mbar_wait(&s->drain, 0, g.error);
+    }
+  } else if (warp >= 4 && warp < 8) {
+    // ------------------------------------------------------------ convert
+    const int ct = threadIdx.x - 4 * 32;
+    const uint32_t magic = 0x64646464u;   // f16 bit pattern 0x64xx = 1024 + x
+    const uint32_t bias = 0x64806480u;    // f16x2 (1152, 1152)
+    uint32_t cnt = 0;
+    bool ok = true;
+    for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
+      for (int st = 0; st < stages && ok; ++st, ++cnt) {
+        const int us = cnt % kNU, fs = cnt % kNF;
+        ok = mbar_wait(&s->u8_full[us], (cnt / kNU) & 1, g.error);
+        if (ok) ok = mbar_wait(&s->f16_empty[fs], ((cnt / kNF) & 1) ^ 1, g.error);
+        if (!ok) break;
+        const uint4* src = reinterpret_cast<const uint4*>(u8 + (size_t)us * u8_stage_bytes);
+        unsigned char* dst = f16 + (size_t)fs * kF16StageBytes;
+        for (int r = ct; r < N * kT; r += kConvThreads) {
+          const uint4 w = src[r];  // 16 channels of beam b at sample t
+          const int b = r / kT, t = r % kT;
+          const uint32_t off = b * kSlotBytes + (t / 8) * 128 + (t % 8) * 16;
+          uint4 o0, o1;
+          asm("sub.f16x2 %0, %1, %2;" : "=r"(o0.x) : "r"(__byte_perm(w.x, magic, 0x4140)), "r"(bias));
+          asm("sub.f16x2 %0, %1, %2;" : "=r"(o0.y) : "r"(__byte_perm(w.x, magic, 0x4342)), "r"(bias));
+          asm("sub.f16x2 %0, %1, %2;" : "=r"(o0.z) : "r"(__byte_perm(w.y, magic, 0x4140)), "r"(bias));
+          asm("sub.f16x2 %0, %1, %2;" : "=r"(o0.w) : "r"(__byte_perm(w.y, magic, 0x4342)), "r"(bias));
+          asm("sub.f16x2 %0, %1, %2;" : "=r"(o1.x) : "r"(__byte_perm(w.z, magic, 0x4140)), "r"(bias));
+          asm("sub.f16x2 %0, %1, %2;" : "=r"(o1.y) : "r"(__byte_perm(w.z, magic, 0x4342)), "r"(bias));
+          asm("sub.f16x2 %0, %1, %2;" : "=r"(o1.z) : "r"(__byte_perm(w.w, magic, 0x4140)), "r"(bias));
+          asm("sub.f16x2 %0, %1, %2;" : "=r"(o1.w) : "r"(__byte_perm(w.w, magic, 0x4342)), "r"(bias));
+          *reinterpret_cast<uint4*>(dst + off) = o0;
+          *reinterpret_cast<uint4*>(dst + kGroupBytes + off) = o1;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&s->u8_empty[us]);
+        mbar_arrive(&s->f16_full[fs]);
+      }
+    }
+  } else if (warp >= 8) {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp - 8;              // TMEM lane quarter
+    const int c = lane % 8;              // channel within the group
+    const int slot = 4 * q + lane / 8;   // D1 row slot (beam a, 0..15)
+    const int slot2 = 16 + 4 * q + lane / 8;  // D2 row slot (TMEM lane 32q + lane)
+    const int64_t n = g.n_samp_sub;
+    uint32_t item_iter = 0;
+    bool ok = true;
+    for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x, ++item_iter) {
+      ok = mbar_wait(&s->acc_full, item_iter & 1, g.error);
+      if (!ok) break;
+      fence_after();
+      float row[2][kGroupSlots];   // D1 row `slot`: G[slot][0..rb)
+      float row2[2][8];            // D2 row `slot2`: G[slot2][16..16+r2)
+#pragma unroll
+      for (int grp = 0; grp < 2; ++grp) {
+#pragma unroll
+        for (int ch = 0; ch < kGroupSlots / 4; ++ch) {
+          if (ch * 4 < g.rb) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + grp * 256 + ch * 32, v);
+            tmem_wait_ld();
+            pick4(v, c, &row[grp][4 * ch]);
+          }
+        }
+        if (g.r2 > 0) {
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + grp * 256 + 192, v);
+          tmem_wait_ld();
+          pick4(v, c, &row2[grp][0]);
+          uint32_t v2[32];
+          tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + grp * 256 + 224, v2);
+          tmem_wait_ld();
+          pick4(v2, c, &row2[grp][4]);
+        }
+      }
+      fence_before();
+      mbar_arrive(&s->acc_empty);  // accumulators may be overwritten now
+
+      const int k = (int)(it / chunks), ch0 = (int)(it % chunks) * kBoxCh;
+      // row sums and inverse standard deviations, shared through smem
+#pragma unroll
+      for (int grp = 0; grp < 2; ++grp) {
+        if (slot < N + 1) {
+          const int64_t sa = (int64_t)row[grp][N];
+          const int64_t var = n * (int64_t)row[grp][slot] - sa * sa;
+          s->s_sum[grp][c][slot] = (int32_t)sa;
+          float inv = 0.f;
+          if (slot < N) {
+            if (var > 0) {
+              const float vf = (float)var;
+              inv = rsqrtf(vf);
+              inv = inv * (1.5f - 0.5f * vf * inv * inv);
+            } else {
+              atomicAdd(g.degenerate, 1ull);
+            }
+          }
+          s->s_inv[grp][c][slot] = inv;
+        }
+        if (g.r2 > 0 && slot2 < N + 1) {
+          const int64_t sa = (int64_t)row2[grp][N - 16];
+          const int64_t var = n * (int64_t)row2[grp][slot2 - 16] - sa * sa;
+          s->s_sum[grp][c][slot2] = (int32_t)sa;
+          float inv = 0.f;
+          if (slot2 < N) {
+            if (var > 0) {
+              const float vf = (float)var;
+              inv = rsqrtf(vf);
+              inv = inv * (1.5f - 0.5f * vf * inv * inv);
+            } else {
+              atomicAdd(g.degenerate, 1ull);
+            }
+          }
+          s->s_inv[grp][c][slot2] = inv;
+        }
+      }
+      named_sync(1, kEpiThreads);
+#pragma unroll
+      for (int grp = 0; grp < 2; ++grp) {
+        const int64_t cell = (int64_t)k * g.n_chan + ch0 + grp * 8 + c;
+        // rows a = slot (all b >= a from D1) and a = slot2 (b >= a from D2)
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass) {
+          const int a = pass == 0 ? slot : slot2;
+          if (pass == 1 && g.r2 == 0) continue;
+          if (a > N) continue;
+          const float* rv = pass == 0 ? row[grp] : row2[grp];
+          const int b0 = pass == 0 ? 0 : 16;
+          const int64_t sa = s->s_sum[grp][c][a];
+          const float inva = s->s_inv[grp][c][a];
+          if (g.corr && a < N) {
+            float* dst = g.corr + cell * (int64_t)(N * (N + 1) / 2) + (a * N - a * (a - 1) / 2);
+#pragma unroll
+            for (int b = 0; b < kGroupSlots; ++b) {
+              if (b < a || b >= N || b < b0 || b - b0 >= (pass == 0 ? g.rb : g.r2)) continue;
+              float r;
+              if (b == a) {
+                r = 1.f;
+              } else {
+                const int64_t cov = n * (int64_t)rv[b - b0] - sa * (int64_t)s->s_sum[grp][c][b];
+                r = (float)cov * inva * s->s_inv[grp][c][b];
+              }
+              dst[b - a] = r;
+            }
+          }
+          if (g.sums) {
+            const int N1 = N + 1;
+            int64_t* dst = g.sums + cell * (int64_t)(N1 * (N1 + 1) / 2) + (a * N1 - a * (a - 1) / 2);
+#pragma unroll
+            for (int b = 0; b < kGroupSlots; ++b) {
+              if (b < a || b > N || b < b0 || b - b0 >= (pass == 0 ? g.rb : g.r2)) continue;
+              const int64_t gab = (int64_t)rv[b - b0];
+              int64_t v;
+              if (a == N) v = n;                                  // (N, N): sample count
+              else if (b == N) v = gab + 128 * n;                 // S_a
+              else v = gab + 128 * (sa + (int64_t)s->s_sum[grp][c][b]) + 16384 * n;
+              dst[b - a] = v;
+            }
+          }
+        }
+      }
+      named_sync(1, kEpiThreads);  // smem tables reused by the next item
+    }
+  }
+  __syncthreads();
+  if (warp == 2) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols));
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+int tc_swap_ls() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("MRAID_TC_SWAP_LS");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  return v;
+}
+
+}  // namespace
+
+bool gram_tc_supported(const mraid_plan_s* pl, const void* d_data) {
+  const mraid_params& p = pl->p;
+  return p.bit_depth == 8 && p.n_beam >= 2 && p.n_beam + 1 <= kGroupSlots &&
+         p.n_samp_sub % kT == 0 && p.n_samp_sub <= 1024 && p.n_chan % kBoxCh == 0 &&
+         pl->beam_stride % 16 == 0 && (reinterpret_cast<uintptr_t>(d_data) & 15) == 0 &&
+         encode_fn() != nullptr;
+}
+
+cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int sub0, int n_sub,
+                           int64_t* d_sums, float* d_corr) {
+  const mraid_params& p = pl->p;
+  if (!gram_tc_supported(pl, d_data)) return cudaErrorNotSupported;
+  CUtensorMap map;
+  const cuuint64_t n_time = (cuuint64_t)(sub0 + n_sub) * p.n_samp_sub;
+  cuuint64_t dims[3] = {(cuuint64_t)p.n_chan, n_time, (cuuint64_t)p.n_beam};
+  cuuint64_t strides[2] = {(cuuint64_t)p.n_chan, (cuuint64_t)pl->beam_stride};
+  cuuint32_t box[3] = {(cuuint32_t)kBoxCh, (cuuint32_t)kT, (cuuint32_t)p.n_beam};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t*>(d_data),
+                           dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  TcArgs a;
+  a.n_beam = p.n_beam;
+  a.n_chan = p.n_chan;
+  a.n_samp_sub = p.n_samp_sub;
+  a.sub0 = sub0;
+  a.n_sub = n_sub;
+  const int R = p.n_beam + 1;              // beams + the row of ones
+  a.rb = (R + 1) / 2 * 2;                  // B of the first MMA: slots 0..R-1, even count
+  a.r2 = R > 16 ? ((R - 16) + 1) / 2 * 2 : 0;
+  a.swap_ls = tc_swap_ls();
+  a.sums = d_sums;
+  a.corr = d_corr;
+  a.degenerate = pl->d_degenerate;
+  a.error = pl->d_error;
+  const size_t smem = smem_bytes(p.n_beam);
+  cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t items = (int64_t)n_sub * (p.n_chan / kBoxCh);
+  const int grid = (int)(items < pl->sm_count ? items : pl->sm_count);
+  if (grid > 0) gram_tc_kernel<<<grid, kThreads, smem, pl->stream>>>(map, a);
+  return cudaGetLastError();
+}
+
+}  // namespace mraid

@@ -21,7 +21,7 @@ struct FlagDev {  // device image of mraid_flag_info
   mraid_flag_info info;
 };
 
-enum KernelId { K_GRAM = 0, K_CORR, K_EIG, K_FLAG, K_COUNT };
+enum KernelId { K_GRAM = 0, K_CORR, K_EIG, K_FLAG, K_GRAM_TC, K_COUNT };
 const char* kernel_name(int id);
 
 struct Profiler {
@@ -40,6 +40,8 @@ struct Workspace {
   int64_t* sums = nullptr;  // [cell][P] (staged Gram for mraid_run)
   float* corr = nullptr;    // [cell][NP]
   size_t cells = 0;
+  float* evals = nullptr;   // [cell][N] when q1 is wanted without eigenvalues
+  size_t evals_cells = 0;
 };
 
 }  // namespace mraid
@@ -72,6 +74,7 @@ struct mraid_plan_s {
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
   mraid::Profiler prof;
+  bool force_dp4a = false;  // use the CUDA-core Gram even where tcgen05 fits
 };
 
 namespace mraid {
@@ -87,12 +90,19 @@ mraid_status cuda_fail(cudaError_t e, const char* what);
 // by cell relative to sub0 (cell = (sub - sub0) * n_chan + chan).
 cudaError_t launch_gram_u8(const mraid_plan_s* pl, const uint8_t* d_data,
                            int sub0, int n_sub, int64_t* d_sums);
+// tensor-core Gram fused with the correlation (gram_tc.cu); either output
+// may be null. cudaErrorNotSupported when the shape or layout does not fit.
+bool gram_tc_supported(const mraid_plan_s* pl, const void* d_data);
+cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int sub0, int n_sub,
+                           int64_t* d_sums, float* d_corr);
 cudaError_t launch_corr_from_sums(const mraid_plan_s* pl, const int64_t* d_sums,
                                   int64_t n_cells, float* d_corr);
 // eig.cu
 cudaError_t launch_eig(const mraid_plan_s* pl, const float* d_corr, int64_t n_cells,
                        float* d_evals, float* d_q1, float* d_stat);
 bool eig_supported(int n_beam);
+// true if a q1 request needs d_evals (the q1 pass reads lambda_1 from it)
+bool eig_q1_needs_evals(int n_beam);
 // flag.cu
 cudaError_t launch_flag(mraid_plan_s* pl, const float* d_stat, uint8_t* d_flags);
 int flag_grid_blocks(int device, int sm_count);

@@ -33,6 +33,7 @@ const char* kernel_name(int id) {
     case K_CORR: return "corr_from_sums";
     case K_EIG: return "eig_jacobi";
     case K_FLAG: return "flag_clip";
+    case K_GRAM_TC: return "gram_tc";
   }
   return "unknown";
 }
@@ -112,6 +113,25 @@ mraid_status ensure_workspace(mraid_plan_s* pl, size_t cells) {
   return MRAID_OK;
 }
 
+// eigenvalue buffer for the q1 pass when the caller wants q1 but not evals
+mraid_status evals_for_q1(mraid_plan_s* pl, size_t cells, float** evals) {
+  if (*evals || !eig_q1_needs_evals(pl->p.n_beam)) return MRAID_OK;
+  if (pl->ws.evals_cells < cells) {
+    cudaFree(pl->ws.evals);
+    pl->ws.evals = nullptr;
+    pl->ws.evals_cells = 0;
+    cudaError_t e = cudaMalloc(&pl->ws.evals, cells * (size_t)pl->p.n_beam * sizeof(float));
+    if (e != cudaSuccess) {
+      pl->ws.evals = nullptr;
+      cudaGetLastError();
+      return cuda_fail(e, "eigenvalue workspace");
+    }
+    pl->ws.evals_cells = cells;
+  }
+  *evals = pl->ws.evals;
+  return MRAID_OK;
+}
+
 mraid_status check_plan(mraid_plan_t pl) {
   if (!pl) {
     set_error("plan is NULL");
@@ -132,6 +152,12 @@ mraid_status check_plan(mraid_plan_t pl) {
 mraid_status ccm_range(mraid_plan_s* pl, const void* d_data, int sub0, int n_sub, int64_t* d_sums,
                        float* d_corr) {
   const int64_t cells = (int64_t)n_sub * pl->p.n_chan;
+  if (!pl->force_dp4a && gram_tc_supported(pl, d_data)) {
+    cudaError_t e = MRAID_PROF(pl, K_GRAM_TC,
+                               launch_gram_tc(pl, static_cast<const uint8_t*>(d_data), sub0, n_sub,
+                                              d_sums, d_corr));
+    return e == cudaSuccess ? MRAID_OK : cuda_fail(e, "gram_tc launch");
+  }
   int64_t* sums = d_sums;
   if (!sums) {
     mraid_status st = ensure_workspace(pl, (size_t)cells);
@@ -316,6 +342,10 @@ mraid_status mraid_eig(mraid_plan_t pl, const float* d_corr, float* d_evals, flo
     set_error("mraid_eig: d_corr and d_stat are required");
     return MRAID_ERR_INVALID_ARG;
   }
+  if (d_q1) {
+    st = evals_for_q1(pl, (size_t)pl->n_cells, &d_evals);
+    if (st != MRAID_OK) return st;
+  }
   cudaError_t e = MRAID_PROF(pl, K_EIG, launch_eig(pl, d_corr, pl->n_cells, d_evals, d_q1, d_stat));
   return e == cudaSuccess ? MRAID_OK : cuda_fail(e, "eig launch");
 }
@@ -345,8 +375,12 @@ mraid_status mraid_run(mraid_plan_t pl, const void* d_data, float* d_evals, floa
   if (st != MRAID_OK) return st;
   cudaError_t e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
   if (e != cudaSuccess) return cuda_fail(e, "memset");
-  st = ccm_range(pl, d_data, 0, pl->p.n_sub, pl->ws.sums, pl->ws.corr);
+  st = ccm_range(pl, d_data, 0, pl->p.n_sub, nullptr, pl->ws.corr);
   if (st != MRAID_OK) return st;
+  if (d_q1) {
+    st = evals_for_q1(pl, (size_t)pl->n_cells, &d_evals);
+    if (st != MRAID_OK) return st;
+  }
   e = MRAID_PROF(pl, K_EIG, launch_eig(pl, pl->ws.corr, pl->n_cells, d_evals, d_q1, d_stat));
   if (e != cudaSuccess) return cuda_fail(e, "eig launch");
   e = MRAID_PROF(pl, K_FLAG, launch_flag(pl, d_stat, d_flags));
@@ -416,7 +450,7 @@ mraid_status mraid_run_host(mraid_plan_t pl, const void* h_data, float* h_stat, 
     pl->beam_stride = (int64_t)chunk * pl->p.n_samp_sub * pl->p.n_chan;
     pl->p.n_sub = ns;
     pl->n_cells = (int64_t)ns * pl->p.n_chan;
-    st = ccm_range(pl, pl->d_chunk[slot], 0, ns, pl->ws.sums, pl->ws.corr);
+    st = ccm_range(pl, pl->d_chunk[slot], 0, ns, nullptr, pl->ws.corr);
     if (st == MRAID_OK) {
       e = MRAID_PROF(pl, K_EIG, launch_eig(pl, pl->ws.corr, pl->n_cells, nullptr, nullptr,
                                            pl->d_stat_full + (int64_t)s0 * pl->p.n_chan));
@@ -447,11 +481,19 @@ mraid_status mraid_sync(mraid_plan_t pl) {
   cudaError_t e = cudaStreamSynchronize(pl->stream);
   if (e != cudaSuccess) return cuda_fail(e, "mraid_sync");
   prof_fold(pl);
+  unsigned dev_err = 0;
+  e = cudaMemcpy(&dev_err, pl->d_error, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "mraid_sync");
+  if (dev_err) {
+    pl->h_info->timed_out = 1;
+    cudaMemset(pl->d_error, 0, sizeof(unsigned));
+  }
   if (pl->pending_info) {
     *pl->pending_info = *pl->h_info;
     pl->pending_info = nullptr;
   }
   if (pl->h_info->timed_out) {
+    pl->h_info->timed_out = 0;
     set_error("a bounded device wait expired");
     return MRAID_ERR_TIMEOUT;
   }
@@ -526,6 +568,7 @@ void mraid_destroy(mraid_plan_t pl) {
   cudaFree(pl->d_flags_full);
   cudaFree(pl->ws.sums);
   cudaFree(pl->ws.corr);
+  cudaFree(pl->ws.evals);
   cudaFree(pl->d_keep);
   cudaFree(pl->d_partials);
   cudaFree(pl->d_info);

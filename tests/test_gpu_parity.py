@@ -84,6 +84,22 @@ def test_shapes_parity(n_beam, n_chan, n_samp_sub, n_sub):
     check_block(data, n_samp_sub, check_flags=n_chan * n_sub >= 16, label=str(cfg))
 
 
+@pytest.mark.parametrize("n_beam,n_chan,n_samp_sub,n_sub", [
+    (19, 32, 1024, 3),   # FAST cell shape on the tensor-core Gram
+    (13, 16, 512, 4),    # 13-beam receiver, one 16-channel box
+    (2, 16, 64, 3),
+    (15, 32, 128, 2),    # beams + ones = 16 rows: one MMA per group
+    (16, 16, 192, 2),    # 17 rows: second MMA begins
+    (23, 16, 64, 3),     # 24 rows: the largest tensor-core shape
+])
+def test_tensor_core_gram_shapes(n_beam, n_chan, n_samp_sub, n_sub):
+    cfg = synth.SynthConfig(n_beam=n_beam, n_chan=n_chan, n_samp_sub=n_samp_sub, n_sub=n_sub,
+                            seed=2000 + n_beam * 7 + n_chan, bandpass=1, n_narrow=1,
+                            n_burst=1, n_spike=1)
+    data = synth.generate(cfg)
+    check_block(data, n_samp_sub, check_flags=n_chan * n_sub >= 32, label=str(cfg))
+
+
 def test_long_subintegration_segments_exact():
     """n_s > 32768 exercises the int32 -> int64 segment flush."""
     rng = np.random.default_rng(5)
