@@ -46,6 +46,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-sub", type=int, default=0,
                     help="shrink the block to this many sub-integrations (profiling runs)")
+    ap.add_argument("--batch-steps", type=int, default=3,
+                    help="timed passes of the batched form (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=3.0,
+                    help="seconds of Poisson arrivals per rate for the served form (0: skip)")
     return ap.parse_args()
 
 
@@ -206,6 +210,130 @@ def cpu_baseline(cfg, h_ptr, seconds):
 
 # ------------------------------------------------------------- main arms
 
+def bench_batched(m, torch, stream, steps):
+    """Four receivers of 5 s each (13/19/36/72 beams) in one graph-captured
+    pass, against the plain form (one mraid_run per block, one after the
+    other on one stream) on the same data."""
+    import synth
+    shapes = synth.BATCH_SHAPES
+    datas = []
+    for cfg in shapes:
+        h = torch.empty(cfg.nbytes, dtype=torch.uint8, pin_memory=True)
+        synth.generate(cfg, out_ptr=h.data_ptr())
+        datas.append(h.to("cuda"))
+        del h
+    cells = sum(c.n_cells for c in shapes)
+    nbytes = sum(c.nbytes for c in shapes)
+    dims = [(c.n_beam, c.n_chan, c.n_samp_sub, c.n_sub) for c in shapes]
+    with torch.cuda.stream(stream):
+        batch = m.Batch(dims, stream=stream)
+        outs = batch.outputs()
+        plans = [m.Plan(*d, stream=stream) for d in dims]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        batch.run(datas, outs, sync=True)
+    e0.record(stream)
+    for _ in range(steps):
+        batch.run(datas, outs, sync=False)
+    e1.record(stream)
+    m.mraid_batch_sync(batch.handle)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / steps
+    infos = [m.FlagInfo() for _ in plans]
+    o2 = [plan._empty(plan.n_cells, dtype=torch.float32) for plan in plans]
+    f2 = [plan._empty(plan.n_cells, dtype=torch.uint8) for plan in plans]
+    for _ in range(2):
+        for plan, d, st, fl, inf in zip(plans, datas, o2, f2, infos):
+            m.mraid_run(plan.handle, d, None, None, st, fl, inf)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        for plan, d, st, fl, inf in zip(plans, datas, o2, f2, infos):
+            m.mraid_run(plan.handle, d, None, None, st, fl, inf)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_p = e0.elapsed_time(e1) / steps
+    inst, upd = batch.graph_stats()
+    for plan in plans:
+        plan.close()
+    batch.close()
+    del datas, outs
+    torch.cuda.empty_cache()
+    return {"workload": "13b/1024ch/512, 19b/4096ch/1024, 36b/2048ch/2048, 72b/1024ch/4096; "
+                        "5 s each, uint8", "cells": cells, "bytes": nbytes,
+            "ms_per_pass": ms_b, "cells_per_s": cells / (ms_b / 1000.0),
+            "plain_ms_per_pass": ms_p, "plain_cells_per_s": cells / (ms_p / 1000.0),
+            "graph_instantiations": inst, "graph_updates": upd,
+            "note": "plain = one mraid_run per block, sequential on one stream; default Gram tiles in both"}
+
+
+def bench_served(m, torch, seconds, rates=(1.0, 2.0, 4.0)):
+    """8 observations (two of each receiver), 1 s blocks arriving as a
+    Poisson process at 1x, 2x and 4x real time in aggregate; latency from
+    submit (block complete in pinned host memory) to flags in host memory."""
+    import numpy as np
+    import synth
+    recv = [(13, 1024, 512, 15625), (19, 4096, 1024, 20345), (36, 2048, 2048, 15625),
+            (72, 1024, 4096, 15625)]   # (beams, channels, N_s, samples per 1 s block)
+    streams = [r for r in recv for _ in range(2)]
+    blocks = []
+    for i, (nb, nc, ns, bs) in enumerate(streams):
+        n_sub = -(-bs // ns)
+        cfg = synth.SynthConfig(n_beam=nb, n_chan=nc, n_samp_sub=ns, n_sub=n_sub, seed=6000 + i,
+                                bandpass=1, n_narrow=max(1, nc // 50), n_burst=0, n_spike=1)
+        full = synth.generate(cfg)
+        h = torch.from_numpy(np.ascontiguousarray(full[:, :bs, :])).pin_memory()
+        blocks.append(h)
+    out = {"streams": "2 x (13b/1024ch/512, 19b/4096ch/1024, 36b/2048ch/2048, 72b/1024ch/4096)",
+           "block_s": 1.0, "rates": {}}
+    rng = np.random.default_rng(77)
+    with m.Server(streams, max_inflight=8) as srv:
+        # warm-up: one block per stream
+        for i in range(len(streams)):
+            srv.submit(i, blocks[i], torch.empty(srv.flags_bytes(i), dtype=torch.uint8).pin_memory(), -1)
+        srv.drain(120000)
+        srv.poll(1024)
+        for rate_x in rates:
+            lam = rate_x * len(streams)   # blocks per second, aggregate
+            n_blocks = max(8, int(lam * seconds))
+            t_arr = np.cumsum(rng.exponential(1.0 / lam, size=n_blocks))
+            keep = []
+            t0 = time.perf_counter()
+            for k, ta in enumerate(t_arr):
+                while time.perf_counter() - t0 < ta:
+                    time.sleep(min(0.0005, max(0.0, ta - (time.perf_counter() - t0))))
+                i = k % len(streams)
+                f = torch.empty(srv.flags_bytes(i), dtype=torch.uint8).pin_memory()
+                keep.append(f)
+                srv.submit(i, blocks[i], f, k)
+            srv.drain(300000)
+            wall = time.perf_counter() - t0
+            res = [r for r in srv.poll(100000) if r["seq"] >= 0]
+            lat = np.array([r["latency_ms"] for r in res])
+            dev = np.array([r["device_ms"] for r in res])
+            cells = sum(r["n_cells"] for r in res)
+            out["rates"][f"{rate_x:g}x"] = {
+                "blocks": len(res), "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "device_p50_ms": float(np.percentile(dev, 50)),
+                "device_p99_ms": float(np.percentile(dev, 99)), "cells_per_s": cells / wall,
+                "offered_blocks_per_s": lam}
+    # plain per-block launch on the same blocks: one block at a time, copy in,
+    # mraid_run_host, flags back
+    plain = []
+    for i, (nb, nc, ns, bs) in enumerate(streams[::2]):
+        n_sub = bs // ns
+        with m.Plan(nb, nc, ns, n_sub, beam_stride=bs * nc) as plan:
+            h = blocks[2 * i]
+            fl = torch.empty(n_sub * nc, dtype=torch.uint8, pin_memory=True)
+            plan.run_host(h, h_flags=fl)
+            t0 = time.perf_counter()
+            for _ in range(3):
+                plan.run_host(h, h_flags=fl)
+            plain.append((time.perf_counter() - t0) / 3 * 1000.0)
+    out["plain_block_ms"] = {f"{s[0]}b": v for s, v in zip(recv, plain)}
+    return out
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -354,6 +482,15 @@ def run_mraid(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg, h.data_ptr(), args.cpu_seconds)
+    plan.close()
+    del d, h
+    torch.cuda.empty_cache()
+    batched = served = None
+    if world == 1 and args.workload == "fast_block" and not args.n_sub:
+        if args.batch_steps > 0:
+            batched = bench_batched(m, torch, stream, args.batch_steps)
+        if args.serve_seconds > 0:
+            served = bench_served(m, torch, args.serve_seconds)
 
     if rank == 0:
         line = {
@@ -373,9 +510,12 @@ def run_mraid(args):
             "cpu_baseline": cpu,
             "mask": {"flagged_fraction": info.n_flagged / cells, "iterations": info.iterations,
                      "threshold": info.thresh, "n_near": info.n_near},
+            "jacobi": {"sweeps_per_cell": info.jacobi_sweeps / cells,
+                       "sweeps_per_warp": info.jacobi_warp_sweeps / max(1, (cells + 31) // 32)},
+            "batched": batched,
+            "served": served,
         }
         print(json.dumps(line), flush=True)
-    plan.close()
     if dist:
         dist.destroy_process_group()
     return 0

@@ -78,6 +78,8 @@ typedef struct {
   int64_t n_used;        /* cells in the final fit */
   int64_t n_near;        /* unpreserved cells with |s - thresh| <= 2e-4 * s */
   int64_t n_degenerate;  /* (beam, cell) pairs with zero variance (mraid_run) */
+  int64_t jacobi_sweeps; /* Jacobi sweeps summed over cells (mraid_run; 0 if not counted) */
+  int64_t jacobi_warp_sweeps; /* sweeps executed, summed over 32-cell warps (mraid_run) */
   int32_t timed_out;     /* 1 if a bounded device wait expired */
   int32_t reserved;
 } mraid_flag_info;
@@ -167,6 +169,118 @@ mraid_status mraid_run(mraid_plan_t plan, const void* d_data, float* d_evals,
  * required. Outputs are valid after mraid_sync. */
 mraid_status mraid_run_host(mraid_plan_t plan, const void* h_data, float* h_stat,
                             uint8_t* h_flags, mraid_flag_info* info);
+
+/* Autotuner (the paper has no counterpart; it picks among this library's
+ * kernel variants). Times every Gram variant that fits the plan's shape on
+ * d_data (tensor-core tiles of 64 samples x 2 stages, 32 x 4 and 32 x 2, and
+ * the CUDA-core Gram), `reps` runs each, and keeps the fastest for this plan.
+ * *choice receives its id (-1 = CUDA-core Gram, 0..2 tensor-core tiles);
+ * report (may be NULL) receives "id:ms;..." for all candidates. Synchronous. */
+mraid_status mraid_autotune(mraid_plan_t plan, const void* d_data, int32_t reps,
+                            int32_t* choice, char* report, int32_t report_len);
+
+/* Select a Gram variant by id (e.g. from a tuning cache): -1 = CUDA-core
+ * Gram, 0..2 tensor-core tiles (ignored where the shape does not fit). */
+mraid_status mraid_set_variant(mraid_plan_t plan, int32_t variant);
+
+/* ------------------------------------------------------------------------
+ * Batched form: blocks of uneven receiver shapes (different N_beam, N_s,
+ * channel counts; e.g. 13-, 19-, 36- and 72-beam systems, Section 5) in one
+ * pass. Cells are independent (Section 3.3), so the units run concurrently
+ * on the GPU; the masking statistics stay per unit (each unit is its own
+ * observation). The pass is captured once into a CUDA graph on the batch's
+ * stream; a later call with different buffers rebinds them through a graph
+ * update instead of a new instantiation.
+ */
+typedef struct mraid_batch_s* mraid_batch_t;
+
+typedef struct {
+  const void* d_data;  /* the unit's samples, layout as for mraid_run */
+  float* d_evals;      /* float32 [cell][N] or NULL */
+  float* d_q1;         /* float32 [cell][N] or NULL */
+  float* d_stat;       /* float32 [cell], required */
+  uint8_t* d_flags;    /* uint8 [cell], required */
+} mraid_unit_io;
+
+/* One plan per unit (params[i], validated as for mraid_plan), all work
+ * buffers allocated here. stream: cudaStream_t of the batch. */
+mraid_status mraid_batch_plan(const mraid_params* params, int32_t n_units, void* stream,
+                              mraid_batch_t* out);
+
+/* Run every unit: io[n_units] buffers, infos[n_units] host structs filled at
+ * mraid_batch_sync (may be NULL). */
+mraid_status mraid_batch_run(mraid_batch_t batch, const mraid_unit_io* io,
+                             mraid_flag_info* infos);
+
+/* Wait for the batch's stream and deliver the per-unit infos. */
+mraid_status mraid_batch_sync(mraid_batch_t batch);
+
+/* Number of graph instantiations and graph updates made so far (a replay
+ * with new buffers is an update, not an instantiation). */
+mraid_status mraid_batch_graph_stats(mraid_batch_t batch, int32_t* instantiations,
+                                     int32_t* updates);
+
+void mraid_batch_destroy(mraid_batch_t batch);
+
+/* ------------------------------------------------------------------------
+ * Served form: continuous batching of blocks from several concurrent
+ * observations (streams) as they arrive. Each observation has its own
+ * receiver shape; its blocks need not hold whole sub-integrations: the
+ * samples left over at the end of a block are kept on the device and
+ * prepended to the next block of that stream, so every cell still spans
+ * N_s consecutive samples (Section 3.2). A server thread admits submitted
+ * blocks while device slots and the HBM budget allow, copies them in on
+ * their stream, runs the path (masking statistics per block, Section 3.3)
+ * and copies the flags out; blocks of different streams overlap on the GPU.
+ * Per-stream state (carry, last flag mask, counters) stays on the device.
+ */
+typedef struct mraid_server_s* mraid_server_t;
+
+typedef struct {
+  mraid_params params;      /* shape of the stream; n_sub is ignored */
+  int32_t block_samples;    /* samples per beam and channel in every block */
+  int32_t reserved;
+} mraid_stream_desc;
+
+typedef struct {
+  int32_t stream;           /* observation index */
+  int32_t n_sub;            /* whole sub-integrations processed for this block */
+  int64_t seq;              /* the caller's sequence number from mraid_serve_submit */
+  int64_t n_cells, n_flagged;
+  double mu, sigma, thresh; /* masking result of this block */
+  double latency_ms;        /* submit -> flags in host memory, host clock */
+  double device_ms;         /* copy-in start -> flags copied out, device events */
+  int32_t status;           /* mraid_status of this block */
+  int32_t reserved;
+} mraid_block_result;
+
+/* Open a server for n_streams observations. hbm_budget: device bytes the
+ * server may hold (0 = 80 % of the free memory at open); max_inflight: blocks
+ * admitted to the GPU at once across streams (>= 1). Buffers of a stream are
+ * allocated when its first block is admitted and only if they fit the
+ * budget; blocks wait in the queue until they do. */
+mraid_status mraid_serve_open(const mraid_stream_desc* streams, int32_t n_streams,
+                              int64_t hbm_budget, int32_t max_inflight, mraid_server_t* out);
+
+/* Queue one block of stream `stream`: h_block is uint8 [beam][block_samples]
+ * [chan] in host memory (pinned for asynchronous copies) and must stay
+ * untouched until its result is polled; h_flags receives uint8 flags of the
+ * block's whole sub-integrations ([n_sub][chan], at most
+ * ceil((block_samples + N_s) / N_s) * n_chan bytes). Non-blocking. */
+mraid_status mraid_serve_submit(mraid_server_t srv, int32_t stream, const void* h_block,
+                                uint8_t* h_flags, int64_t seq);
+
+/* Copy up to max finished blocks into out (FIFO order of completion);
+ * *n receives the count. Non-blocking. */
+mraid_status mraid_serve_poll(mraid_server_t srv, mraid_block_result* out, int32_t max,
+                              int32_t* n);
+
+/* Wait until every submitted block has finished (bounded by timeout_ms;
+ * MRAID_ERR_TIMEOUT when it expires). */
+mraid_status mraid_serve_drain(mraid_server_t srv, int32_t timeout_ms);
+
+/* Stop the server thread and free everything (finishes admitted blocks). */
+void mraid_serve_close(mraid_server_t srv);
 
 /* Wait for the plan's stream, then deliver pending mraid_flag_info. Returns
  * the first device error seen (MRAID_ERR_TIMEOUT, MRAID_ERR_CUDA) or OK. */

@@ -22,7 +22,10 @@ __all__ = [
     "mraid_flag", "mraid_run", "mraid_run_host", "mraid_sync", "mraid_query",
     "mraid_destroy", "mraid_status_string", "mraid_last_error", "mraid_abi_version",
     "mraid_profile_enable", "mraid_profile_read", "mraid_profile_reset", "mraid_ccm_noalloc",
-    "STATUS",
+    "mraid_batch_plan", "mraid_batch_run", "mraid_batch_sync", "mraid_batch_graph_stats",
+    "mraid_batch_destroy", "UnitIO", "Batch", "mraid_serve_open", "mraid_serve_submit",
+    "mraid_serve_poll", "mraid_serve_drain", "mraid_serve_close", "StreamDesc", "BlockResult",
+    "Server", "mraid_autotune", "mraid_set_variant", "tune", "STATUS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -62,8 +65,34 @@ class FlagInfo(ctypes.Structure):
         ("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
         ("n_flagged", ctypes.c_int64), ("n_used", ctypes.c_int64),
         ("n_near", ctypes.c_int64), ("n_degenerate", ctypes.c_int64),
+        ("jacobi_sweeps", ctypes.c_int64), ("jacobi_warp_sweeps", ctypes.c_int64),
         ("timed_out", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class UnitIO(ctypes.Structure):
+    """mraid_unit_io: one unit's device buffers in the batched form."""
+    _fields_ = [("d_data", ctypes.c_void_p), ("d_evals", ctypes.c_void_p),
+                ("d_q1", ctypes.c_void_p), ("d_stat", ctypes.c_void_p),
+                ("d_flags", ctypes.c_void_p)]
+
+
+class StreamDesc(ctypes.Structure):
+    """mraid_stream_desc: one observation of the served form."""
+    _fields_ = [("params", Params), ("block_samples", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class BlockResult(ctypes.Structure):
+    """mraid_block_result: one finished block of the served form."""
+    _fields_ = [("stream", ctypes.c_int32), ("n_sub", ctypes.c_int32), ("seq", ctypes.c_int64),
+                ("n_cells", ctypes.c_int64), ("n_flagged", ctypes.c_int64),
+                ("mu", ctypes.c_double), ("sigma", ctypes.c_double), ("thresh", ctypes.c_double),
+                ("latency_ms", ctypes.c_double), ("device_ms", ctypes.c_double),
+                ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -109,6 +138,20 @@ def load():
                                               ctypes.POINTER(i32)]),
         "mraid_profile_reset": (ctypes.c_int, [vp]),
         "mraid_ccm_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), vp, i32, i32, vp, vp]),
+        "mraid_batch_plan": (ctypes.c_int, [ctypes.POINTER(Params), i32, vp, ctypes.POINTER(vp)]),
+        "mraid_batch_run": (ctypes.c_int, [vp, ctypes.POINTER(UnitIO), ctypes.POINTER(FlagInfo)]),
+        "mraid_batch_sync": (ctypes.c_int, [vp]),
+        "mraid_batch_graph_stats": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "mraid_batch_destroy": (None, [vp]),
+        "mraid_serve_open": (ctypes.c_int, [ctypes.POINTER(StreamDesc), i32, ctypes.c_int64, i32,
+                                            ctypes.POINTER(vp)]),
+        "mraid_serve_submit": (ctypes.c_int, [vp, i32, vp, vp, ctypes.c_int64]),
+        "mraid_serve_poll": (ctypes.c_int, [vp, ctypes.POINTER(BlockResult), i32,
+                                            ctypes.POINTER(i32)]),
+        "mraid_serve_drain": (ctypes.c_int, [vp, i32]),
+        "mraid_serve_close": (None, [vp]),
+        "mraid_autotune": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32), ctypes.c_char_p, i32]),
+        "mraid_set_variant": (ctypes.c_int, [vp, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -227,6 +270,104 @@ def mraid_profile_reset(plan: int):
     _check(load().mraid_profile_reset(plan), "mraid_profile_reset")
 
 
+def mraid_batch_plan(params, stream: int = 0) -> int:
+    arr = (Params * len(params))(*params)
+    out = ctypes.c_void_p()
+    _check(load().mraid_batch_plan(arr, len(params), stream or None, ctypes.byref(out)),
+           "mraid_batch_plan")
+    return out.value
+
+
+def mraid_batch_run(batch: int, ios, infos=None):
+    arr = (UnitIO * len(ios))(*ios)
+    _check(load().mraid_batch_run(batch, arr, infos), "mraid_batch_run")
+
+
+def mraid_batch_sync(batch: int):
+    _check(load().mraid_batch_sync(batch), "mraid_batch_sync")
+
+
+def mraid_batch_graph_stats(batch: int):
+    a, b = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(load().mraid_batch_graph_stats(batch, ctypes.byref(a), ctypes.byref(b)),
+           "mraid_batch_graph_stats")
+    return a.value, b.value
+
+
+def mraid_batch_destroy(batch: int):
+    load().mraid_batch_destroy(batch)
+
+
+def mraid_serve_open(descs, hbm_budget: int = 0, max_inflight: int = 8) -> int:
+    arr = (StreamDesc * len(descs))(*descs)
+    out = ctypes.c_void_p()
+    _check(load().mraid_serve_open(arr, len(descs), hbm_budget, max_inflight, ctypes.byref(out)),
+           "mraid_serve_open")
+    return out.value
+
+
+def mraid_serve_submit(srv: int, stream: int, h_block, h_flags, seq: int):
+    _check(load().mraid_serve_submit(srv, stream, _ptr(h_block), _ptr(h_flags), seq),
+           "mraid_serve_submit")
+
+
+def mraid_serve_poll(srv: int, max_results: int = 256):
+    arr = (BlockResult * max_results)()
+    n = ctypes.c_int32(0)
+    _check(load().mraid_serve_poll(srv, arr, max_results, ctypes.byref(n)), "mraid_serve_poll")
+    return [arr[i].as_dict() for i in range(n.value)]
+
+
+def mraid_serve_drain(srv: int, timeout_ms: int = 60000):
+    _check(load().mraid_serve_drain(srv, timeout_ms), "mraid_serve_drain")
+
+
+def mraid_serve_close(srv: int):
+    load().mraid_serve_close(srv)
+
+
+def mraid_autotune(plan: int, d_data, reps: int = 3):
+    """(chosen variant, {variant: ms}) for the plan's Gram stage."""
+    choice = ctypes.c_int32(0)
+    buf = ctypes.create_string_buffer(512)
+    _check(load().mraid_autotune(plan, _ptr(d_data), reps, ctypes.byref(choice), buf, 512),
+           "mraid_autotune")
+    times = {}
+    for item in buf.value.decode().split(";"):
+        if item:
+            k, v = item.split(":")
+            times[int(k)] = float(v)
+    return choice.value, times
+
+
+def mraid_set_variant(plan: int, variant: int):
+    _check(load().mraid_set_variant(plan, variant), "mraid_set_variant")
+
+
+def tune(plan: int, d_data, n_beam: int, n_chan: int, n_samp_sub: int,
+         cache_path: Optional[str] = None, reps: int = 3) -> int:
+    """Pick the Gram variant for this shape: from the JSON tuning cache
+    (keyed by beams, channels, samples per sub-integration, sample type) if it
+    holds the shape, else by mraid_autotune, recording the result."""
+    import json
+    key = f"{n_beam},{n_chan},{n_samp_sub},u8"
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+    if key in cache:
+        mraid_set_variant(plan, int(cache[key]["variant"]))
+        return int(cache[key]["variant"])
+    choice, times = mraid_autotune(plan, d_data, reps)
+    if cache_path:
+        cache[key] = {"variant": choice, "ms": {str(k): v for k, v in times.items()}}
+        tmp = cache_path + f".{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache_path)
+    return choice
+
+
 # ------------------------------------------------------------ convenience
 
 class Plan:
@@ -326,3 +467,112 @@ class Plan:
 
     def sync(self):
         mraid_sync(self.handle)
+
+
+class Batch:
+    """Batched form over units of uneven shapes (mraid_batch_*); outputs are
+    torch tensors, one set per unit."""
+
+    def __init__(self, shapes, stream=None, eig_k: float = 3.0, max_clip_iter: int = 64):
+        import torch
+        self.torch = torch
+        self.params = []
+        for (n_beam, n_chan, n_samp_sub, n_sub) in shapes:
+            p = mraid_default_params(n_beam, n_chan, n_samp_sub, n_sub)
+            p.eig_k = eig_k
+            p.max_clip_iter = max_clip_iter
+            self.params.append(p)
+        self.shapes = list(shapes)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = mraid_batch_plan(self.params, self.stream.cuda_stream)
+
+    def outputs(self):
+        t = self.torch
+        outs = []
+        for (n_beam, n_chan, _, n_sub) in self.shapes:
+            cells = n_chan * n_sub
+            outs.append({
+                "evals": t.empty(cells, n_beam, dtype=t.float32, device="cuda"),
+                "q1": t.empty(cells, n_beam, dtype=t.float32, device="cuda"),
+                "stat": t.empty(cells, dtype=t.float32, device="cuda"),
+                "flags": t.empty(cells, dtype=t.uint8, device="cuda"),
+            })
+        return outs
+
+    def run(self, datas, outs=None, sync: bool = True):
+        outs = outs if outs is not None else self.outputs()
+        ios = [UnitIO(_ptr(d), _ptr(o["evals"]), _ptr(o["q1"]), _ptr(o["stat"]), _ptr(o["flags"]))
+               for d, o in zip(datas, outs)]
+        infos = (FlagInfo * len(ios))()
+        mraid_batch_run(self.handle, ios, infos)
+        if sync:
+            mraid_batch_sync(self.handle)
+            for o, i in zip(outs, infos):
+                o["info"] = i.as_dict()
+        else:
+            self._infos = infos
+        return outs
+
+    def graph_stats(self):
+        return mraid_batch_graph_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mraid_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Server:
+    """Served form (mraid_serve_*): streams = [(n_beam, n_chan, n_samp_sub,
+    block_samples), ...]."""
+
+    def __init__(self, streams, hbm_budget: int = 0, max_inflight: int = 8, eig_k: float = 3.0):
+        self.descs = []
+        for (n_beam, n_chan, n_samp_sub, block_samples) in streams:
+            p = mraid_default_params(n_beam, n_chan, n_samp_sub, 1)
+            p.eig_k = eig_k
+            self.descs.append(StreamDesc(p, block_samples, 0))
+        self.streams = list(streams)
+        self.handle = mraid_serve_open(self.descs, hbm_budget, max_inflight)
+
+    def flags_bytes(self, stream: int) -> int:
+        n_beam, n_chan, n_s, block = self.streams[stream]
+        return ((block + n_s) // n_s + 1) * n_chan
+
+    def submit(self, stream: int, h_block, h_flags, seq: int):
+        mraid_serve_submit(self.handle, stream, h_block, h_flags, seq)
+
+    def poll(self, max_results: int = 256):
+        return mraid_serve_poll(self.handle, max_results)
+
+    def drain(self, timeout_ms: int = 60000):
+        mraid_serve_drain(self.handle, timeout_ms)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mraid_serve_close(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

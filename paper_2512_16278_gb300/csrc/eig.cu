@@ -40,9 +40,11 @@ __device__ __forceinline__ void static_for(F&& f) {
 
 constexpr int kEigThreads = 64;
 constexpr int kMaxSweeps = 16;
-// Stop when off(A)_F^2 <= kTol2 * ||A||_F^2 (off(A)_F <= 3e-7 ||A||_F);
-// the diagonal then holds the eigenvalues to well below 1e-5 of lambda_max.
-constexpr float kTol2 = 9e-14f;
+// Stop when off(A)_F^2 <= kTol2 * ||A||_F^2, i.e. off(A)_F <= 1e-5 ||A||_F.
+// By Weyl's inequality every diagonal entry is then within off(A)_F of an
+// eigenvalue: <= 1e-5 sqrt(N) lambda_max, inside the 1e-4 lambda_max bound
+// (the actual error is second order in off(A) and far smaller).
+constexpr float kTol2 = 1e-10f;
 
 template <int N>
 struct Slots {
@@ -51,6 +53,10 @@ struct Slots {
   static constexpr int H = M / 2;             // pair slots (2i, 2i+1)
   static constexpr int S0 = kOdd ? 1 : 0;     // first stored slot
   static constexpr int NP = N * (N + 1) / 2;
+  // per-thread shared-memory row: the staged packed matrix, later the two
+  // ping-pong scale vectors of M floats each; odd for conflict-free rows
+  static constexpr int STR = ((NP > 2 * M) ? NP : 2 * M) | 1;
+  static_assert(STR >= NP && STR >= 2 * M, "row too short");
   // packed upper triangle over stored slots (slot s holds beam s - S0 at start)
   __host__ __device__ static constexpr int idx(int k, int l) {
     return (k <= l) ? ((k - S0) * N - (k - S0) * (k - S0 - 1) / 2 + (l - k))
@@ -100,6 +106,17 @@ struct Slots {
   }
 };
 
+// Explicit shared-memory accesses (32-bit shared addresses), so the scale
+// vectors never go through generic addressing.
+__device__ __forceinline__ float lds(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void sts(uint32_t addr, float v) {
+  asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
 __device__ __forceinline__ void rotation(float app, float aqq, float apq, float& c, float& s,
                                          float& t) {
   // t = tan(theta) of the rotation zeroing apq (smaller root of
@@ -114,47 +131,74 @@ __device__ __forceinline__ void rotation(float app, float aqq, float apq, float&
   s = t * c;
 }
 
+// One round of the scaled ("fast") two-sided Jacobi. The matrix is held as
+// A = D A~ D with D = diag(d) per slot. For the pair (p, q) with rotation
+// J (J_pp = J_qq = c, J_pq = s = t c, J_qp = -s) one has
+// J^T D = D' M, D' = c D on p and q, M = [[1, alpha], [beta, 1]] with
+// alpha = -t w, beta = t / w, w = d_q / d_p; so A~' = M A~ M^T, which costs
+// one FMA per element and side instead of two multiplies and an add.
+// The rotated pairs are the slots (2i, 2i+1); the results are written into
+// circularly permuted slots (sigma), scales included.
 template <int N>
-__device__ __forceinline__ void jacobi_round(float (&a)[Slots<N>::NP]) {
+__device__ __forceinline__ void jacobi_round(float (&a)[Slots<N>::NP], uint32_t dsrc,
+                                             uint32_t ddst) {
   using S = Slots<N>;
-  float c[S::H], s[S::H], t[S::H];
-  static_for<S::H>([&](auto ii) {
-    constexpr int i = decltype(ii)::value;
-    if constexpr (i >= S::S0)
-      rotation(a[S::idx(2 * i, 2 * i)], a[S::idx(2 * i + 1, 2 * i + 1)],
-               a[S::idx(2 * i, 2 * i + 1)], c[i], s[i], t[i]);
-  });
-  float b[S::NP];
-  // diagonal 2x2 blocks: the rotated pair
+  float al[S::H], be[S::H];
   static_for<S::H>([&](auto ii) {
     constexpr int i = decltype(ii)::value;
     if constexpr (i >= S::S0) {
       constexpr int p = 2 * i, q = 2 * i + 1;
-      const float apq = a[S::idx(p, q)];
-      b[S::idx(S::sigma(p), S::sigma(p))] = fmaf(-t[i], apq, a[S::idx(p, p)]);
-      b[S::idx(S::sigma(q), S::sigma(q))] = fmaf(t[i], apq, a[S::idx(q, q)]);
+      // tan(theta) from the true entries, scaled by 1 / (d_p d_q):
+      // a_pp / (d_p d_q) = a~_pp / w, a_qq / (d_p d_q) = w a~_qq
+      const float dp = lds(dsrc + 4 * p), dq = lds(dsrc + 4 * q);
+      const float w = __fdividef(dq, dp), iw = __fdividef(dp, dq);
+      const float app = a[S::idx(p, p)], aqq = a[S::idx(q, q)], apq = a[S::idx(p, q)];
+      const float dd = fmaf(w, aqq, -iw * app);
+      const float h2 = 2.f * apq;
+      const float r2 = fmaf(dd, dd, h2 * h2);
+      const float den = fmaxf(fabsf(dd) + r2 * rsqrtf(fmaxf(r2, 1e-37f)), 1e-30f);
+      const float t = __fdividef(dd >= 0.f ? h2 : -h2, den);
+      const float u = fmaf(t, t, 1.f);
+      const float c = rsqrtf(u);
+      al[i] = -t * w;
+      be[i] = t * iw;
+      sts(ddst + 4 * S::sigma(p), dp * c);  // scales move with their slots
+      sts(ddst + 4 * S::sigma(q), dq * c);
+    }
+  });
+  if constexpr (S::kOdd) sts(ddst + 4 * S::sigma(1), lds(dsrc + 4));  // idle slot keeps its scale
+  float b[S::NP];
+  // diagonal 2x2 blocks: A~' = M A~ M^T, off-diagonal entry annihilated
+  static_for<S::H>([&](auto ii) {
+    constexpr int i = decltype(ii)::value;
+    if constexpr (i >= S::S0) {
+      constexpr int p = 2 * i, q = 2 * i + 1;
+      const float app = a[S::idx(p, p)], aqq = a[S::idx(q, q)], apq = a[S::idx(p, q)];
+      const float h2 = 2.f * apq;
+      b[S::idx(S::sigma(p), S::sigma(p))] = fmaf(al[i], fmaf(al[i], aqq, h2), app);
+      b[S::idx(S::sigma(q), S::sigma(q))] = fmaf(be[i], fmaf(be[i], app, h2), aqq);
       b[S::idx(S::sigma(p), S::sigma(q))] = 0.f;
     }
   });
   if constexpr (S::kOdd) b[S::idx(S::sigma(1), S::sigma(1))] = a[S::idx(1, 1)];  // idle slot
-  // off-diagonal blocks (i < j): B' = J_i^T B J_j
+  // off-diagonal blocks (i < j): B~' = M_i B~ M_j^T
   static_for<S::NB>([&](auto ee) {
     constexpr int i = S::blk_i(decltype(ee)::value), j = S::blk_j(decltype(ee)::value);
     constexpr int pi = 2 * i, qi = 2 * i + 1, pj = 2 * j, qj = 2 * j + 1;
     if constexpr (S::kOdd && i == 0) {
-      // slot 0 is the dummy; slot 1 is idle this round: right rotation only
+      // slot 0 is the dummy; slot 1 is idle this round: right factor only
       const float y0 = a[S::idx(qi, pj)], y1 = a[S::idx(qi, qj)];
-      b[S::idx(S::sigma(qi), S::sigma(pj))] = c[j] * y0 - s[j] * y1;
-      b[S::idx(S::sigma(qi), S::sigma(qj))] = fmaf(s[j], y0, c[j] * y1);
+      b[S::idx(S::sigma(qi), S::sigma(pj))] = fmaf(al[j], y1, y0);
+      b[S::idx(S::sigma(qi), S::sigma(qj))] = fmaf(be[j], y0, y1);
     } else {
       const float x00 = a[S::idx(pi, pj)], x01 = a[S::idx(pi, qj)];
       const float x10 = a[S::idx(qi, pj)], x11 = a[S::idx(qi, qj)];
-      const float l00 = c[i] * x00 - s[i] * x10, l01 = c[i] * x01 - s[i] * x11;
-      const float l10 = fmaf(s[i], x00, c[i] * x10), l11 = fmaf(s[i], x01, c[i] * x11);
-      b[S::idx(S::sigma(pi), S::sigma(pj))] = c[j] * l00 - s[j] * l01;
-      b[S::idx(S::sigma(pi), S::sigma(qj))] = fmaf(s[j], l00, c[j] * l01);
-      b[S::idx(S::sigma(qi), S::sigma(pj))] = c[j] * l10 - s[j] * l11;
-      b[S::idx(S::sigma(qi), S::sigma(qj))] = fmaf(s[j], l10, c[j] * l11);
+      const float l00 = fmaf(al[i], x10, x00), l01 = fmaf(al[i], x11, x01);
+      const float l10 = fmaf(be[i], x00, x10), l11 = fmaf(be[i], x01, x11);
+      b[S::idx(S::sigma(pi), S::sigma(pj))] = fmaf(al[j], l01, l00);
+      b[S::idx(S::sigma(pi), S::sigma(qj))] = fmaf(be[j], l00, l01);
+      b[S::idx(S::sigma(qi), S::sigma(pj))] = fmaf(al[j], l11, l10);
+      b[S::idx(S::sigma(qi), S::sigma(qj))] = fmaf(be[j], l10, l11);
     }
   });
   static_for<S::NP>([&](auto ee) { a[decltype(ee)::value] = b[decltype(ee)::value]; });
@@ -232,10 +276,10 @@ __device__ bool dominant_vector(const float* r, float lambda1, float (&x)[N]) {
 template <int N>
 __global__ void __launch_bounds__(kEigThreads)
 eig_reg_kernel(const float* __restrict__ corr, int64_t n_cells, float* __restrict__ evals,
-               float* __restrict__ stat) {
+               float* __restrict__ stat, unsigned long long* __restrict__ sweep_count) {
   using S = Slots<N>;
   constexpr int NP = S::NP;
-  constexpr int STR = NP | 1;  // odd stride: conflict-free per-thread rows
+  constexpr int STR = S::STR;
   extern __shared__ float sm[];
   const int64_t cell0 = (int64_t)blockIdx.x * kEigThreads;
   const int ncell = (int)min((int64_t)kEigThreads, n_cells - cell0);
@@ -255,16 +299,41 @@ eig_reg_kernel(const float* __restrict__ corr, int64_t n_cells, float* __restric
   });
 
   bool conv = !active;
+  int sweeps = 0;
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
     if (!__any_sync(0xffffffffu, !conv)) break;
-    for (int r = 0; r < S::M - 1; ++r) jacobi_round<N>(a);
+    // scales live in this thread's (now free) staging row of shared memory,
+    // ping-ponged between two halves so a round reads the old ones
+    const uint32_t d0 = static_cast<uint32_t>(__cvta_generic_to_shared(sm + threadIdx.x * STR));
+    const uint32_t d1 = d0 + 4 * S::M;
+    static_for<S::M>([&](auto kk) { sts(d0 + 4 * decltype(kk)::value, 1.f); });
+    // two rounds per iteration: the scheduler can overlap the next round's
+    // rotation chains with this round's block updates
+#pragma unroll 2
+    for (int r = 0; r < S::M - 1; ++r) jacobi_round<N>(a, (r & 1) ? d1 : d0, (r & 1) ? d0 : d1);
+    const uint32_t dl = ((S::M - 1) & 1) ? d1 : d0;
+    float d[S::M];
+    static_for<S::M>([&](auto kk) { d[decltype(kk)::value] = lds(dl + 4 * decltype(kk)::value); });
+    // back to true entries (a_kl = d_k a~_kl d_l), then the convergence test
     float off = 0.f, dia = 0.f;
     static_for<NP>([&](auto ee) {
       constexpr int e = decltype(ee)::value;
-      if constexpr (S::row_of(e) == S::col_of(e)) dia = fmaf(a[e], a[e], dia);
+      constexpr int k = S::row_of(e) + S::S0, l = S::col_of(e) + S::S0;
+      a[e] *= d[k] * d[l];
+      if constexpr (k == l) dia = fmaf(a[e], a[e], dia);
       else off = fmaf(a[e], a[e], off);
     });
+    if (!conv) ++sweeps;
     conv = conv || (off <= kTol2 * fmaf(2.f, off, dia));
+  }
+  if (sweep_count) {
+    // executed sweeps of this warp (its slowest cell) and sweeps per cell
+    const int wmax = __reduce_max_sync(0xffffffffu, sweeps);
+    const unsigned wsum = __reduce_add_sync(0xffffffffu, (unsigned)sweeps);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&sweep_count[0], (unsigned long long)wsum);
+      atomicAdd(&sweep_count[1], (unsigned long long)wmax);
+    }
   }
   float ev[N];
   static_for<N>([&](auto kk) {
@@ -296,7 +365,7 @@ __global__ void __launch_bounds__(kEigThreads)
 q1_reg_kernel(const float* __restrict__ corr, int64_t n_cells, const float* __restrict__ evals,
               float* __restrict__ q1) {
   constexpr int NP = Slots<N>::NP;
-  constexpr int STR = NP | 1;
+  constexpr int STR = Slots<N>::STR;
   extern __shared__ float sm[];
   const int64_t cell0 = (int64_t)blockIdx.x * kEigThreads;
   const int ncell = (int)min((int64_t)kEigThreads, n_cells - cell0);
@@ -505,8 +574,8 @@ eig_block_kernel(const float* __restrict__ corr, int64_t n_cells, int N, float* 
 
 template <int N>
 cudaError_t launch_reg(const float* d_corr, int64_t n_cells, float* d_evals, float* d_q1,
-                       float* d_stat, cudaStream_t stream) {
-  constexpr int STR = Slots<N>::NP | 1;
+                       float* d_stat, unsigned long long* sweep_count, cudaStream_t stream) {
+  constexpr int STR = Slots<N>::STR;
   const size_t smem = (size_t)kEigThreads * STR * sizeof(float);
   const int64_t blocks = (n_cells + kEigThreads - 1) / kEigThreads;
   cudaError_t e = cudaFuncSetAttribute(eig_reg_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -514,7 +583,7 @@ cudaError_t launch_reg(const float* d_corr, int64_t n_cells, float* d_evals, flo
   if (e != cudaSuccess) return e;
   if (blocks > 0)
     eig_reg_kernel<N><<<(unsigned)blocks, kEigThreads, smem, stream>>>(d_corr, n_cells, d_evals,
-                                                                          d_stat);
+                                                                          d_stat, sweep_count);
   if (d_q1) {
     e = cudaFuncSetAttribute(q1_reg_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -537,11 +606,11 @@ cudaError_t launch_eig(const mraid_plan_s* pl, const float* d_corr, int64_t n_ce
                        float* d_q1, float* d_stat) {
   const int N = pl->p.n_beam;
   switch (N) {
-    case 2: return launch_reg<2>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->stream);
-    case 3: return launch_reg<3>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->stream);
-    case 4: return launch_reg<4>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->stream);
-    case 13: return launch_reg<13>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->stream);
-    case 19: return launch_reg<19>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->stream);
+    case 2: return launch_reg<2>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->d_sweeps, pl->stream);
+    case 3: return launch_reg<3>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->d_sweeps, pl->stream);
+    case 4: return launch_reg<4>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->d_sweeps, pl->stream);
+    case 13: return launch_reg<13>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->d_sweeps, pl->stream);
+    case 19: return launch_reg<19>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->d_sweeps, pl->stream);
     default: break;
   }
   const int ld = N + 1;

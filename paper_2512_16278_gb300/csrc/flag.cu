@@ -21,7 +21,7 @@ namespace cg = cooperative_groups;
 namespace mraid {
 namespace {
 
-constexpr int kFlagThreads = 256;
+constexpr int kFlagThreads = 512;
 
 struct FlagArgs {
   const float* stat;
@@ -58,9 +58,41 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c, doub
   }
 }
 
+// Sum of the per-block partials [nb][3] in a fixed order: lane l takes
+// blocks l, l+32, ... sequentially, then a fixed shuffle tree; every block
+// computes the same bits. Result broadcast through shared memory.
+__device__ __forceinline__ void grid_total3(const double* part, int nb, double* bcast, double& a,
+                                            double& b, double& c) {
+  if (threadIdx.x < 32) {
+    double x = 0.0, y = 0.0, z = 0.0;
+    for (int i = threadIdx.x; i < nb; i += 32) {
+      x += part[3 * i];
+      y += part[3 * i + 1];
+      z += part[3 * i + 2];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_xor_sync(0xffffffffu, x, o);
+      y += __shfl_xor_sync(0xffffffffu, y, o);
+      z += __shfl_xor_sync(0xffffffffu, z, o);
+    }
+    if (threadIdx.x == 0) {
+      bcast[0] = x;
+      bcast[1] = y;
+      bcast[2] = z;
+    }
+  }
+  __syncthreads();
+  a = bcast[0];
+  b = bcast[1];
+  c = bcast[2];
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(kFlagThreads) flag_kernel(FlagArgs f) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double red[3 * (kFlagThreads / 32)];
+  __shared__ double bcast[3];
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = tid; i < f.n_cells; i += nthr) f.flags[i] = 0;
@@ -71,7 +103,7 @@ __global__ void __launch_bounds__(kFlagThreads) flag_kernel(FlagArgs f) {
   for (int pass = 0;; ++pass) {
     double cnt = 0.0, s1 = 0.0, s2 = 0.0;
     for (int64_t i = tid; i < f.n_cells; i += nthr) {
-      if (f.keep && f.keep[i % f.n_chan]) continue;
+      if (f.keep && f.keep[(uint32_t)i % (uint32_t)f.n_chan]) continue;
       const double v = (double)f.stat[i];
       uint8_t m = f.flags[i];
       if (!m && v > thresh) {
@@ -92,12 +124,7 @@ __global__ void __launch_bounds__(kFlagThreads) flag_kernel(FlagArgs f) {
       part[3 * blockIdx.x + 2] = s2;
     }
     grid.sync();
-    cnt = s1 = s2 = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) {  // same order in every block
-      cnt += part[3 * b];
-      s1 += part[3 * b + 1];
-      s2 += part[3 * b + 2];
-    }
+    grid_total3(part, gridDim.x, bcast, cnt, s1, s2);
     if (pass >= 1 && cnt == prev_count) {  // the last threshold masked nothing
       converged = 1;
       break;
@@ -122,7 +149,7 @@ __global__ void __launch_bounds__(kFlagThreads) flag_kernel(FlagArgs f) {
   double nflag = 0.0, nnear = 0.0, dummy = 0.0;
   for (int64_t i = tid; i < f.n_cells; i += nthr) {
     nflag += f.flags[i];
-    if (f.keep && f.keep[i % f.n_chan]) continue;
+    if (f.keep && f.keep[(uint32_t)i % (uint32_t)f.n_chan]) continue;
     const double v = (double)f.stat[i];
     if (fabs(v - thresh) <= 2e-4 * v) nnear += 1.0;
   }
@@ -132,14 +159,15 @@ __global__ void __launch_bounds__(kFlagThreads) flag_kernel(FlagArgs f) {
   if (threadIdx.x == 0) {
     part[3 * blockIdx.x] = nflag;
     part[3 * blockIdx.x + 1] = nnear;
+    part[3 * blockIdx.x + 2] = 0.0;
   }
   grid.sync();
+  if (blockIdx.x == 0) {
+    double tf = 0.0, tn = 0.0, unused = 0.0;
+    grid_total3(part, gridDim.x, bcast, tf, tn, unused);
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    double tf = 0.0, tn = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) {
-      tf += part[3 * b];
-      tn += part[3 * b + 1];
-    }
+    const double tf = bcast[0], tn = bcast[1];
     mraid_flag_info* o = f.info;
     o->mu = mu;
     o->sigma = sigma;
@@ -149,7 +177,6 @@ __global__ void __launch_bounds__(kFlagThreads) flag_kernel(FlagArgs f) {
     o->n_flagged = (int64_t)tf;
     o->n_used = (int64_t)used;
     o->n_near = (int64_t)tn;
-    o->timed_out = 0;
   }
 }
 
@@ -162,7 +189,7 @@ int flag_grid_blocks(int device, int sm_count) {
       per_sm < 1)
     return 0;
   (void)device;
-  return sm_count * (per_sm < 2 ? per_sm : 2);
+  return sm_count;  // one block per SM: fewer partials to combine
 }
 
 cudaError_t launch_flag(mraid_plan_s* pl, const float* d_stat, uint8_t* d_flags) {
@@ -176,9 +203,19 @@ cudaError_t launch_flag(mraid_plan_s* pl, const float* d_stat, uint8_t* d_flags)
   f.flags = d_flags;
   f.partials = pl->d_partials;
   f.info = pl->d_info;
-  void* args[] = {&f};
-  return cudaLaunchCooperativeKernel((const void*)flag_kernel, dim3(pl->flag_blocks),
-                                    dim3(kFlagThreads), args, 0, pl->stream);
+  // cooperative launch (all blocks co-resident for the grid barrier), in the
+  // form that stream capture accepts
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(pl->flag_blocks);
+  cfg.blockDim = dim3(kFlagThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = pl->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, flag_kernel, f);
 }
 
 }  // namespace mraid

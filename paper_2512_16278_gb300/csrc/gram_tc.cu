@@ -12,8 +12,9 @@
 // S_ab = G_ab + 128 (G_a + G_b) + 128^2 n and S_a = G_a + 128 n.
 //
 // Data flow per persistent CTA (one per SM), warp-specialised:
-//   warp 0    TMA: box {16 channels, 64 samples, N beams} of u8 into a
-//             4-deep ring (cp.async.bulk.tensor, mbarrier transaction count);
+//   warp 0    TMA: box {16 channels, 32 samples, N beams} of u8 into a ring
+//             as deep as shared memory allows (cp.async.bulk.tensor, mbarrier
+//             transaction count), so streaming continues through epilogues;
 //   warps 4-7 convert each box to centred f16 operand tiles in the
 //             MN-major canonical layout (8 channels x 8 samples per core
 //             matrix), one tile per 8-channel group, into a 2-deep ring;
@@ -37,15 +38,23 @@
 namespace mraid {
 namespace {
 
-constexpr int kT = 64;                 // samples per stage
 constexpr int kBoxCh = 16;             // channels per TMA box (16 bytes)
 constexpr int kGroupSlots = 24;        // slots laid out per 8-channel group
 constexpr int kSlack = 8;              // slots after group 1 (A2 rows 24..31)
-constexpr int kSlotBytes = kT * 16;    // one slot: kT samples x 8 channels x f16
-constexpr int kGroupBytes = kGroupSlots * kSlotBytes;
-constexpr int kF16StageBytes = (2 * kGroupSlots + kSlack) * kSlotBytes;
-constexpr int kNU = 4;                 // u8 ring depth
-constexpr int kNF = 2;                 // f16 ring depth
+constexpr int kMaxNU = 16;             // u8 ring depth bound (sized at launch)
+constexpr int kMaxNF = 4;              // f16 ring depth bound
+constexpr size_t kSmemBudget = 227 * 1024;
+
+// Tile shape of one kernel variant: T samples per stage, NF f16 stages.
+template <int T_, int NF_>
+struct TcCfg {
+  static constexpr int kT = T_;
+  static constexpr int kNF = NF_;
+  static constexpr int kSlotBytes = kT * 16;  // one slot: kT samples x 8 channels x f16
+  static constexpr int kGroupBytes = kGroupSlots * kSlotBytes;
+  static constexpr int kF16StageBytes = (2 * kGroupSlots + kSlack) * kSlotBytes;
+  static_assert(kT % 16 == 0 && NF_ <= kMaxNF, "bad variant");
+};
 constexpr int kThreads = 384;
 constexpr int kConvThreads = 128;
 constexpr int kEpiThreads = 128;
@@ -180,25 +189,41 @@ __device__ __forceinline__ void pick4(const uint32_t (&v)[32], int c, float* out
 }
 
 struct Smem {
-  uint64_t u8_full[kNU], u8_empty[kNU];
-  uint64_t f16_full[kNF], f16_empty[kNF];
+  uint64_t u8_full[kMaxNU], u8_empty[kMaxNU];
+  uint64_t f16_full[kMaxNF], f16_empty[kMaxNF];
   uint64_t acc_full, acc_empty, drain;
   uint32_t tmem_base;
   int32_t s_sum[2][8][kGroupSlots];   // centred row sums G_a per group/channel/slot
   float s_inv[2][8][kGroupSlots];     // 1/sqrt(var_a), 0 if var_a == 0
 };
 
+// u8 ring depth for n_beam beams: as deep as the shared memory allows, so
+// TMA keeps streaming while the MMAs pause for an epilogue
+template <class C>
+__host__ __device__ constexpr int u8_ring_depth(int n_beam) {
+  return (int)((kSmemBudget - 1024 - (size_t)C::kNF * C::kF16StageBytes - sizeof(Smem)) /
+               ((size_t)n_beam * C::kT * kBoxCh)) < kMaxNU
+             ? (int)((kSmemBudget - 1024 - (size_t)C::kNF * C::kF16StageBytes - sizeof(Smem)) /
+                     ((size_t)n_beam * C::kT * kBoxCh))
+             : kMaxNU;
+}
 // dynamic shared memory for n_beam beams: f16 ring, u8 ring, barriers
+template <class C>
 __host__ __device__ constexpr size_t smem_bytes(int n_beam) {
-  return 1024 /* alignment slack */ + (size_t)kNF * kF16StageBytes +
-         (size_t)kNU * n_beam * kT * kBoxCh + sizeof(Smem);
+  return 1024 /* alignment slack */ + (size_t)C::kNF * C::kF16StageBytes +
+         (size_t)u8_ring_depth<C>(n_beam) * n_beam * C::kT * kBoxCh + sizeof(Smem);
 }
 
+template <int T_, int NF_>
 __global__ void __launch_bounds__(kThreads, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
+  using C = TcCfg<T_, NF_>;
+  constexpr int kT = C::kT, kNF = C::kNF, kSlotBytes = C::kSlotBytes;
+  constexpr int kGroupBytes = C::kGroupBytes, kF16StageBytes = C::kF16StageBytes;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int kNU = u8_ring_depth<C>(g.n_beam);
   unsigned char* f16 = base;                                   // kNF stages
   unsigned char* u8 = f16 + (size_t)kNF * kF16StageBytes;      // kNU stages
   const int u8_stage_bytes = g.n_beam * kT * kBoxCh;
@@ -352,7 +377,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
     }
   } else if (warp >= 8) {
     // ------------------------------------------------------------ epilogue
-    const int q = warp - 8;              // TMEM lane quarter
+    const int q = warp - 8;              // TMEM lane quarter (warp % 4)
     const int c = lane % 8;              // channel within the group
     const int slot = 4 * q + lane / 8;   // D1 row slot (beam a, 0..15)
     const int slot2 = 16 + 4 * q + lane / 8;  // D2 row slot (TMEM lane 32q + lane)
@@ -367,36 +392,60 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
       float row2[2][8];            // D2 row `slot2`: G[slot2][16..16+r2)
 #pragma unroll
       for (int grp = 0; grp < 2; ++grp) {
+        // D1 row: chunks of 4 slots, two loads in flight per wait
 #pragma unroll
-        for (int ch = 0; ch < kGroupSlots / 4; ++ch) {
+        for (int ch = 0; ch < kGroupSlots / 4; ch += 2) {
           if (ch * 4 < g.rb) {
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + grp * 256 + ch * 32, v);
+            uint32_t v[32], w[32];
+            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + grp * 256 + ch * 32;
+            tmem_ld32(ta, v);
+            if ((ch + 1) * 4 < g.rb) tmem_ld32(ta + 32, w);
             tmem_wait_ld();
             pick4(v, c, &row[grp][4 * ch]);
+            if ((ch + 1) * 4 < g.rb) pick4(w, c, &row[grp][4 * ch + 4]);
           }
         }
         if (g.r2 > 0) {
-          uint32_t v[32];
-          tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + grp * 256 + 192, v);
+          uint32_t v[32], w[32];
+          const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + grp * 256 + 192;
+          tmem_ld32(ta, v);
+          if (g.r2 > 4) tmem_ld32(ta + 32, w);
           tmem_wait_ld();
           pick4(v, c, &row2[grp][0]);
-          uint32_t v2[32];
-          tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + grp * 256 + 224, v2);
-          tmem_wait_ld();
-          pick4(v2, c, &row2[grp][4]);
+          if (g.r2 > 4) pick4(w, c, &row2[grp][4]);
+          else {
+#pragma unroll
+            for (int u = 4; u < 8; ++u) row2[grp][u] = 0.f;
+          }
         }
       }
       fence_before();
       mbar_arrive(&s->acc_empty);  // accumulators may be overwritten now
+      // entries at runtime positions, fetched with compile-time indices:
+      // G[a][N] (row sum) and G[a][a] for the D1 row and the D2 row
+      float sumN[2], diag[2], sumN2[2], diag2[2];
+#pragma unroll
+      for (int grp = 0; grp < 2; ++grp) {
+        sumN[grp] = diag[grp] = sumN2[grp] = diag2[grp] = 0.f;
+#pragma unroll
+        for (int b = 0; b < kGroupSlots; ++b) {
+          if (b == N) sumN[grp] = row[grp][b];
+          if (b == slot) diag[grp] = row[grp][b];
+        }
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          if (b == N - 16) sumN2[grp] = row2[grp][b];
+          if (b == slot2 - 16) diag2[grp] = row2[grp][b];
+        }
+      }
 
       const int k = (int)(it / chunks), ch0 = (int)(it % chunks) * kBoxCh;
       // row sums and inverse standard deviations, shared through smem
 #pragma unroll
       for (int grp = 0; grp < 2; ++grp) {
         if (slot < N + 1) {
-          const int64_t sa = (int64_t)row[grp][N];
-          const int64_t var = n * (int64_t)row[grp][slot] - sa * sa;
+          const int64_t sa = (int64_t)sumN[grp];
+          const int64_t var = n * (int64_t)diag[grp] - sa * sa;
           s->s_sum[grp][c][slot] = (int32_t)sa;
           float inv = 0.f;
           if (slot < N) {
@@ -411,8 +460,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
           s->s_inv[grp][c][slot] = inv;
         }
         if (g.r2 > 0 && slot2 < N + 1) {
-          const int64_t sa = (int64_t)row2[grp][N - 16];
-          const int64_t var = n * (int64_t)row2[grp][slot2 - 16] - sa * sa;
+          const int64_t sa = (int64_t)sumN2[grp];
+          const int64_t var = n * (int64_t)diag2[grp] - sa * sa;
           s->s_sum[grp][c][slot2] = (int32_t)sa;
           float inv = 0.f;
           if (slot2 < N) {
@@ -501,6 +550,14 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
+}  // namespace
+
+// Stage length (samples) of tensor-core Gram variant v: 0 = {64 samples,
+// 2 f16 stages}, 1 = {32, 4}, 2 = {32, 2}.
+int tc_variant_samples(int v) { return (v == 1 || v == 2) ? 32 : 64; }
+
+namespace {
+
 int tc_swap_ls() {
   static int v = -1;
   if (v < 0) {
@@ -514,8 +571,9 @@ int tc_swap_ls() {
 
 bool gram_tc_supported(const mraid_plan_s* pl, const void* d_data) {
   const mraid_params& p = pl->p;
+  const int t = tc_variant_samples(pl->tc_variant);
   return p.bit_depth == 8 && p.n_beam >= 2 && p.n_beam + 1 <= kGroupSlots &&
-         p.n_samp_sub % kT == 0 && p.n_samp_sub <= 1024 && p.n_chan % kBoxCh == 0 &&
+         p.n_samp_sub % t == 0 && p.n_samp_sub <= 1024 && p.n_chan % kBoxCh == 0 &&
          pl->beam_stride % 16 == 0 && (reinterpret_cast<uintptr_t>(d_data) & 15) == 0 &&
          encode_fn() != nullptr;
 }
@@ -528,7 +586,8 @@ cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int su
   const cuuint64_t n_time = (cuuint64_t)(sub0 + n_sub) * p.n_samp_sub;
   cuuint64_t dims[3] = {(cuuint64_t)p.n_chan, n_time, (cuuint64_t)p.n_beam};
   cuuint64_t strides[2] = {(cuuint64_t)p.n_chan, (cuuint64_t)pl->beam_stride};
-  cuuint32_t box[3] = {(cuuint32_t)kBoxCh, (cuuint32_t)kT, (cuuint32_t)p.n_beam};
+  const int t = tc_variant_samples(pl->tc_variant);
+  cuuint32_t box[3] = {(cuuint32_t)kBoxCh, (cuuint32_t)t, (cuuint32_t)p.n_beam};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t*>(d_data),
                            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -549,13 +608,24 @@ cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int su
   a.corr = d_corr;
   a.degenerate = pl->d_degenerate;
   a.error = pl->d_error;
-  const size_t smem = smem_bytes(p.n_beam);
-  cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
   const int64_t items = (int64_t)n_sub * (p.n_chan / kBoxCh);
   const int grid = (int)(items < pl->sm_count ? items : pl->sm_count);
-  if (grid > 0) gram_tc_kernel<<<grid, kThreads, smem, pl->stream>>>(map, a);
+  cudaError_t e = cudaSuccess;
+#define MRAID_TC_LAUNCH(T, NF)                                                                   \
+  do {                                                                                           \
+    const size_t smem = smem_bytes<TcCfg<T, NF>>(p.n_beam);                                      \
+    e = cudaFuncSetAttribute(gram_tc_kernel<T, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)smem);                                                         \
+    if (e == cudaSuccess && grid > 0)                                                            \
+      gram_tc_kernel<T, NF><<<grid, kThreads, smem, pl->stream>>>(map, a);                       \
+  } while (0)
+  switch (pl->tc_variant) {
+    case 1: MRAID_TC_LAUNCH(32, 4); break;
+    case 2: MRAID_TC_LAUNCH(32, 2); break;
+    default: MRAID_TC_LAUNCH(64, 2); break;
+  }
+#undef MRAID_TC_LAUNCH
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -61,6 +61,7 @@ struct mraid_plan_s {
   mraid_flag_info* d_info = nullptr;  // device flag info
   unsigned long long* d_degenerate = nullptr;
   unsigned* d_error = nullptr;        // device error word (bounded waits)
+  unsigned long long* d_sweeps = nullptr;  // Jacobi sweeps: [0] per cell, [1] per warp
   mraid_flag_info* h_info = nullptr;  // pinned staging
   mraid_flag_info* pending_info = nullptr;  // user pointer to fill at sync
   mraid::Workspace ws;
@@ -75,11 +76,17 @@ struct mraid_plan_s {
   cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
   mraid::Profiler prof;
   bool force_dp4a = false;  // use the CUDA-core Gram even where tcgen05 fits
+  int tc_variant = 0;       // tensor-core Gram tile variant (autotuned)
 };
 
 namespace mraid {
 
 void set_error(const char* fmt, ...);
+// Allocate every work buffer mraid_run can need (so later calls allocate
+// nothing, e.g. inside a stream capture).
+mraid_status plan_prepare(mraid_plan_s* pl);
+// Copy the staged mraid_flag_info to the caller's struct (stream synced).
+void plan_deliver_info(mraid_plan_s* pl);
 // Bracket a kernel launch with profiling events (no-ops unless enabled).
 void prof_begin(mraid_plan_s* pl, int id, cudaEvent_t* start);
 void prof_end(mraid_plan_s* pl, int id, cudaEvent_t start);
@@ -93,6 +100,8 @@ cudaError_t launch_gram_u8(const mraid_plan_s* pl, const uint8_t* d_data,
 // tensor-core Gram fused with the correlation (gram_tc.cu); either output
 // may be null. cudaErrorNotSupported when the shape or layout does not fit.
 bool gram_tc_supported(const mraid_plan_s* pl, const void* d_data);
+int tc_variant_samples(int v);
+constexpr int kTcVariants = 3;
 cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int sub0, int n_sub,
                            int64_t* d_sums, float* d_corr);
 cudaError_t launch_corr_from_sums(const mraid_plan_s* pl, const int64_t* d_sums,

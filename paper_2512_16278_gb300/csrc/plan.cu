@@ -187,6 +187,21 @@ mraid_status enqueue_info_copy(mraid_plan_s* pl, mraid_flag_info* info) {
 }
 
 }  // namespace
+
+mraid_status plan_prepare(mraid_plan_s* pl) {
+  mraid_status st = ensure_workspace(pl, (size_t)pl->n_cells);
+  if (st != MRAID_OK) return st;
+  float* ev = nullptr;
+  return evals_for_q1(pl, (size_t)pl->n_cells, &ev);
+}
+
+void plan_deliver_info(mraid_plan_s* pl) {
+  if (pl->pending_info) {
+    *pl->pending_info = *pl->h_info;
+    pl->pending_info = nullptr;
+  }
+}
+
 }  // namespace mraid
 
 using namespace mraid;
@@ -266,6 +281,10 @@ mraid_status mraid_validate(const mraid_params* p) {
     set_error("max_clip_iter %d outside [1, %d]", p->max_clip_iter, kMaxClipIter);
     return MRAID_ERR_INVALID_ARG;
   }
+  if ((int64_t)p->n_sub * p->n_chan > 2147483647ll) {
+    set_error("n_sub * n_chan exceeds 2^31 - 1 cells");
+    return MRAID_ERR_INVALID_ARG;
+  }
   if (p->reserved != 0) {
     set_error("reserved field must be 0");
     return MRAID_ERR_INVALID_ARG;
@@ -303,6 +322,8 @@ mraid_status mraid_plan(const mraid_params* p, void* stream, mraid_plan_t* out) 
   if (e == cudaSuccess) e = cudaMalloc(&pl->d_info, sizeof(mraid_flag_info));
   if (e == cudaSuccess) e = cudaMalloc(&pl->d_degenerate, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&pl->d_error, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(&pl->d_sweeps, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_sweeps, 0, 2 * sizeof(unsigned long long), pl->stream);
   if (e == cudaSuccess) e = cudaMallocHost(&pl->h_info, sizeof(mraid_flag_info));
   if (e == cudaSuccess && p->keep) {
     e = cudaMalloc(&pl->d_keep, (size_t)p->n_chan);
@@ -374,6 +395,8 @@ mraid_status mraid_run(mraid_plan_t pl, const void* d_data, float* d_evals, floa
   st = ensure_workspace(pl, (size_t)pl->n_cells);
   if (st != MRAID_OK) return st;
   cudaError_t e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(pl->d_sweeps, 0, 2 * sizeof(unsigned long long), pl->stream);
   if (e != cudaSuccess) return cuda_fail(e, "memset");
   st = ccm_range(pl, d_data, 0, pl->p.n_sub, nullptr, pl->ws.corr);
   if (st != MRAID_OK) return st;
@@ -387,7 +410,10 @@ mraid_status mraid_run(mraid_plan_t pl, const void* d_data, float* d_evals, floa
   if (e != cudaSuccess) return cuda_fail(e, "flag launch");
   e = cudaMemcpyAsync(&pl->d_info->n_degenerate, pl->d_degenerate, sizeof(int64_t),
                       cudaMemcpyDeviceToDevice, pl->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "degenerate copy");
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&pl->d_info->jacobi_sweeps, pl->d_sweeps, 2 * sizeof(int64_t),
+                        cudaMemcpyDeviceToDevice, pl->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "counter copy");
   return enqueue_info_copy(pl, info);
 }
 
@@ -427,6 +453,8 @@ mraid_status mraid_run_host(mraid_plan_t pl, const void* h_data, float* h_stat, 
   st = ensure_workspace(pl, (size_t)chunk * pl->p.n_chan);
   if (st != MRAID_OK) return st;
   e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(pl->d_sweeps, 0, 2 * sizeof(unsigned long long), pl->stream);
   // The chunk buffer holds [beam][chunk subs * n_samp_sub][chan]; the kernels
   // see it as a block of `chunk` sub-integrations with beam stride
   // chunk * n_samp_sub * n_chan.
@@ -465,6 +493,9 @@ mraid_status mraid_run_host(mraid_plan_t pl, const void* h_data, float* h_stat, 
   e = MRAID_PROF(pl, K_FLAG, launch_flag(pl, pl->d_stat_full, pl->d_flags_full));
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&pl->d_info->n_degenerate, pl->d_degenerate, sizeof(int64_t),
+                        cudaMemcpyDeviceToDevice, pl->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&pl->d_info->jacobi_sweeps, pl->d_sweeps, 2 * sizeof(int64_t),
                         cudaMemcpyDeviceToDevice, pl->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h_flags, pl->d_flags_full, (size_t)pl->n_cells, cudaMemcpyDeviceToHost, pl->stream);
@@ -507,6 +538,76 @@ mraid_status mraid_query(mraid_plan_t pl) {
   if (e == cudaErrorNotReady) return MRAID_ERR_NOT_READY;
   if (e != cudaSuccess) return cuda_fail(e, "mraid_query");
   return mraid_sync(pl);
+}
+
+mraid_status mraid_set_variant(mraid_plan_t pl, int32_t variant) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  if (variant < -1 || variant >= kTcVariants) {
+    set_error("mraid_set_variant: variant %d outside [-1, %d)", variant, kTcVariants);
+    return MRAID_ERR_INVALID_ARG;
+  }
+  pl->force_dp4a = variant < 0;
+  pl->tc_variant = variant < 0 ? 0 : variant;
+  return MRAID_OK;
+}
+
+mraid_status mraid_autotune(mraid_plan_t pl, const void* d_data, int32_t reps, int32_t* choice,
+                            char* report, int32_t report_len) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  if (!d_data || !choice || reps < 1 || reps > 1000 || (report && report_len < 1)) {
+    set_error("mraid_autotune: bad arguments");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  st = ensure_workspace(pl, (size_t)pl->n_cells);
+  if (st != MRAID_OK) return st;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_fail(e, "mraid_autotune");
+  const bool save_dp4a = pl->force_dp4a;
+  const int save_v = pl->tc_variant;
+  float best = 1e30f;
+  int best_v = -2;
+  int used = 0;
+  if (report) report[0] = 0;
+  for (int v = -1; v < kTcVariants && st == MRAID_OK; ++v) {
+    pl->force_dp4a = v < 0;
+    pl->tc_variant = v < 0 ? 0 : v;
+    if (v >= 0 && !gram_tc_supported(pl, d_data)) continue;
+    st = ccm_range(pl, d_data, 0, pl->p.n_sub, nullptr, pl->ws.corr);  // warm-up
+    if (st != MRAID_OK) break;
+    e = cudaEventRecord(e0, pl->stream);
+    for (int r = 0; r < reps && st == MRAID_OK && e == cudaSuccess; ++r)
+      st = ccm_range(pl, d_data, 0, pl->p.n_sub, nullptr, pl->ws.corr);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, pl->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "mraid_autotune");
+      break;
+    }
+    ms /= reps;
+    if (report && used < report_len - 1)
+      used += snprintf(report + used, (size_t)(report_len - used), "%d:%.4f;", v, ms);
+    if (ms < best) {
+      best = ms;
+      best_v = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != MRAID_OK || best_v < -1) {
+    pl->force_dp4a = save_dp4a;
+    pl->tc_variant = save_v;
+    return st != MRAID_OK ? st : MRAID_ERR_UNSUPPORTED;
+  }
+  pl->force_dp4a = best_v < 0;
+  pl->tc_variant = best_v < 0 ? 0 : best_v;
+  *choice = best_v;
+  return MRAID_OK;
 }
 
 mraid_status mraid_profile_enable(mraid_plan_t pl, int32_t enable) {
@@ -574,6 +675,7 @@ void mraid_destroy(mraid_plan_t pl) {
   cudaFree(pl->d_info);
   cudaFree(pl->d_degenerate);
   cudaFree(pl->d_error);
+  cudaFree(pl->d_sweeps);
   if (pl->h_info) cudaFreeHost(pl->h_info);
   if (dev >= 0 && dev != pl->device) cudaSetDevice(dev);
   delete pl;

@@ -1,0 +1,63 @@
+"""Batched form over uneven receiver shapes (mraid_batch_*), needs a GPU.
+
+Every unit's result in the batch must equal the same unit run alone
+(mraid_run) bit for bit, and match the oracle at the stated tolerances; a
+replay with new buffers must rebind them through a graph update."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import compare_eig, compare_flags, compare_q1, lib, STAT_TOL
+
+pytestmark = pytest.mark.gpu
+
+# 13-, 19-, 36- and 72-beam receivers at reduced channel counts
+SHAPES = [(13, 16, 512, 4), (19, 32, 1024, 3), (36, 6, 256, 3), (72, 3, 512, 2)]
+
+
+def unit_data(i, shape):
+    n_beam, n_chan, n_s, n_sub = shape
+    cfg = synth.SynthConfig(n_beam=n_beam, n_chan=n_chan, n_samp_sub=n_s, n_sub=n_sub,
+                            seed=3000 + i, bandpass=1, n_narrow=1, n_burst=1, n_spike=1)
+    return cfg, synth.generate(cfg)
+
+
+def test_batch_equals_alone_and_oracle():
+    import torch
+    m = lib()
+    cfgs, datas = zip(*[unit_data(i, s) for i, s in enumerate(SHAPES)])
+    d_dev = [torch.from_numpy(d).cuda() for d in datas]
+    with m.Batch(SHAPES) as batch:
+        outs = batch.run(d_dev)
+        torch.cuda.synchronize()
+        # alone
+        for (shape, d, o, cfg, data) in zip(SHAPES, d_dev, outs, cfgs, datas):
+            n_beam, n_chan, n_s, n_sub = shape
+            with m.Plan(n_beam, n_chan, n_s, n_sub) as plan:
+                alone = plan.run(d)
+            for k in ("evals", "q1", "stat", "flags"):
+                assert torch.equal(alone[k], o[k]), (shape, k)
+            assert alone["info"]["n_flagged"] == o["info"]["n_flagged"]
+            # oracle
+            subs = np.repeat(np.arange(n_sub, dtype=np.int32), n_chan)
+            chans = np.tile(np.arange(n_chan, dtype=np.int32), n_sub)
+            orc = oracle.cells(data, n_s, subs, chans, n_threads=synth.default_threads())
+            ev = o["evals"].cpu().numpy()
+            compare_eig(ev, orc["evals"], str(shape))
+            compare_q1(o["q1"].cpu().numpy(), orc["q1"], orc["evals"])
+            st = o["stat"].cpu().numpy()
+            assert (np.abs(st - orc["stat"]) / orc["stat"]).max() <= STAT_TOL
+            f_o, i_o = oracle.flag(orc["stat"], n_chan)
+            compare_flags(o["flags"].cpu().numpy(), f_o, orc["stat"], o["info"], i_o)
+        # replay with new output buffers: one instantiation, then an update
+        outs2 = batch.run(d_dev)
+        torch.cuda.synchronize()
+        for o, o2 in zip(outs, outs2):
+            for k in ("evals", "q1", "stat", "flags"):
+                assert torch.equal(o[k], o2[k])
+        inst, upd = batch.graph_stats()
+        assert inst == 1 and upd == 1
+        # replay with the same buffers: neither
+        batch.run(d_dev, outs2)
+        assert batch.graph_stats() == (1, 1)
