@@ -65,9 +65,10 @@ def _load():
         lib.orc_block_u8.argtypes = [_P, i32, i64, i32, i32, i32, i32, _P, _P, _P]
         lib.orc_cells_u8.argtypes = [_P, i32, i64, i32, i32, i64, _P, _P, i32, _P, _P, _P, _P]
         lib.orc_flag.argtypes = [_P, i64, i32, _P, dbl, i32, _P, ctypes.POINTER(FlagInfo)]
+        lib.orc_beam_flags.argtypes = [_P, _P, i64, i32, _P, i32, dbl, _P, _P]
         for f in ("orc_cell_gram_u8", "orc_cell_cov_f32", "orc_corr_from_gram",
                   "orc_corr_from_cov", "orc_jacobi", "orc_cell_u8", "orc_block_u8",
-                  "orc_cells_u8", "orc_flag"):
+                  "orc_cells_u8", "orc_flag", "orc_beam_flags"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -206,3 +207,19 @@ def flag(stat_: np.ndarray, n_chan: int, keep: Optional[np.ndarray] = None,
     _check(_load().orc_flag(_ptr(stat_), stat_.shape[0], n_chan, _ptr(kp), k_sigma,
                             max_iter, _ptr(flags), ctypes.byref(info)), "flag")
     return flags, info.as_dict()
+
+
+def beam_flags(q1: np.ndarray, flags: np.ndarray, n_chan: int, keep: Optional[np.ndarray] = None,
+               t: float = 1.0):
+    """(bits uint32 [cells][ceil(N/32)], mu_sigma [N][2]) of the eigenvector
+    refinement."""
+    q1 = np.ascontiguousarray(q1, dtype=np.float64)
+    n_cells, n_beam = q1.shape
+    flags = np.ascontiguousarray(flags, dtype=np.uint8).ravel()
+    W = (n_beam + 31) // 32
+    bits = np.zeros((n_cells, W), dtype=np.uint32)
+    ms = np.zeros((n_beam, 2))
+    kp = None if keep is None else np.ascontiguousarray(keep, dtype=np.uint8)
+    _check(_load().orc_beam_flags(_ptr(q1), _ptr(flags), n_cells, n_chan, _ptr(kp), n_beam, t,
+                                  _ptr(bits), _ptr(ms)), "beam_flags")
+    return bits, ms

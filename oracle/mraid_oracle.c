@@ -385,3 +385,48 @@ int orc_flag(const double* stat, int64_t n_cells, int32_t n_chan,
   free(vals);
   return 0;
 }
+
+/* --------------------------------------- eigenvector refinement (Sec. 3.3) */
+
+int orc_beam_flags(const double* q1, const uint8_t* flags, int64_t n_cells, int32_t n_chan,
+                   const uint8_t* keep, int32_t n_beam, double t, uint32_t* bits,
+                   double* mu_sigma) {
+  if (!q1 || !flags || !bits || n_cells < 0 || n_chan < 1 || n_beam < 1 || !(t >= 0.0))
+    return -1;
+  const int32_t W = (n_beam + 31) / 32;
+  double* vals = (double*)malloc(sizeof(double) * (size_t)(n_cells > 0 ? n_cells : 1));
+  double* mu = (double*)calloc((size_t)n_beam, sizeof(double));
+  double* sg = (double*)calloc((size_t)n_beam, sizeof(double));
+  if (!vals || !mu || !sg) {
+    free(vals);
+    free(mu);
+    free(sg);
+    return -1;
+  }
+  for (int32_t b = 0; b < n_beam; ++b) {
+    /* Gaussian fit to the beam's eigenvector elements of non-RFI cells */
+    int64_t m = 0;
+    for (int64_t i = 0; i < n_cells; ++i)
+      if (!flags[i] && !(keep && keep[i % n_chan])) vals[m++] = fabs(q1[i * n_beam + b]);
+    if (m > 0) {
+      mu[b] = pairwise_sum(vals, m) / (double)m;
+      for (int64_t i = 0; i < m; ++i) vals[i] = (vals[i] - mu[b]) * (vals[i] - mu[b]);
+      sg[b] = sqrt(pairwise_sum(vals, m) / (double)m);
+    }
+  }
+  for (int64_t i = 0; i < n_cells; ++i) {
+    for (int32_t w = 0; w < W; ++w) bits[i * W + w] = 0u;
+    if (!flags[i]) continue;
+    for (int32_t b = 0; b < n_beam; ++b)
+      if (fabs(q1[i * n_beam + b]) > mu[b] + t * sg[b]) bits[i * W + b / 32] |= 1u << (b % 32);
+  }
+  if (mu_sigma)
+    for (int32_t b = 0; b < n_beam; ++b) {
+      mu_sigma[2 * b] = mu[b];
+      mu_sigma[2 * b + 1] = sg[b];
+    }
+  free(vals);
+  free(mu);
+  free(sg);
+  return 0;
+}

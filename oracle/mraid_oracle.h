@@ -99,6 +99,17 @@ int orc_flag(const double* stat, int64_t n_cells, int32_t n_chan,
              const uint8_t* keep, double k_sigma, int32_t max_iter,
              uint8_t* flags, orc_flag_info* info);
 
+/* Eigenvector refinement (Section 3.3 last paragraph, Section 4.5
+ * eigenvector threshold, t = 1): for every beam b a Gaussian fit (mean,
+ * population sigma) to |q1_b| over the cells NOT flagged by the eigenvalue
+ * mask and not preserved; a flagged cell marks beam b as affected when
+ * |q1_b| > mu_b + t sigma_b. q1 [cell][N]; flags [cell]; keep [n_chan] or
+ * NULL; bits [cell][ceil(N/32)] (bit b of word b/32); mu_sigma [N][2] or
+ * NULL. Returns 0 or -1. */
+int orc_beam_flags(const double* q1, const uint8_t* flags, int64_t n_cells, int32_t n_chan,
+                   const uint8_t* keep, int32_t n_beam, double t, uint32_t* bits,
+                   double* mu_sigma);
+
 #ifdef __cplusplus
 }
 #endif

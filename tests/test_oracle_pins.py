@@ -353,3 +353,63 @@ def test_beam_common_rfi_flagged_single_beam_not(small_block):
     # RFI cells have a near rank-one CCM
     assert min(S[k, c] for (k, c) in cells["burst"]) > 0.5
     assert info["converged"] == 1
+
+
+# ------------------------------- eigenvector refinement (Sec. 3.3, 4.5)
+
+def test_beam_flags_closed_form():
+    """Unflagged cells with |q1_b| in {0.1, 0.3} equally often give mu_b = 0.2,
+    sigma_b = 0.1 exactly; a flagged cell marks beam b iff |q1_b| > 0.2 + t 0.1."""
+    n_beam, n_clean = 3, 100
+    q = np.zeros((n_clean + 2, n_beam))
+    q[:n_clean:2] = 0.1
+    q[1:n_clean:2] = -0.3                  # magnitudes count, not signs
+    flags = np.zeros(n_clean + 2, dtype=np.uint8)
+    flags[n_clean:] = 1
+    q[n_clean] = [0.35, 0.25, -0.31]        # t = 1: threshold 0.3
+    q[n_clean + 1] = [0.29, 0.9, 0.0]
+    bits, ms = oracle.beam_flags(q, flags, 1, t=1.0)
+    np.testing.assert_allclose(ms[:, 0], 0.2, atol=1e-15)
+    np.testing.assert_allclose(ms[:, 1], 0.1, atol=1e-15)
+    assert bits[n_clean, 0] == 0b101 and bits[n_clean + 1, 0] == 0b010
+    assert not bits[:n_clean].any()        # unflagged cells carry no beam bits
+    bits2, _ = oracle.beam_flags(q, flags, 1, t=0.0)   # threshold 0.2
+    assert bits2[n_clean, 0] == 0b111 and bits2[n_clean + 1, 0] == 0b011
+
+
+def test_beam_flags_monotone_in_t_and_many_beams():
+    rng = np.random.default_rng(41)
+    n_cells, n_beam = 2000, 40                 # two words of bits
+    q = rng.normal(0, 1, size=(n_cells, n_beam))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    flags = (rng.random(n_cells) < 0.1).astype(np.uint8)
+    prev = None
+    for t in (0.0, 1.0, 2.0, 3.0):
+        bits, ms = oracle.beam_flags(q, flags, 1, t=t)
+        assert bits.shape == (n_cells, 2)
+        count = sum(bin(int(x)).count("1") for x in bits.ravel())
+        if prev is not None:
+            assert count <= prev
+        prev = count
+    # beam 35 lives in word 1, bit 3
+    bits, ms = oracle.beam_flags(q, flags, 1, t=0.0)
+    i = int(np.flatnonzero(flags)[0])
+    assert ((bits[i, 1] >> 3) & 1) == (abs(q[i, 35]) > ms[35, 0])
+
+
+def test_beam_flags_rfi_beams_on_small_block(small_block):
+    """Beam-common narrowband RFI with per-beam gains (Sec. 3.3, Fig. 3): in
+    its channel, the beams with larger eigenvector elements are the ones
+    marked as affected; unflagged cells carry no beam bits."""
+    cfg = synth.SMALL
+    res = oracle.block(small_block, cfg.n_samp_sub, n_threads=synth.default_threads())
+    flags, _ = oracle.flag(res["stat"], cfg.n_chan)
+    bits, ms = oracle.beam_flags(res["q1"], flags, cfg.n_chan, t=1.0)
+    assert not bits[flags == 0].any()
+    ch = synth.events(cfg)["narrow"][0][0]
+    b = bits.reshape(cfg.n_sub, cfg.n_chan, -1)[:, ch, 0]
+    freq = np.array([np.mean((b >> k) & 1) for k in range(cfg.n_beam)])
+    mag = np.abs(res["q1"].reshape(cfg.n_sub, cfg.n_chan, -1)[:, ch, :]).mean(axis=0)
+    rank = lambda v: np.argsort(np.argsort(v))
+    rho = np.corrcoef(rank(freq), rank(mag))[0, 1]      # Spearman
+    assert rho > 0.6, rho
