@@ -145,14 +145,25 @@ def gpu_index(local_rank):
 
 # ------------------------------------------------------------- peaks
 
+EIG_NAMES = {0: "jacobi (looped rounds)", 1: "jacobi (unrolled sweep)",
+             2: "householder + implicit QR", 3: "householder + implicit QR (compact)"}
+SMS, FP32_LANES = 152, 128          # GB300: SMs, FP32 lanes per SM
+
+
 def measured_peaks():
+    """HBM copy bandwidth (measured), and the FP32 ALU peak derived from the
+    lane count at the maximum SM clock the same file records: 152 SMs x 128
+    lanes x 2 flops per FMA x 2070 MHz = 80.5 TFLOP/s."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+        mhz = float(d.get("sm_max_mhz", 2070.0))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured",
+                "fp32_tflops": SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12}
     except (OSError, KeyError, ValueError):
-        return {"hbm_gbs": 6800.0, "source": "fallback"}
+        return {"hbm_gbs": 6800.0, "source": "fallback",
+                "fp32_tflops": SMS * FP32_LANES * 2 * 2070e6 / 1e12}
 
 
 def kernel_traffic(name):
@@ -334,6 +345,22 @@ def bench_served(m, torch, seconds, rates=(1.0, 2.0, 4.0)):
     return out
 
 
+def max_over_ranks(value, dist, device=None):
+    """The largest value over all ranks (the step time the job is charged);
+    value itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device) if device else torch.tensor([float(value)])
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(cells_per_rank, world, ms_max):
+    """Whole-job cells/s: all ranks' cells over the slowest rank's time."""
+    return world * cells_per_rank / (ms_max / 1000.0)
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -371,6 +398,41 @@ def run_reference(args):
     return 0
 
 
+def kernel_rooflines(cfg, kt, peaks):
+    """Roofline of every timed kernel: algorithmic work per launch (bytes for
+    the memory-bound kernels, flops for the eigensolver) over its average
+    launch time, against the bound that limits it."""
+    N, cells = cfg.n_beam, cfg.n_cells
+    np_, psum = N * (N + 1) // 2, (N + 1) * (N + 2) // 2
+    in_bytes = N * cfg.n_samp_sub * cells
+    hbm = {  # bytes per launch: what the kernel must read and write once
+        "gram_tc": in_bytes + cells * 4 * np_,                 # samples in, r out
+        "gram_u8": in_bytes + cells * 8 * psum,                # samples in, sums out
+        "corr_from_sums": cells * (8 * psum + 4 * np_),
+        "flag_clip": cells * 5,                                # stat in, flag out
+    }
+    # eigensolver: the dense floor, (4/3) N^3 flops of a tridiagonal
+    # reduction per cell (all N eigenvalues then cost O(N^2) more)
+    eig_flops = cells * 4.0 * N ** 3 / 3.0
+    out = {}
+    for k, (n, ms) in kt.items():
+        if k == "eig":
+            a = eig_flops / (ms / 1e3) / 1e12
+            out[k] = {"bound": "alu", "kernel": k, "achieved": a, "peak": peaks["fp32_tflops"],
+                      "unit": "TFLOP/s", "frac": a / peaks["fp32_tflops"],
+                      "traffic": kernel_traffic(k),
+                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                      "work_per_launch": eig_flops, "ms_per_launch": ms}
+        else:
+            b = hbm.get(k, in_bytes)
+            a = b / (ms / 1e3) / 1e9
+            out[k] = {"bound": "hbm", "kernel": k, "achieved": a, "peak": peaks["hbm_gbs"],
+                      "unit": "GB/s", "frac": a / peaks["hbm_gbs"], "traffic": kernel_traffic(k),
+                      "peak_source": peaks["source"] + " (burst copy)",
+                      "work_per_launch": b, "ms_per_launch": ms}
+    return out
+
+
 def run_mraid(args):
     world, rank, local = dist_setup(args)
     import torch
@@ -399,6 +461,10 @@ def run_mraid(args):
         stat = torch.empty(cells, dtype=torch.float32, device="cuda")
         flags = torch.empty(cells, dtype=torch.uint8, device="cuda")
     info = m.FlagInfo()
+    # the plan's kernel variants, picked by the autotuner for this shape
+    # (cached per shape; tuning runs before and outside the timed region)
+    tune_cache = os.path.join(ROOT, "paper_2512_16278_gb300", "_build", "tune.json")
+    variants = m.tune(plan.handle, d, N, cfg.n_chan, cfg.n_samp_sub, tune_cache)
 
     def step():
         m.mraid_run(plan.handle, d, evals, q1, stat, flags, info)
@@ -427,11 +493,8 @@ def run_mraid(args):
     ms = e0.elapsed_time(e1) / args.steps
     m.mraid_profile_enable(plan.handle, False)
     prof = m.mraid_profile_read(plan.handle)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * cells / (ms / 1000.0)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = job_throughput(cells, world, ms)
 
     # roofline of the dominant kernel (per-launch averages from the events
     # the plan recorded around each launch inside the timed region)
@@ -439,21 +502,10 @@ def run_mraid(args):
     launches = sum(n for (n, _) in prof.values())
     dom = max(kt, key=lambda k: kt[k][0] * kt[k][1])
     peaks = measured_peaks()
+    roofs = kernel_rooflines(cfg, kt, peaks)
+    roof = roofs[dom]
     in_bytes = cfg.n_beam * cfg.n_samp_sub * cells          # samples read once
     out_bytes = cells * (4 + 1 + 8 * N)                     # stat, flag, evals, q1
-    np_, psum = N * (N + 1) // 2, (N + 1) * (N + 2) // 2
-    alg = {  # algorithmic bytes per launch of each kernel
-        "gram_u8": in_bytes,
-        "corr_from_sums": cells * (8 * psum + 4 * np_),
-        "eig_jacobi": cells * (4 * np_ + 4 + 8 * N),
-        "flag_clip": cells * 5,
-    }
-    dom_ms = kt[dom][1]
-    achieved = alg.get(dom, in_bytes) / (dom_ms / 1000.0) / 1e9
-    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
-            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-            "traffic": kernel_traffic(dom), "peak_source": peaks["source"] + " (burst copy)",
-            "ms_per_launch": dom_ms}
     path_gbs = (in_bytes + out_bytes) / (ms / 1000.0) / 1e9
 
     # end to end through the C ABI with host buffers (pinned), copies inside
@@ -470,11 +522,7 @@ def run_mraid(args):
         for _ in range(args.e2e_steps):
             m.mraid_run_host(plan.handle, h, h_stat, h_flags, hinfo)
             m.mraid_sync(plan.handle)
-        te = (time.perf_counter() - t0) / args.e2e_steps
-        if dist:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dist, "cuda")
         e2e = {"value": world * cells / te, "unit": UNIT, "h2d_bytes_per_step": cfg.nbytes,
                "d2h_bytes_per_step": cells * 5, "ms_per_step": te * 1000.0,
                "api": "mraid_run_host (pinned host input, stat + flags copied back)"}
@@ -503,6 +551,7 @@ def run_mraid(args):
                     "frac_of_measured": path_gbs / peaks["hbm_gbs"],
                     "frac_of_8tbs_nominal": path_gbs / 8000.0},
             "roofline": roof,
+            "rooflines": roofs,
             "kernels_ms_per_launch": {k: v[1] for k, v in kt.items()},
             "gpu_launches": launches,
             "clocks": clk,
@@ -510,8 +559,11 @@ def run_mraid(args):
             "cpu_baseline": cpu,
             "mask": {"flagged_fraction": info.n_flagged / cells, "iterations": info.iterations,
                      "threshold": info.thresh, "n_near": info.n_near},
-            "jacobi": {"sweeps_per_cell": info.jacobi_sweeps / cells,
-                       "sweeps_per_warp": info.jacobi_warp_sweeps / max(1, (cells + 31) // 32)},
+            "variants": {"gram": variants[0], "eig": variants[1],
+                         "eig_name": EIG_NAMES.get(variants[1], "?")},
+            "eig_iterations": {"per_cell": info.jacobi_sweeps / cells,
+                               "per_warp": info.jacobi_warp_sweeps / max(1, (cells + 31) // 32),
+                               "unit": "QR steps" if variants[1] >= 2 else "Jacobi sweeps"},
             "batched": batched,
             "served": served,
         }

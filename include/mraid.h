@@ -78,8 +78,11 @@ typedef struct {
   int64_t n_used;        /* cells in the final fit */
   int64_t n_near;        /* unpreserved cells with |s - thresh| <= 2e-4 * s */
   int64_t n_degenerate;  /* (beam, cell) pairs with zero variance (mraid_run) */
-  int64_t jacobi_sweeps; /* Jacobi sweeps summed over cells (mraid_run; 0 if not counted) */
-  int64_t jacobi_warp_sweeps; /* sweeps executed, summed over 32-cell warps (mraid_run) */
+  int64_t jacobi_sweeps; /* eigensolver iterations summed over cells (mraid_run; 0 if not
+                            counted): Jacobi sweeps, or implicit QR steps for the
+                            tridiagonal variant */
+  int64_t jacobi_warp_sweeps; /* the same, as executed: each 32-cell warp counts its slowest
+                                 cell (mraid_run) */
   int32_t timed_out;     /* 1 if a bounded device wait expired */
   int32_t reserved;
 } mraid_flag_info;
@@ -156,6 +159,18 @@ mraid_status mraid_eig(mraid_plan_t plan, const float* d_corr, float* d_evals,
 mraid_status mraid_flag(mraid_plan_t plan, const float* d_stat, uint8_t* d_flags,
                         mraid_flag_info* info);
 
+/* Eigenvector refinement (Section 3.3 last paragraph; threshold multiple
+ * vec_t, Section 4.5): which beams each RFI cell affects. For every beam b,
+ * a Gaussian fit (mean, population sigma) to |q1_b| over the cells that
+ * d_flags leaves unflagged (and not preserved); a flagged cell gets bit b
+ * when |q1_b| > mu_b + vec_t sigma_b.
+ *   d_q1:        float32 [cell][N] from mraid_eig / mraid_run.
+ *   d_flags:     uint8 [cell] from mraid_flag / mraid_run.
+ *   d_beam_bits: uint32 [cell][ceil(N/32)], bit b % 32 of word b / 32.
+ *   d_mu_sigma:  float64 [N][2] (mu_b, sigma_b), device; may be NULL. */
+mraid_status mraid_refine(mraid_plan_t plan, const float* d_q1, const uint8_t* d_flags,
+                          uint32_t* d_beam_bits, double* d_mu_sigma);
+
 /* The whole path (Eq. 1, Eq. 2, masking) on one block already in device
  * memory. d_evals and d_q1 may be NULL; d_stat and d_flags are required;
  * info as in mraid_flag. */
@@ -163,25 +178,37 @@ mraid_status mraid_run(mraid_plan_t plan, const void* d_data, float* d_evals,
                        float* d_q1, float* d_stat, uint8_t* d_flags,
                        mraid_flag_info* info);
 
-/* The whole path on one block in HOST memory: copies h_data to the device in
- * pieces overlapped with the computation, then copies the statistic and the
- * flags back. h_stat (float32 [cell]) may be NULL; h_flags (uint8 [cell]) is
+/* The whole path on one block in HOST memory (layout and beam stride as in
+ * the plan): copies h_data to the device in pieces overlapped with the
+ * computation, then copies the statistic and the flags back. h_stat (float32 [cell]) may be NULL; h_flags (uint8 [cell]) is
  * required. Outputs are valid after mraid_sync. */
 mraid_status mraid_run_host(mraid_plan_t plan, const void* h_data, float* h_stat,
                             uint8_t* h_flags, mraid_flag_info* info);
 
 /* Autotuner (the paper has no counterpart; it picks among this library's
- * kernel variants). Times every Gram variant that fits the plan's shape on
- * d_data (tensor-core tiles of 64 samples x 2 stages, 32 x 4 and 32 x 2, and
- * the CUDA-core Gram), `reps` runs each, and keeps the fastest for this plan.
- * *choice receives its id (-1 = CUDA-core Gram, 0..2 tensor-core tiles);
- * report (may be NULL) receives "id:ms;..." for all candidates. Synchronous. */
+ * kernel variants). Times, `reps` runs each on d_data, every Gram variant
+ * that fits the plan's shape (tensor-core tiles of 64 samples x 2 stages,
+ * 32 x 4 and 32 x 2, and the CUDA-core Gram) and the three register
+ * eigensolvers (Jacobi rounds in a loop; the Jacobi sweep unrolled;
+ * Householder tridiagonalisation + implicit QR in two code layouts), and
+ * keeps the fastest of each for this plan. *gram_choice: -1 = CUDA-core,
+ * 0..2 tiles; *eig_choice: 0..3. report (may be NULL) receives "g<id>:ms;e<id>:ms;...".
+ * Synchronous. */
 mraid_status mraid_autotune(mraid_plan_t plan, const void* d_data, int32_t reps,
-                            int32_t* choice, char* report, int32_t report_len);
+                            int32_t* gram_choice, int32_t* eig_choice, char* report,
+                            int32_t report_len);
 
-/* Select a Gram variant by id (e.g. from a tuning cache): -1 = CUDA-core
- * Gram, 0..2 tensor-core tiles (ignored where the shape does not fit). */
+/* Select variants by id (e.g. from a tuning cache). Gram: -1 = CUDA-core,
+ * 0..2 tensor-core tiles (ignored where the shape does not fit).
+ * Eigensolver (beam counts with a one-thread-per-matrix kernel: 2, 3, 4, 13,
+ * 19; other counts always use the warp-per-matrix Jacobi): 0 = Jacobi,
+ * looped rounds; 1 = Jacobi, unrolled sweep; 2 = Householder reduction to
+ * tridiagonal form, implicit QR with the Wilkinson shift (one unrolled step
+ * per deflation level), q1 by inverse iteration on the tridiagonal matrix;
+ * 3 = the same with one masked QR step for all levels (smaller code; the
+ * default). All give the same outputs to the stated tolerances. */
 mraid_status mraid_set_variant(mraid_plan_t plan, int32_t variant);
+mraid_status mraid_set_eig_variant(mraid_plan_t plan, int32_t variant);
 
 /* ------------------------------------------------------------------------
  * Batched form: blocks of uneven receiver shapes (different N_beam, N_s,

@@ -25,7 +25,8 @@ __all__ = [
     "mraid_batch_plan", "mraid_batch_run", "mraid_batch_sync", "mraid_batch_graph_stats",
     "mraid_batch_destroy", "UnitIO", "Batch", "mraid_serve_open", "mraid_serve_submit",
     "mraid_serve_poll", "mraid_serve_drain", "mraid_serve_close", "StreamDesc", "BlockResult",
-    "Server", "mraid_autotune", "mraid_set_variant", "tune", "STATUS",
+    "Server", "mraid_autotune", "mraid_set_variant", "mraid_set_eig_variant", "tune",
+    "mraid_refine", "STATUS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -150,8 +151,11 @@ def load():
                                             ctypes.POINTER(i32)]),
         "mraid_serve_drain": (ctypes.c_int, [vp, i32]),
         "mraid_serve_close": (None, [vp]),
-        "mraid_autotune": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32), ctypes.c_char_p, i32]),
+        "mraid_autotune": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                          ctypes.c_char_p, i32]),
         "mraid_set_variant": (ctypes.c_int, [vp, i32]),
+        "mraid_set_eig_variant": (ctypes.c_int, [vp, i32]),
+        "mraid_refine": (ctypes.c_int, [vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -162,11 +166,15 @@ def load():
 
 
 def _ptr(x) -> Optional[int]:
-    """Device/host address of a torch tensor, an int, or None."""
+    """Device/host address of a torch tensor, an int, or None. The C ABI
+    takes dense row-major buffers, so a tensor with other strides is an
+    error rather than a silently misread buffer."""
     if x is None:
         return None
     if isinstance(x, int):
         return x
+    if not x.is_contiguous():
+        raise ValueError("mraid buffers must be contiguous (row-major) tensors")
     return x.data_ptr()
 
 
@@ -327,28 +335,38 @@ def mraid_serve_close(srv: int):
 
 
 def mraid_autotune(plan: int, d_data, reps: int = 3):
-    """(chosen variant, {variant: ms}) for the plan's Gram stage."""
-    choice = ctypes.c_int32(0)
+    """((gram variant, jacobi variant), {"g<id>" / "e<id>": ms}) for the plan."""
+    g, e = ctypes.c_int32(0), ctypes.c_int32(0)
     buf = ctypes.create_string_buffer(512)
-    _check(load().mraid_autotune(plan, _ptr(d_data), reps, ctypes.byref(choice), buf, 512),
-           "mraid_autotune")
+    _check(load().mraid_autotune(plan, _ptr(d_data), reps, ctypes.byref(g), ctypes.byref(e),
+                                 buf, 512), "mraid_autotune")
     times = {}
     for item in buf.value.decode().split(";"):
         if item:
             k, v = item.split(":")
-            times[int(k)] = float(v)
-    return choice.value, times
+            times[k] = float(v)
+    return (g.value, e.value), times
+
+
+def mraid_refine(plan: int, d_q1, d_flags, d_beam_bits, d_mu_sigma=None):
+    _check(load().mraid_refine(plan, _ptr(d_q1), _ptr(d_flags), _ptr(d_beam_bits),
+                               _ptr(d_mu_sigma)), "mraid_refine")
 
 
 def mraid_set_variant(plan: int, variant: int):
     _check(load().mraid_set_variant(plan, variant), "mraid_set_variant")
 
 
+def mraid_set_eig_variant(plan: int, variant: int):
+    _check(load().mraid_set_eig_variant(plan, variant), "mraid_set_eig_variant")
+
+
 def tune(plan: int, d_data, n_beam: int, n_chan: int, n_samp_sub: int,
-         cache_path: Optional[str] = None, reps: int = 3) -> int:
-    """Pick the Gram variant for this shape: from the JSON tuning cache
-    (keyed by beams, channels, samples per sub-integration, sample type) if it
-    holds the shape, else by mraid_autotune, recording the result."""
+         cache_path: Optional[str] = None, reps: int = 3):
+    """Pick the Gram and Jacobi variants for this shape: from the JSON tuning
+    cache (keyed by beams, channels, samples per sub-integration, sample type)
+    if it holds the shape, else by mraid_autotune, recording the result.
+    Returns (gram variant, jacobi variant)."""
     import json
     key = f"{n_beam},{n_chan},{n_samp_sub},u8"
     cache = {}
@@ -356,16 +374,18 @@ def tune(plan: int, d_data, n_beam: int, n_chan: int, n_samp_sub: int,
         with open(cache_path) as f:
             cache = json.load(f)
     if key in cache:
-        mraid_set_variant(plan, int(cache[key]["variant"]))
-        return int(cache[key]["variant"])
-    choice, times = mraid_autotune(plan, d_data, reps)
+        g, e = int(cache[key]["gram"]), int(cache[key]["jacobi"])
+        mraid_set_variant(plan, g)
+        mraid_set_eig_variant(plan, e)
+        return g, e
+    (g, e), times = mraid_autotune(plan, d_data, reps)
     if cache_path:
-        cache[key] = {"variant": choice, "ms": {str(k): v for k, v in times.items()}}
+        cache[key] = {"gram": g, "jacobi": e, "ms": times}
         tmp = cache_path + f".{os.getpid()}.tmp"
         with open(tmp, "w") as f:
             json.dump(cache, f, indent=1, sort_keys=True)
         os.replace(tmp, cache_path)
-    return choice
+    return g, e
 
 
 # ------------------------------------------------------------ convenience
@@ -376,7 +396,7 @@ class Plan:
 
     def __init__(self, n_beam: int, n_chan: int, n_samp_sub: int, n_sub: int, *,
                  eig_k: float = 3.0, vec_t: float = 1.0, max_clip_iter: int = 64,
-                 keep=None, beam_stride: int = 0, stream=None):
+                 keep=None, beam_stride: int = 0, stream=None, bit_depth: int = 8):
         import numpy as np
         import torch
         self.torch = torch
@@ -385,6 +405,7 @@ class Plan:
         self.p.vec_t = vec_t
         self.p.max_clip_iter = max_clip_iter
         self.p.beam_stride = beam_stride
+        self.p.bit_depth = bit_depth
         self._keep = None
         if keep is not None:
             self._keep = np.ascontiguousarray(np.asarray(keep, dtype=np.uint8))
@@ -454,6 +475,17 @@ class Plan:
             mraid_sync(self.handle)
             out["info"] = info.as_dict()
         return out
+
+    def refine(self, q1, flags):
+        """(beam bits uint32 [cell][ceil(N/32)], (mu, sigma) [N][2]) of the
+        eigenvector refinement."""
+        t = self.torch
+        W = (self.n_beam + 31) // 32
+        bits = t.empty(self.n_cells, W, dtype=t.int32, device=self.device)
+        ms = t.empty(self.n_beam, 2, dtype=t.float64, device=self.device)
+        mraid_refine(self.handle, q1, flags, bits, ms)
+        mraid_sync(self.handle)
+        return bits, ms
 
     def run_host(self, h_data, h_stat=None, h_flags=None):
         """Whole path from a host block (pinned torch tensor or address)."""

@@ -313,3 +313,176 @@ cudaError_t launch_corr_from_sums(const mraid_plan_s* pl, const int64_t* d_sums,
 }
 
 }  // namespace mraid
+
+// ---------------------------------------------------------------------------
+// Float32 samples (beamformer output): correlation on CUDA cores in FP32.
+// Each cell's samples are shifted by the cell's first sample of each beam
+// before the sums (the covariance does not depend on a per-beam shift, and
+// the shift keeps the sums near zero mean so n S_ab - S_a S_b does not
+// cancel); the sums, the covariance and the correlation are FP32.
+namespace mraid {
+namespace {
+
+constexpr int kF32T = 16;  // samples staged per chunk
+
+struct F32Args {
+  const float* data;
+  int64_t beam_stride;
+  int n_beam, n_chan, n_samp_sub, sub0;
+  int R, cpb, tiles, ntask, cs;
+  int np;
+  float* corr;
+  unsigned long long* degenerate;
+};
+
+__global__ void __launch_bounds__(kGramThreads) gram_f32_kernel(F32Args g) {
+  extern __shared__ float fsm[];
+  float* xs = fsm;                                 // [cpb][R][kF32T] (+1 pad per channel)
+  float* shift = xs + g.cpb * g.cs;                // [cpb][R]
+  float* gram = shift + g.cpb * g.R;               // [cpb][R][R] for the epilogue
+  uint16_t* tile_ij = reinterpret_cast<uint16_t*>(gram + g.cpb * g.R * g.R);
+  const int c0 = blockIdx.x * g.cpb;
+  const int sub = g.sub0 + blockIdx.y;
+  const int T1 = g.R / 4;
+  for (int t = threadIdx.x; t < g.tiles; t += blockDim.x) {
+    int ti = 0, rem = t;
+    while (rem >= T1 - ti) {
+      rem -= T1 - ti;
+      ++ti;
+    }
+    tile_ij[t] = (uint16_t)(ti | ((ti + rem) << 8));
+  }
+  const int64_t t_sub0 = (int64_t)sub * g.n_samp_sub;
+  // shifts: the cell's first sample per beam (0 for the ones row and padding)
+  for (int i = threadIdx.x; i < g.cpb * g.R; i += blockDim.x) {
+    const int c = i / g.R, r = i % g.R;
+    float v = 0.f;
+    if (r < g.n_beam && c0 + c < g.n_chan) v = g.data[r * g.beam_stride + t_sub0 * g.n_chan + c0 + c];
+    shift[i] = v;
+  }
+  float acc[4][16];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc[j][e] = 0.f;
+  __syncthreads();
+  for (int tb = 0; tb < g.n_samp_sub; tb += kF32T) {
+    __syncthreads();
+    const int nv = min(kF32T, g.n_samp_sub - tb);
+    for (int w = threadIdx.x; w < g.R * kF32T * g.cpb; w += blockDim.x) {
+      const int c = w % g.cpb;
+      const int rt = w / g.cpb;
+      const int t = rt % kF32T, r = rt / kF32T;
+      float v = 0.f;
+      if (t < nv && c0 + c < g.n_chan) {
+        if (r < g.n_beam)
+          v = g.data[r * g.beam_stride + (t_sub0 + tb + t) * g.n_chan + c0 + c] - shift[c * g.R + r];
+        else if (r == g.n_beam)
+          v = 1.f;
+      }
+      xs[c * g.cs + r * kF32T + t] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int task = threadIdx.x + j * kGramThreads;
+      if (task < g.ntask) {
+        const int c = task % g.cpb;
+        const uint16_t tij = tile_ij[task / g.cpb];
+        const float* ra = xs + c * g.cs + 4 * (tij & 0xff) * kF32T;
+        const float* rb = xs + c * g.cs + 4 * (tij >> 8) * kF32T;
+        for (int t = 0; t < kF32T; ++t) {
+          float a[4], b[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            a[i] = ra[i * kF32T + t];
+            b[i] = rb[i * kF32T + t];
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[j][4 * i + k] = fmaf(a[i], b[k], acc[j][4 * i + k]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // Gram tiles to shared memory (both triangles), then the correlation
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int task = threadIdx.x + j * kGramThreads;
+    if (task >= g.ntask) continue;
+    const int c = task % g.cpb;
+    const uint16_t tij = tile_ij[task / g.cpb];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int a = 4 * (tij & 0xff) + i, b = 4 * (tij >> 8) + k;
+        gram[(c * g.R + a) * g.R + b] = acc[j][4 * i + k];
+        gram[(c * g.R + b) * g.R + a] = acc[j][4 * i + k];
+      }
+  }
+  __syncthreads();
+  const int N = g.n_beam;
+  for (int e = threadIdx.x; e < g.cpb * g.np; e += blockDim.x) {
+    const int c = e / g.np;
+    if (c0 + c >= g.n_chan) continue;
+    int rem = e - c * g.np, a = 0;
+    while (rem >= N - a) {
+      rem -= N - a;
+      ++a;
+    }
+    const int b = a + rem;
+    const float* G = gram + c * g.R * g.R;
+    const float n = G[N * g.R + N];
+    const float va = n * G[a * g.R + a] - G[a * g.R + N] * G[a * g.R + N];
+    const float vb = n * G[b * g.R + b] - G[b * g.R + N] * G[b * g.R + N];
+    float r;
+    if (a == b) {
+      r = 1.f;
+      if (!(va > 0.f)) atomicAdd(g.degenerate, 1ull);
+    } else if (!(va > 0.f) || !(vb > 0.f)) {
+      r = 0.f;
+    } else {
+      const float cov = n * G[a * g.R + b] - G[a * g.R + N] * G[b * g.R + N];
+      r = cov * rsqrtf(va) * rsqrtf(vb);
+    }
+    g.corr[((int64_t)blockIdx.y * g.n_chan + c0 + c) * g.np + (e - c * g.np)] = r;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gram_f32(const mraid_plan_s* pl, const float* d_data, int sub0, int n_sub,
+                            float* d_corr) {
+  F32Args g;
+  g.data = d_data;
+  g.beam_stride = pl->beam_stride;
+  g.n_beam = pl->p.n_beam;
+  g.n_chan = pl->p.n_chan;
+  g.n_samp_sub = pl->p.n_samp_sub;
+  g.sub0 = sub0;
+  g.R = ((g.n_beam + 1 + 3) / 4) * 4;
+  const int T1 = g.R / 4;
+  g.tiles = T1 * (T1 + 1) / 2;
+  int cpb = (4 * kGramThreads) / g.tiles;
+  cpb = cpb >= 16 ? 16 : (cpb < 1 ? 1 : cpb);
+  if (cpb > g.n_chan) cpb = g.n_chan;
+  g.cpb = cpb;
+  g.ntask = cpb * g.tiles;
+  g.cs = g.R * kF32T + 1;
+  g.np = pl->np;
+  g.corr = d_corr;
+  g.degenerate = pl->d_degenerate;
+  const size_t smem = sizeof(float) * ((size_t)cpb * g.cs + (size_t)cpb * g.R + (size_t)cpb * g.R * g.R) +
+                      (size_t)g.tiles * 2 + 16;
+  cudaError_t e = cudaFuncSetAttribute(gram_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((g.n_chan + cpb - 1) / cpb, n_sub);
+  gram_f32_kernel<<<grid, kGramThreads, smem, pl->stream>>>(g);
+  return cudaGetLastError();
+}
+
+}  // namespace mraid

@@ -33,6 +33,8 @@
 #include <stdint.h>
 #include <stdlib.h>
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace mraid {
@@ -63,6 +65,7 @@ constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 struct TcArgs {
   int n_beam, n_chan, n_samp_sub, sub0, n_sub;
+  int n_u8;  // u8 ring depth (stages), fixed at launch with the shared-memory size
   int rb;   // slots in B of the first MMA (N+1 rounded up to even)
   int r2;   // slots in B of the second MMA (0 if N+1 <= 16), even
   int swap_ls;  // nonzero: exchange the LBO / SBO fields of the descriptors
@@ -197,21 +200,23 @@ struct Smem {
   float s_inv[2][8][kGroupSlots];     // 1/sqrt(var_a), 0 if var_a == 0
 };
 
-// u8 ring depth for n_beam beams: as deep as the shared memory allows, so
-// TMA keeps streaming while the MMAs pause for an epilogue
+// u8 ring depth for n_beam beams: as deep as the shared memory allows
+// (less `reserve` bytes left for a kernel running beside this one), so TMA
+// keeps streaming while the MMAs pause for an epilogue
 template <class C>
-__host__ __device__ constexpr int u8_ring_depth(int n_beam) {
-  return (int)((kSmemBudget - 1024 - (size_t)C::kNF * C::kF16StageBytes - sizeof(Smem)) /
+__host__ __device__ constexpr int u8_ring_depth(int n_beam, size_t reserve) {
+  return (int)((kSmemBudget - reserve - 1024 - (size_t)C::kNF * C::kF16StageBytes - sizeof(Smem)) /
                ((size_t)n_beam * C::kT * kBoxCh)) < kMaxNU
-             ? (int)((kSmemBudget - 1024 - (size_t)C::kNF * C::kF16StageBytes - sizeof(Smem)) /
+             ? (int)((kSmemBudget - reserve - 1024 - (size_t)C::kNF * C::kF16StageBytes -
+                      sizeof(Smem)) /
                      ((size_t)n_beam * C::kT * kBoxCh))
              : kMaxNU;
 }
-// dynamic shared memory for n_beam beams: f16 ring, u8 ring, barriers
+// dynamic shared memory for n_beam beams and a ring of n_u8 stages
 template <class C>
-__host__ __device__ constexpr size_t smem_bytes(int n_beam) {
+__host__ __device__ constexpr size_t smem_bytes(int n_beam, int n_u8) {
   return 1024 /* alignment slack */ + (size_t)C::kNF * C::kF16StageBytes +
-         (size_t)u8_ring_depth<C>(n_beam) * n_beam * C::kT * kBoxCh + sizeof(Smem);
+         (size_t)n_u8 * n_beam * C::kT * kBoxCh + sizeof(Smem);
 }
 
 template <int T_, int NF_>
@@ -223,7 +228,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int kNU = u8_ring_depth<C>(g.n_beam);
+  const int kNU = g.n_u8;
   unsigned char* f16 = base;                                   // kNF stages
   unsigned char* u8 = f16 + (size_t)kNF * kF16StageBytes;      // kNU stages
   const int u8_stage_bytes = g.n_beam * kT * kBoxCh;
@@ -392,30 +397,30 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
       float row2[2][8];            // D2 row `slot2`: G[slot2][16..16+r2)
 #pragma unroll
       for (int grp = 0; grp < 2; ++grp) {
-        // D1 row: chunks of 4 slots, two loads in flight per wait
+        // D1 row: chunks of 32 columns (4 slots x 8 channels), one load in
+        // flight per wait to keep the register count low
 #pragma unroll
-        for (int ch = 0; ch < kGroupSlots / 4; ch += 2) {
+        for (int ch = 0; ch < kGroupSlots / 4; ++ch) {
           if (ch * 4 < g.rb) {
-            uint32_t v[32], w[32];
-            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + grp * 256 + ch * 32;
-            tmem_ld32(ta, v);
-            if ((ch + 1) * 4 < g.rb) tmem_ld32(ta + 32, w);
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + grp * 256 + ch * 32, v);
             tmem_wait_ld();
             pick4(v, c, &row[grp][4 * ch]);
-            if ((ch + 1) * 4 < g.rb) pick4(w, c, &row[grp][4 * ch + 4]);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) row[grp][4 * ch + u] = 0.f;
           }
         }
-        if (g.r2 > 0) {
-          uint32_t v[32], w[32];
-          const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + grp * 256 + 192;
-          tmem_ld32(ta, v);
-          if (g.r2 > 4) tmem_ld32(ta + 32, w);
-          tmem_wait_ld();
-          pick4(v, c, &row2[grp][0]);
-          if (g.r2 > 4) pick4(w, c, &row2[grp][4]);
-          else {
 #pragma unroll
-            for (int u = 4; u < 8; ++u) row2[grp][u] = 0.f;
+        for (int ch = 0; ch < 2; ++ch) {
+          if (g.r2 > 4 * ch) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + grp * 256 + 192 + ch * 32, v);
+            tmem_wait_ld();
+            pick4(v, c, &row2[grp][4 * ch]);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) row2[grp][4 * ch + u] = 0.f;
           }
         }
       }
@@ -480,26 +485,28 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
 #pragma unroll
       for (int grp = 0; grp < 2; ++grp) {
         const int64_t cell = (int64_t)k * g.n_chan + ch0 + grp * 8 + c;
-        // rows a = slot (all b >= a from D1) and a = slot2 (b >= a from D2)
-#pragma unroll
-        for (int pass = 0; pass < 2; ++pass) {
+        // row a of the packed outputs from the D1 row (a = slot, b in
+        // [0, rb)) or the D2 row (a = slot2, b in [16, 16 + r2)); the row
+        // values have compile-time indices, so the two passes are separate
+        // instantiations
+        auto emit = [&](auto pass_c, const float(&rv)[kGroupSlots], int nb) {
+          constexpr int pass = decltype(pass_c)::value;
+          constexpr int b0 = pass == 0 ? 0 : 16;
           const int a = pass == 0 ? slot : slot2;
-          if (pass == 1 && g.r2 == 0) continue;
-          if (a > N) continue;
-          const float* rv = pass == 0 ? row[grp] : row2[grp];
-          const int b0 = pass == 0 ? 0 : 16;
+          if (a > N) return;
           const int64_t sa = s->s_sum[grp][c][a];
           const float inva = s->s_inv[grp][c][a];
           if (g.corr && a < N) {
             float* dst = g.corr + cell * (int64_t)(N * (N + 1) / 2) + (a * N - a * (a - 1) / 2);
 #pragma unroll
-            for (int b = 0; b < kGroupSlots; ++b) {
-              if (b < a || b >= N || b < b0 || b - b0 >= (pass == 0 ? g.rb : g.r2)) continue;
+            for (int j = 0; j < kGroupSlots; ++j) {
+              const int b = b0 + j;
+              if (b < a || b >= N || j >= nb) continue;
               float r;
               if (b == a) {
                 r = 1.f;
               } else {
-                const int64_t cov = n * (int64_t)rv[b - b0] - sa * (int64_t)s->s_sum[grp][c][b];
+                const int64_t cov = n * (int64_t)rv[j] - sa * (int64_t)s->s_sum[grp][c][b];
                 r = (float)cov * inva * s->s_inv[grp][c][b];
               }
               dst[b - a] = r;
@@ -509,9 +516,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
             const int N1 = N + 1;
             int64_t* dst = g.sums + cell * (int64_t)(N1 * (N1 + 1) / 2) + (a * N1 - a * (a - 1) / 2);
 #pragma unroll
-            for (int b = 0; b < kGroupSlots; ++b) {
-              if (b < a || b > N || b < b0 || b - b0 >= (pass == 0 ? g.rb : g.r2)) continue;
-              const int64_t gab = (int64_t)rv[b - b0];
+            for (int j = 0; j < kGroupSlots; ++j) {
+              const int b = b0 + j;
+              if (b < a || b > N || j >= nb) continue;
+              const int64_t gab = (int64_t)rv[j];
               int64_t v;
               if (a == N) v = n;                                  // (N, N): sample count
               else if (b == N) v = gab + 128 * n;                 // S_a
@@ -519,6 +527,13 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
               dst[b - a] = v;
             }
           }
+        };
+        emit(std::integral_constant<int, 0>{}, row[grp], g.rb);
+        if (g.r2 > 0) {
+          float r2v[kGroupSlots];
+#pragma unroll
+          for (int j = 0; j < kGroupSlots; ++j) r2v[j] = j < 8 ? row2[grp][j] : 0.f;
+          emit(std::integral_constant<int, 1>{}, r2v, g.r2);
         }
       }
       named_sync(1, kEpiThreads);  // smem tables reused by the next item
@@ -613,7 +628,10 @@ cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int su
   cudaError_t e = cudaSuccess;
 #define MRAID_TC_LAUNCH(T, NF)                                                                   \
   do {                                                                                           \
-    const size_t smem = smem_bytes<TcCfg<T, NF>>(p.n_beam);                                      \
+    using C_ = TcCfg<T, NF>;                                                                     \
+    const int n_u8 = u8_ring_depth<C_>(p.n_beam, 0);                                             \
+    a.n_u8 = n_u8;                                                                               \
+    const size_t smem = smem_bytes<C_>(p.n_beam, n_u8);                                          \
     e = cudaFuncSetAttribute(gram_tc_kernel<T, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              (int)smem);                                                         \
     if (e == cudaSuccess && grid > 0)                                                            \

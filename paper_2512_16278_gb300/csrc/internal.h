@@ -77,6 +77,12 @@ struct mraid_plan_s {
   mraid::Profiler prof;
   bool force_dp4a = false;  // use the CUDA-core Gram even where tcgen05 fits
   int tc_variant = 0;       // tensor-core Gram tile variant (autotuned)
+  int eig_variant = 3;      // register kernels: 0 = Jacobi, looped rounds; 1 = Jacobi,
+                            // unrolled sweep; 2 = Householder + implicit QR, one
+                            // step copy per level; 3 = the same, one masked copy
+  double* d_refine_part = nullptr;   // eigenvector refinement: [sm][N][3]
+  float* d_refine_thresh = nullptr;  // [N]
+  double* d_refine_ms = nullptr;     // [N][2] when the caller passes none
 };
 
 namespace mraid {
@@ -88,8 +94,8 @@ mraid_status plan_prepare(mraid_plan_s* pl);
 // Copy the staged mraid_flag_info to the caller's struct (stream synced).
 void plan_deliver_info(mraid_plan_s* pl);
 // Bracket a kernel launch with profiling events (no-ops unless enabled).
-void prof_begin(mraid_plan_s* pl, int id, cudaEvent_t* start);
-void prof_end(mraid_plan_s* pl, int id, cudaEvent_t start);
+void prof_begin(mraid_plan_s* pl, int id, cudaEvent_t* start, cudaStream_t stream);
+void prof_end(mraid_plan_s* pl, int id, cudaEvent_t start, cudaStream_t stream);
 mraid_status cuda_fail(cudaError_t e, const char* what);
 
 // gram.cu
@@ -97,11 +103,15 @@ mraid_status cuda_fail(cudaError_t e, const char* what);
 // by cell relative to sub0 (cell = (sub - sub0) * n_chan + chan).
 cudaError_t launch_gram_u8(const mraid_plan_s* pl, const uint8_t* d_data,
                            int sub0, int n_sub, int64_t* d_sums);
+// float32 samples: correlation on CUDA cores (d_corr relative to sub0)
+cudaError_t launch_gram_f32(const mraid_plan_s* pl, const float* d_data, int sub0, int n_sub,
+                            float* d_corr);
 // tensor-core Gram fused with the correlation (gram_tc.cu); either output
 // may be null. cudaErrorNotSupported when the shape or layout does not fit.
 bool gram_tc_supported(const mraid_plan_s* pl, const void* d_data);
 int tc_variant_samples(int v);
 constexpr int kTcVariants = 3;
+constexpr int kEigVariants = 4;  // register eigensolvers (see eig_variant)
 cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int sub0, int n_sub,
                            int64_t* d_sums, float* d_corr);
 cudaError_t launch_corr_from_sums(const mraid_plan_s* pl, const int64_t* d_sums,
@@ -109,9 +119,15 @@ cudaError_t launch_corr_from_sums(const mraid_plan_s* pl, const int64_t* d_sums,
 // eig.cu
 cudaError_t launch_eig(const mraid_plan_s* pl, const float* d_corr, int64_t n_cells,
                        float* d_evals, float* d_q1, float* d_stat);
+// the same on another stream of the plan's device
+cudaError_t launch_eig(const mraid_plan_s* pl, const float* d_corr, int64_t n_cells,
+                       float* d_evals, float* d_q1, float* d_stat, cudaStream_t stream);
 bool eig_supported(int n_beam);
 // true if a q1 request needs d_evals (the q1 pass reads lambda_1 from it)
 bool eig_q1_needs_evals(int n_beam);
+// refine.cu
+cudaError_t launch_refine(mraid_plan_s* pl, const float* d_q1, const uint8_t* d_flags,
+                          uint32_t* d_bits, double* d_mu_sigma);
 // flag.cu
 cudaError_t launch_flag(mraid_plan_s* pl, const float* d_stat, uint8_t* d_flags);
 int flag_grid_blocks(int device, int sm_count);

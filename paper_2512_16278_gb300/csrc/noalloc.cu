@@ -51,6 +51,10 @@ extern "C" mraid_status mraid_ccm_noalloc(const mraid_params* p, const void* d_d
                                           int32_t n_sub, float* d_corr, void* stream) {
   mraid_status st = mraid_validate(p);
   if (st != MRAID_OK) return st;
+  if (p->bit_depth != 8) {
+    set_error("mraid_ccm_noalloc: 8-bit samples only");
+    return MRAID_ERR_UNSUPPORTED;
+  }
   if (!d_data || !d_corr) {
     set_error("mraid_ccm_noalloc: d_data and d_corr are required");
     return MRAID_ERR_INVALID_ARG;

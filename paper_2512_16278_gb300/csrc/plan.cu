@@ -31,7 +31,7 @@ const char* kernel_name(int id) {
   switch (id) {
     case K_GRAM: return "gram_u8";
     case K_CORR: return "corr_from_sums";
-    case K_EIG: return "eig_jacobi";
+    case K_EIG: return "eig";
     case K_FLAG: return "flag_clip";
     case K_GRAM_TC: return "gram_tc";
   }
@@ -49,19 +49,19 @@ static cudaEvent_t take_event(mraid_plan_s* pl) {
   return e;
 }
 
-void prof_begin(mraid_plan_s* pl, int id, cudaEvent_t* start) {
+void prof_begin(mraid_plan_s* pl, int id, cudaEvent_t* start, cudaStream_t stream) {
   (void)id;
   *start = nullptr;
   if (!pl->prof.on) return;
   *start = take_event(pl);
-  if (*start) cudaEventRecord(*start, pl->stream);
+  if (*start) cudaEventRecord(*start, stream);
 }
 
-void prof_end(mraid_plan_s* pl, int id, cudaEvent_t start) {
+void prof_end(mraid_plan_s* pl, int id, cudaEvent_t start, cudaStream_t stream) {
   if (!pl->prof.on || !start) return;
   cudaEvent_t stop = take_event(pl);
   if (!stop) return;
-  cudaEventRecord(stop, pl->stream);
+  cudaEventRecord(stop, stream);
   pl->prof.pending.push_back({id, start, stop});
 }
 
@@ -79,14 +79,15 @@ static void prof_fold(mraid_plan_s* pl) {
   pl->prof.pending.clear();
 }
 
-#define MRAID_PROF(pl, id, expr)          \
-  ([&]() {                                \
-    cudaEvent_t s_;                       \
-    prof_begin((pl), (id), &s_);          \
-    cudaError_t e_ = (expr);              \
-    prof_end((pl), (id), s_);             \
-    return e_;                            \
+#define MRAID_PROF_ON(pl, id, stream, expr)   \
+  ([&]() {                                    \
+    cudaEvent_t s_;                           \
+    prof_begin((pl), (id), &s_, (stream));    \
+    cudaError_t e_ = (expr);                  \
+    prof_end((pl), (id), s_, (stream));       \
+    return e_;                                \
   }())
+#define MRAID_PROF(pl, id, expr) MRAID_PROF_ON(pl, id, (pl)->stream, expr)
 
 namespace {
 
@@ -118,6 +119,9 @@ mraid_status evals_for_q1(mraid_plan_s* pl, size_t cells, float** evals) {
   if (*evals || !eig_q1_needs_evals(pl->p.n_beam)) return MRAID_OK;
   if (pl->ws.evals_cells < cells) {
     cudaFree(pl->ws.evals);
+  cudaFree(pl->d_refine_part);
+  cudaFree(pl->d_refine_thresh);
+  cudaFree(pl->d_refine_ms);
     pl->ws.evals = nullptr;
     pl->ws.evals_cells = 0;
     cudaError_t e = cudaMalloc(&pl->ws.evals, cells * (size_t)pl->p.n_beam * sizeof(float));
@@ -152,6 +156,21 @@ mraid_status check_plan(mraid_plan_t pl) {
 mraid_status ccm_range(mraid_plan_s* pl, const void* d_data, int sub0, int n_sub, int64_t* d_sums,
                        float* d_corr) {
   const int64_t cells = (int64_t)n_sub * pl->p.n_chan;
+  if (pl->p.bit_depth == 32) {
+    if (d_sums) {
+      set_error("exact sums exist for 8-bit data only");
+      return MRAID_ERR_INVALID_ARG;
+    }
+    if (!d_corr) return MRAID_OK;
+    for (int s = 0; s < n_sub; s += kMaxSubPerLaunch) {
+      const int ns = (n_sub - s) < kMaxSubPerLaunch ? (n_sub - s) : kMaxSubPerLaunch;
+      cudaError_t e = MRAID_PROF(pl, K_GRAM,
+                                 launch_gram_f32(pl, static_cast<const float*>(d_data), sub0 + s, ns,
+                                                 d_corr + (int64_t)s * pl->p.n_chan * pl->np));
+      if (e != cudaSuccess) return cuda_fail(e, "gram_f32 launch");
+    }
+    return MRAID_OK;
+  }
   if (!pl->force_dp4a && gram_tc_supported(pl, d_data)) {
     cudaError_t e = MRAID_PROF(pl, K_GRAM_TC,
                                launch_gram_tc(pl, static_cast<const uint8_t*>(d_data), sub0, n_sub,
@@ -202,6 +221,27 @@ void plan_deliver_info(mraid_plan_s* pl) {
   }
 }
 
+}  // namespace mraid
+
+namespace mraid {
+namespace {
+// Mean time of `reps` runs of fn on the plan's stream (after one warm-up).
+template <class F>
+mraid_status time_runs(mraid_plan_s* pl, int reps, cudaEvent_t e0, cudaEvent_t e1, F fn,
+                       float* ms) {
+  mraid_status st = fn();
+  if (st != MRAID_OK) return st;
+  cudaError_t e = cudaEventRecord(e0, pl->stream);
+  for (int r = 0; r < reps && st == MRAID_OK && e == cudaSuccess; ++r) st = fn();
+  if (st != MRAID_OK) return st;
+  if (e == cudaSuccess) e = cudaEventRecord(e1, pl->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  if (e != cudaSuccess) return cuda_fail(e, "mraid_autotune");
+  *ms /= reps;
+  return MRAID_OK;
+}
+}  // namespace
 }  // namespace mraid
 
 using namespace mraid;
@@ -263,8 +303,8 @@ mraid_status mraid_validate(const mraid_params* p) {
     set_error("n_samp_sub %d outside [2, %d]", p->n_samp_sub, kMaxSampSub);
     return MRAID_ERR_INVALID_ARG;
   }
-  if (p->bit_depth != 8) {
-    set_error("bit_depth %d: only 8-bit samples are built", p->bit_depth);
+  if (p->bit_depth != 8 && p->bit_depth != 32) {
+    set_error("bit_depth %d: 8-bit and float32 samples are built", p->bit_depth);
     return MRAID_ERR_UNSUPPORTED;
   }
   const int64_t dense = (int64_t)p->n_sub * p->n_samp_sub * p->n_chan;
@@ -384,6 +424,25 @@ mraid_status mraid_flag(mraid_plan_t pl, const float* d_stat, uint8_t* d_flags,
   return enqueue_info_copy(pl, info);
 }
 
+mraid_status mraid_refine(mraid_plan_t pl, const float* d_q1, const uint8_t* d_flags,
+                          uint32_t* d_beam_bits, double* d_mu_sigma) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  if (!d_q1 || !d_flags || !d_beam_bits) {
+    set_error("mraid_refine: d_q1, d_flags and d_beam_bits are required");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!pl->d_refine_part) {
+    e = cudaMalloc(&pl->d_refine_part, sizeof(double) * 3 * (size_t)pl->sm_count * kMaxBeam);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_refine_thresh, sizeof(float) * kMaxBeam);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_refine_ms, sizeof(double) * 2 * kMaxBeam);
+    if (e != cudaSuccess) return cuda_fail(e, "refine buffers");
+  }
+  e = launch_refine(pl, d_q1, d_flags, d_beam_bits, d_mu_sigma ? d_mu_sigma : pl->d_refine_ms);
+  return e == cudaSuccess ? MRAID_OK : cuda_fail(e, "refine launch");
+}
+
 mraid_status mraid_run(mraid_plan_t pl, const void* d_data, float* d_evals, float* d_q1,
                        float* d_stat, uint8_t* d_flags, mraid_flag_info* info) {
   mraid_status st = check_plan(pl);
@@ -398,12 +457,12 @@ mraid_status mraid_run(mraid_plan_t pl, const void* d_data, float* d_evals, floa
   if (e == cudaSuccess)
     e = cudaMemsetAsync(pl->d_sweeps, 0, 2 * sizeof(unsigned long long), pl->stream);
   if (e != cudaSuccess) return cuda_fail(e, "memset");
-  st = ccm_range(pl, d_data, 0, pl->p.n_sub, nullptr, pl->ws.corr);
-  if (st != MRAID_OK) return st;
   if (d_q1) {
     st = evals_for_q1(pl, (size_t)pl->n_cells, &d_evals);
     if (st != MRAID_OK) return st;
   }
+  st = ccm_range(pl, d_data, 0, pl->p.n_sub, nullptr, pl->ws.corr);
+  if (st != MRAID_OK) return st;
   e = MRAID_PROF(pl, K_EIG, launch_eig(pl, pl->ws.corr, pl->n_cells, d_evals, d_q1, d_stat));
   if (e != cudaSuccess) return cuda_fail(e, "eig launch");
   e = MRAID_PROF(pl, K_FLAG, launch_flag(pl, d_stat, d_flags));
@@ -423,10 +482,6 @@ mraid_status mraid_run_host(mraid_plan_t pl, const void* h_data, float* h_stat, 
   if (st != MRAID_OK) return st;
   if (!h_data || !h_flags) {
     set_error("mraid_run_host: h_data and h_flags are required");
-    return MRAID_ERR_INVALID_ARG;
-  }
-  if (pl->beam_stride != (int64_t)pl->p.n_sub * pl->p.n_samp_sub * pl->p.n_chan) {
-    set_error("mraid_run_host: host blocks must be dense (beam_stride 0)");
     return MRAID_ERR_INVALID_ARG;
   }
   const size_t esz = pl->p.bit_depth == 8 ? 1 : 4;
@@ -552,61 +607,101 @@ mraid_status mraid_set_variant(mraid_plan_t pl, int32_t variant) {
   return MRAID_OK;
 }
 
-mraid_status mraid_autotune(mraid_plan_t pl, const void* d_data, int32_t reps, int32_t* choice,
-                            char* report, int32_t report_len) {
+mraid_status mraid_set_eig_variant(mraid_plan_t pl, int32_t variant) {
   mraid_status st = check_plan(pl);
   if (st != MRAID_OK) return st;
-  if (!d_data || !choice || reps < 1 || reps > 1000 || (report && report_len < 1)) {
+  if (variant < 0 || variant >= kEigVariants) {
+    set_error("mraid_set_eig_variant: variant %d outside [0, %d)", variant, kEigVariants);
+    return MRAID_ERR_INVALID_ARG;
+  }
+  pl->eig_variant = variant;
+  return MRAID_OK;
+}
+
+
+mraid_status mraid_autotune(mraid_plan_t pl, const void* d_data, int32_t reps, int32_t* gram_choice,
+                            int32_t* eig_choice, char* report, int32_t report_len) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  if (!d_data || !gram_choice || !eig_choice || reps < 1 || reps > 1000 ||
+      (report && report_len < 1)) {
     set_error("mraid_autotune: bad arguments");
     return MRAID_ERR_INVALID_ARG;
   }
   st = ensure_workspace(pl, (size_t)pl->n_cells);
   if (st != MRAID_OK) return st;
+  float* stat = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  if (e != cudaSuccess) return cuda_fail(e, "mraid_autotune");
+  if (e == cudaSuccess) e = cudaMalloc(&stat, sizeof(float) * (size_t)pl->n_cells);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return cuda_fail(e, "mraid_autotune");
+  }
+  int used = 0;
+  if (report) report[0] = 0;
+  auto note = [&](char tag, int v, float ms) {
+    if (report && used < report_len - 1)
+      used += snprintf(report + used, (size_t)(report_len - used), "%c%d:%.4f;", tag, v, ms);
+  };
+  // Gram stage
   const bool save_dp4a = pl->force_dp4a;
   const int save_v = pl->tc_variant;
   float best = 1e30f;
-  int best_v = -2;
-  int used = 0;
-  if (report) report[0] = 0;
+  int best_g = -2;
   for (int v = -1; v < kTcVariants && st == MRAID_OK; ++v) {
     pl->force_dp4a = v < 0;
     pl->tc_variant = v < 0 ? 0 : v;
     if (v >= 0 && !gram_tc_supported(pl, d_data)) continue;
-    st = ccm_range(pl, d_data, 0, pl->p.n_sub, nullptr, pl->ws.corr);  // warm-up
-    if (st != MRAID_OK) break;
-    e = cudaEventRecord(e0, pl->stream);
-    for (int r = 0; r < reps && st == MRAID_OK && e == cudaSuccess; ++r)
-      st = ccm_range(pl, d_data, 0, pl->p.n_sub, nullptr, pl->ws.corr);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, pl->stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e != cudaSuccess) {
-      st = cuda_fail(e, "mraid_autotune");
-      break;
-    }
-    ms /= reps;
-    if (report && used < report_len - 1)
-      used += snprintf(report + used, (size_t)(report_len - used), "%d:%.4f;", v, ms);
+    st = time_runs(pl, reps, e0, e1,
+                   [&] { return ccm_range(pl, d_data, 0, pl->p.n_sub, nullptr, pl->ws.corr); }, &ms);
+    if (st != MRAID_OK) break;
+    note('g', v, ms);
     if (ms < best) {
       best = ms;
-      best_v = v;
+      best_g = v;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (st != MRAID_OK || best_v < -1) {
+  if (st == MRAID_OK && best_g >= -1) {
+    pl->force_dp4a = best_g < 0;
+    pl->tc_variant = best_g < 0 ? 0 : best_g;
+  } else {
     pl->force_dp4a = save_dp4a;
     pl->tc_variant = save_v;
-    return st != MRAID_OK ? st : MRAID_ERR_UNSUPPORTED;
   }
-  pl->force_dp4a = best_v < 0;
-  pl->tc_variant = best_v < 0 ? 0 : best_v;
-  *choice = best_v;
+  // Jacobi stage on the correlations just computed
+  int best_e = pl->eig_variant;
+  if (st == MRAID_OK) {
+    best = 1e30f;
+    for (int v = 0; v < kEigVariants && st == MRAID_OK; ++v) {
+      pl->eig_variant = v;
+      float ms = 0.f;
+      st = time_runs(pl, reps, e0, e1,
+                     [&]() -> mraid_status {
+                       cudaError_t le = launch_eig(pl, pl->ws.corr, pl->n_cells, nullptr, nullptr, stat);
+                       return le == cudaSuccess ? MRAID_OK : cuda_fail(le, "eig launch");
+                     },
+                     &ms);
+      if (st != MRAID_OK) break;
+      note('e', v, ms);
+      if (ms < best) {
+        best = ms;
+        best_e = v;
+      }
+    }
+    pl->eig_variant = best_e;
+  }
+  cudaStreamSynchronize(pl->stream);
+  cudaFree(stat);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != MRAID_OK) return st;
+  if (best_g < -1) return MRAID_ERR_UNSUPPORTED;
+  *gram_choice = best_g;
+  *eig_choice = best_e;
   return MRAID_OK;
 }
 
@@ -665,11 +760,15 @@ void mraid_destroy(mraid_plan_t pl) {
   }
   prof_fold(pl);
   for (cudaEvent_t ev : pl->prof.pool) cudaEventDestroy(ev);
+
   cudaFree(pl->d_stat_full);
   cudaFree(pl->d_flags_full);
   cudaFree(pl->ws.sums);
   cudaFree(pl->ws.corr);
   cudaFree(pl->ws.evals);
+  cudaFree(pl->d_refine_part);
+  cudaFree(pl->d_refine_thresh);
+  cudaFree(pl->d_refine_ms);
   cudaFree(pl->d_keep);
   cudaFree(pl->d_partials);
   cudaFree(pl->d_info);

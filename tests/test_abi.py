@@ -90,3 +90,14 @@ def test_null_plan_calls_are_rejected(lib):
     assert lib.mraid_ccm(None, None, None, None) == 1
     assert lib.mraid_sync(None) == 1
     lib.mraid_destroy(None)                    # no-op
+
+
+def test_binding_rejects_non_contiguous_buffers():
+    """A strided view would be read as if it were dense: refuse it."""
+    import torch
+    import paper_2512_16278_gb300 as m
+    t = torch.zeros(6, 4)
+    assert m._ptr(t) == t.data_ptr()
+    assert m._ptr(None) is None and m._ptr(1234) == 1234
+    with pytest.raises(ValueError):
+        m._ptr(t.t())
