@@ -205,18 +205,48 @@ def cpu_baseline(cfg, h_ptr, seconds):
         subs = (idx // cfg.n_chan).astype(np.int32)
         chans = (idx % cfg.n_chan).astype(np.int32)
         t0 = time.perf_counter()
-        oracle.cells(None, cfg.n_samp_sub, subs, chans, n_threads=threads, data_ptr=h_ptr,
-                     shape=shape)
-        return time.perf_counter() - t0
+        res = oracle.cells(None, cfg.n_samp_sub, subs, chans, n_threads=threads, data_ptr=h_ptr,
+                           shape=shape)
+        return time.perf_counter() - t0, idx, res
 
     n = threads * 4
-    t = run(n)
+    t, _, _ = run(n)
     n2 = max(threads, int(n * max(seconds - t, 0.5) / max(t, 1e-6)))
-    t2 = run(n2)
+    t2, idx, res = run(n2)
     return {"value": n2 / t2, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{n2} random cells of the same block (per-cell Gram, FP64 Jacobi, "
                       f"statistic; {t2:.1f} s on {threads} threads); the mask pass is "
-                      "excluded (it is O(cells) and negligible)"}
+                      "excluded (it is O(cells) and negligible)"}, (idx, res)
+
+
+def sampled_parity(sample, evals, q1, stat):
+    """GPU outputs of the timed run against the oracle on the sampled cells
+    (the bench's own parity check at full size, same tolerances as the
+    tests: eigenvalues 1e-4 of lambda_max, s 2e-4 relative, q1 1e-3 where
+    the relative gap is at least 1e-2)."""
+    import numpy as np
+    idx, res = sample
+    it = torch_index(idx)
+    ev = evals.index_select(0, it.to(evals.device)).cpu().numpy().astype(np.float64)
+    qv = q1.index_select(0, it.to(q1.device)).cpu().numpy().astype(np.float64)
+    sv = stat.index_select(0, it.to(stat.device)).cpu().numpy().astype(np.float64)
+    eo, qo, so = res["evals"], res["q1"], res["stat"]
+    lmax = np.abs(eo).max(axis=1)
+    e_err = (np.abs(ev - eo).max(axis=1) / lmax)
+    s_err = np.abs(sv - so) / np.maximum(so, 1e-30)
+    gap = (eo[:, 0] - eo[:, 1]) / eo[:, 0]
+    sel = gap >= 1e-2
+    q_err = np.abs(qv[sel] - qo[sel]).max(axis=1) if sel.any() else np.zeros(1)
+    return {"cells": int(len(idx)), "eig_err_rel_max": float(e_err.max()),
+            "eig_err_rel_p99": float(np.percentile(e_err, 99)),
+            "stat_err_rel_max": float(s_err.max()), "q1_err_max": float(q_err.max()),
+            "q1_cells": int(sel.sum()),
+            "pass": bool(e_err.max() <= 1e-4 and s_err.max() <= 2e-4 and q_err.max() <= 1e-3)}
+
+
+def torch_index(idx):
+    import torch
+    return torch.from_numpy(idx.astype("int64"))
 
 
 # ------------------------------------------------------------- main arms
@@ -380,7 +410,7 @@ def run_reference(args):
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     vals = []
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(cfg, h.data_ptr(), per_step)
+        r, _ = cpu_baseline(cfg, h.data_ptr(), per_step)
         if i >= args.warmup:
             vals.append(r["value"])
     v = statistics.median(vals)
@@ -527,9 +557,10 @@ def run_mraid(args):
                "d2h_bytes_per_step": cells * 5, "ms_per_step": te * 1000.0,
                "api": "mraid_run_host (pinned host input, stat + flags copied back)"}
 
-    cpu = None
+    cpu = parity = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(cfg, h.data_ptr(), args.cpu_seconds)
+        cpu, sample = cpu_baseline(cfg, h.data_ptr(), args.cpu_seconds)
+        parity = sampled_parity(sample, evals, q1, stat)
     plan.close()
     del d, h
     torch.cuda.empty_cache()
@@ -557,6 +588,7 @@ def run_mraid(args):
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "sampled_parity": parity,
             "mask": {"flagged_fraction": info.n_flagged / cells, "iterations": info.iterations,
                      "threshold": info.thresh, "n_near": info.n_near},
             "variants": {"gram": variants[0], "eig": variants[1],

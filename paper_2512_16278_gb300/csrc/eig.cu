@@ -128,6 +128,27 @@ __device__ __forceinline__ void sts(uint32_t addr, float v) {
   asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
 
+// Copy the packed matrices of a block's cells from global memory into
+// per-thread shared-memory rows of STR floats. Asynchronous copies keep
+// many loads in flight; a plain load-then-store loop waits out the memory
+// latency once per element.
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+template <int NP, int STR>
+__device__ __forceinline__ void stage_rows(float* sm, const float* __restrict__ src, int ncell) {
+  const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(sm));
+  for (int i = threadIdx.x; i < ncell * NP; i += blockDim.x) {
+    const int c = i / NP;
+    cp_async4(base + 4u * (uint32_t)(c * STR + (i - c * NP)), src + i);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+}
+
 __device__ __forceinline__ void rotation(float app, float aqq, float apq, float& c, float& s,
                                          float& t) {
   // t = tan(theta) of the rotation zeroing apq (smaller root of
@@ -355,12 +376,7 @@ eig_reg_kernel(const float* __restrict__ corr, int64_t n_cells, float* __restric
   extern __shared__ float sm[];
   const int64_t cell0 = (int64_t)blockIdx.x * kEigThreads;
   const int ncell = (int)min((int64_t)kEigThreads, n_cells - cell0);
-  const float* src = corr + cell0 * NP;
-  for (int i = threadIdx.x; i < ncell * NP; i += blockDim.x) {
-    const int c = i / NP;
-    sm[c * STR + (i - c * NP)] = src[i];
-  }
-  __syncthreads();
+  stage_rows<NP, STR>(sm, corr + cell0 * NP, ncell);
   const bool active = (int)threadIdx.x < ncell;
   const float* my = sm + threadIdx.x * STR;
   float a[NP];
@@ -447,12 +463,7 @@ q1_reg_kernel(const float* __restrict__ corr, int64_t n_cells, const float* __re
   extern __shared__ float sm[];
   const int64_t cell0 = (int64_t)blockIdx.x * kEigThreads;
   const int ncell = (int)min((int64_t)kEigThreads, n_cells - cell0);
-  const float* src = corr + cell0 * NP;
-  for (int i = threadIdx.x; i < ncell * NP; i += blockDim.x) {
-    const int c = i / NP;
-    sm[c * STR + (i - c * NP)] = src[i];
-  }
-  __syncthreads();
+  stage_rows<NP, STR>(sm, corr + cell0 * NP, ncell);
   if ((int)threadIdx.x >= ncell) return;
   const int64_t cell = cell0 + threadIdx.x;
   float x[N];
@@ -531,12 +542,7 @@ eig_tri_kernel(const float* __restrict__ corr, int64_t n_cells, float* __restric
   extern __shared__ float sm[];
   const int64_t cell0 = (int64_t)blockIdx.x * kEigThreads;
   const int ncell = (int)min((int64_t)kEigThreads, n_cells - cell0);
-  const float* src = corr + cell0 * NP;
-  for (int i = threadIdx.x; i < ncell * NP; i += blockDim.x) {
-    const int c = i / NP;
-    sm[c * STR + (i - c * NP)] = src[i];
-  }
-  __syncthreads();
+  stage_rows<NP, STR>(sm, corr + cell0 * NP, ncell);
   const bool active = (int)threadIdx.x < ncell;
   float* row = sm + threadIdx.x * STR;
   const uint32_t rowa = static_cast<uint32_t>(__cvta_generic_to_shared(row));
@@ -799,7 +805,9 @@ eig_warp_kernel(const float* __restrict__ corr, int64_t n_cells, int N, float* _
   for (int64_t cell = (int64_t)blockIdx.x * kWarpEigWarps + w; cell < n_cells;
        cell += (int64_t)gridDim.x * kWarpEigWarps) {
     const float* src = corr + cell * NP;
-    for (int e = lane; e < NP; e += 32) A[e] = src[e];
+    const uint32_t abase = static_cast<uint32_t>(__cvta_generic_to_shared(A));
+    for (int e = lane; e < NP; e += 32) cp_async4(abase + 4u * e, src + e);
+    cp_async_wait_all();
     __syncwarp();
     int sweeps = 0;
     for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
