@@ -649,25 +649,26 @@ eig_tri_kernel(const float* __restrict__ corr, int64_t n_cells, float* __restric
     // one copy of the step over the whole length, masked to each lane's
     // unreduced block [l, m]: lanes deflate at their own pace
     for (int it = 0; it < kMaxQrIter * (N - 1); ++it) {
-      int m = 0;  // bottom of the lowest unreduced block
+      // one pass from the top: m is one past the last non-negligible e
+      // (the bottom of the lowest unreduced block), l one past the last
+      // negligible e above it (its top)
+      int m = 0, l = 0, last_small = 0;
+      float dm1 = 0.f, dm = 0.f, em = 0.f;
       static_for<N - 1>([&](auto ii) {
         constexpr int i = decltype(ii)::value;
-        if (e[i] * e[i] > thr2) m = i + 1;
+        if (e[i] * e[i] > thr2) {
+          m = i + 1;
+          l = last_small;
+          dm1 = d[i];
+          dm = d[i + 1];
+          em = e[i];
+        } else {
+          last_small = i + 1;
+        }
       });
       const bool need = active && m > 0;
       if (!__any_sync(0xffffffffu, need)) break;
       if (need) {
-        int l = 0;
-        float dm1 = 0.f, dm = 0.f, em = 0.f;
-        static_for<N - 1>([&](auto ii) {
-          constexpr int i = decltype(ii)::value;
-          if (i < m - 1 && e[i] * e[i] <= thr2) l = i + 1;
-          if (i + 1 == m) {
-            dm1 = d[i];
-            dm = d[i + 1];
-            em = e[i];
-          }
-        });
         qr_step<N>(d, e, l, m, dm1, dm, em);
         ++steps;
       }
@@ -1094,6 +1095,12 @@ cudaError_t launch_reg(const float* d_corr, int64_t n_cells, float* d_evals, flo
 
 bool eig_supported(int n_beam) { return n_beam >= 2 && n_beam <= kMaxBeam; }
 
+bool eig_needs_tri_workspace(const mraid_plan_s* pl) {
+  const int N = pl->p.n_beam;
+  const bool reg = N == 2 || N == 3 || N == 4 || N == 13 || N == 19;
+  return !reg && pl->eig_variant >= 2;
+}
+
 bool eig_q1_needs_evals(int n_beam) {
   return n_beam == 2 || n_beam == 3 || n_beam == 4 || n_beam == 13 || n_beam == 19;
 }
@@ -1108,6 +1115,10 @@ cudaError_t launch_eig(const mraid_plan_s* pl, const float* d_corr, int64_t n_ce
     case 13: return launch_reg<13>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->d_sweeps, pl->eig_variant, pl->sm_count, stream);
     case 19: return launch_reg<19>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->d_sweeps, pl->eig_variant, pl->sm_count, stream);
     default: break;
+  }
+  if (eig_needs_tri_workspace(pl)) {
+    if (!pl->ws.tri || pl->ws.tri_cells < (size_t)n_cells) return cudaErrorInvalidValue;
+    return launch_eig_large(pl, d_corr, n_cells, d_evals, d_q1, d_stat, pl->ws.tri, stream);
   }
   const int M = (N & 1) ? N + 1 : N, H = M / 2, NP = N * (N + 1) / 2;
   const size_t smem = sizeof(float) * (size_t)kWarpEigWarps * (NP + 4 * H + 2 * N + 32);

@@ -42,6 +42,8 @@ struct Workspace {
   size_t cells = 0;
   float* evals = nullptr;   // [cell][N] when q1 is wanted without eigenvalues
   size_t evals_cells = 0;
+  float* tri = nullptr;     // [cell][tri_workspace_floats(N)]: larger-N eigensolver
+  size_t tri_cells = 0;
 };
 
 }  // namespace mraid
@@ -123,6 +125,14 @@ cudaError_t launch_eig(const mraid_plan_s* pl, const float* d_corr, int64_t n_ce
 cudaError_t launch_eig(const mraid_plan_s* pl, const float* d_corr, int64_t n_cells,
                        float* d_evals, float* d_q1, float* d_stat, cudaStream_t stream);
 bool eig_supported(int n_beam);
+// eig_large.cu: tridiagonal eigensolver for beam counts without a
+// one-thread kernel; d_work holds tri_workspace_floats(N) floats per cell
+size_t tri_workspace_floats(int n_beam);
+cudaError_t launch_eig_large(const mraid_plan_s* pl, const float* d_corr, int64_t n_cells,
+                             float* d_evals, float* d_q1, float* d_stat, float* d_work,
+                             cudaStream_t stream);
+// true if the plan's eigensolver needs the tridiagonal workspace
+bool eig_needs_tri_workspace(const mraid_plan_s* pl);
 // true if a q1 request needs d_evals (the q1 pass reads lambda_1 from it)
 bool eig_q1_needs_evals(int n_beam);
 // refine.cu

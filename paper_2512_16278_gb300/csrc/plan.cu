@@ -94,7 +94,27 @@ namespace {
 // Sub-integrations per gram launch (grid.y bound) and per host-path chunk.
 constexpr int kMaxSubPerLaunch = 32768;
 
+// Workspace of the tridiagonal eigensolver, for beam counts it serves.
+mraid_status ensure_tri_workspace(mraid_plan_s* pl, size_t cells) {
+  const int N = pl->p.n_beam;
+  const bool reg = N == 2 || N == 3 || N == 4 || N == 13 || N == 19;
+  if (reg || pl->ws.tri_cells >= cells) return MRAID_OK;
+  cudaFree(pl->ws.tri);
+  pl->ws.tri = nullptr;
+  pl->ws.tri_cells = 0;
+  cudaError_t e = cudaMalloc(&pl->ws.tri, cells * tri_workspace_floats(N) * sizeof(float));
+  if (e != cudaSuccess) {
+    pl->ws.tri = nullptr;
+    cudaGetLastError();
+    return cuda_fail(e, "eigensolver workspace");
+  }
+  pl->ws.tri_cells = cells;
+  return MRAID_OK;
+}
+
 mraid_status ensure_workspace(mraid_plan_s* pl, size_t cells) {
+  mraid_status st = ensure_tri_workspace(pl, cells);
+  if (st != MRAID_OK) return st;
   if (pl->ws.cells >= cells) return MRAID_OK;
   cudaFree(pl->ws.sums);
   cudaFree(pl->ws.corr);
@@ -119,9 +139,6 @@ mraid_status evals_for_q1(mraid_plan_s* pl, size_t cells, float** evals) {
   if (*evals || !eig_q1_needs_evals(pl->p.n_beam)) return MRAID_OK;
   if (pl->ws.evals_cells < cells) {
     cudaFree(pl->ws.evals);
-  cudaFree(pl->d_refine_part);
-  cudaFree(pl->d_refine_thresh);
-  cudaFree(pl->d_refine_ms);
     pl->ws.evals = nullptr;
     pl->ws.evals_cells = 0;
     cudaError_t e = cudaMalloc(&pl->ws.evals, cells * (size_t)pl->p.n_beam * sizeof(float));
@@ -407,6 +424,8 @@ mraid_status mraid_eig(mraid_plan_t pl, const float* d_corr, float* d_evals, flo
     st = evals_for_q1(pl, (size_t)pl->n_cells, &d_evals);
     if (st != MRAID_OK) return st;
   }
+  st = ensure_tri_workspace(pl, (size_t)pl->n_cells);
+  if (st != MRAID_OK) return st;
   cudaError_t e = MRAID_PROF(pl, K_EIG, launch_eig(pl, d_corr, pl->n_cells, d_evals, d_q1, d_stat));
   return e == cudaSuccess ? MRAID_OK : cuda_fail(e, "eig launch");
 }
@@ -766,6 +785,7 @@ void mraid_destroy(mraid_plan_t pl) {
   cudaFree(pl->ws.sums);
   cudaFree(pl->ws.corr);
   cudaFree(pl->ws.evals);
+  cudaFree(pl->ws.tri);
   cudaFree(pl->d_refine_part);
   cudaFree(pl->d_refine_thresh);
   cudaFree(pl->d_refine_ms);

@@ -68,3 +68,36 @@ def test_eig_variant_matches_oracle(N, variant):
     # closed forms: rank one gives (N, 0, ...), the identity all ones
     assert np.abs(ev[0::8, 0] - N).max() <= 1e-4 * N
     assert np.abs(ev[1::8] - 1.0).max() <= 1e-4
+
+
+@pytest.mark.parametrize("N", [5, 8, 36, 72, 128])
+@pytest.mark.parametrize("variant", [0, 3])
+def test_large_beam_counts_match_oracle(N, variant):
+    """Beam counts without a one-thread kernel: warp-per-matrix Jacobi
+    (variant 0) and the tridiagonal solver (Householder by a warp, QR by a
+    thread, back-transform by a warp; the default)."""
+    import torch
+    m = lib()
+    n_chan, n_sub = 16, 6
+    cells = n_chan * n_sub
+    R = structured_corrs(N, cells, 300 + N)
+    iu = np.triu_indices(N)
+    packed = np.ascontiguousarray(R[:, iu[0], iu[1]], dtype=np.float32)
+    R32 = np.zeros_like(R)
+    R32[:, iu[0], iu[1]] = packed
+    R32[:, iu[1], iu[0]] = packed
+    ev_o = np.zeros((cells, N))
+    q1_o = np.zeros((cells, N))
+    st_o = np.zeros(cells)
+    for c in range(cells):
+        ev_o[c], q1_o[c], _ = oracle.jacobi(R32[c])
+        st_o[c] = oracle.stat(ev_o[c])
+    with m.Plan(N, n_chan, 64, n_sub) as plan:
+        m.mraid_set_eig_variant(plan.handle, variant)
+        ev, q1, st = plan.eig(torch.from_numpy(packed).cuda())
+        ev, q1, st = ev.cpu().numpy(), q1.cpu().numpy(), st.cpu().numpy()
+    compare_eig(ev, ev_o, f"N={N} variant={variant}")
+    compare_q1(q1, q1_o, ev_o)
+    assert np.all(np.abs(st - st_o) <= STAT_TOL * st_o + 1e-7), np.abs(st - st_o).max()
+    assert np.abs(ev[0::8, 0] - N).max() <= 1e-4 * N
+    assert np.abs(ev[1::8] - 1.0).max() <= 1e-4
