@@ -99,7 +99,10 @@ __device__ __forceinline__ void stage_chunk(const GramArgs& g, uint32_t* xs, int
   }
 }
 
-template <int TPT, bool VEC4>
+// kSeg: sub-integrations longer than kGramSegment samples, whose int32
+// partial sums must be flushed into int64 totals; shorter ones (every
+// receiver here) accumulate in int32 only and keep half the registers.
+template <int TPT, bool VEC4, bool kSeg>
 __global__ void __launch_bounds__(kGramThreads)
 gram_u8_kernel(GramArgs g) {
   extern __shared__ uint32_t smem[];
@@ -119,14 +122,15 @@ gram_u8_kernel(GramArgs g) {
   }
 
   uint32_t acc[TPT][16];
-  unsigned long long tot[TPT][16];
+  unsigned long long tot[kSeg ? TPT : 1][16];
 #pragma unroll
   for (int j = 0; j < TPT; ++j)
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      acc[j][e] = 0;
-      tot[j][e] = 0;
-    }
+    for (int e = 0; e < 16; ++e) acc[j][e] = 0;
+#pragma unroll
+  for (int j = 0; j < (kSeg ? TPT : 1); ++j)
+#pragma unroll
+    for (int e = 0; e < 16; ++e) tot[j][e] = 0;
   __syncthreads();
 
   int in_segment = 0;
@@ -157,16 +161,18 @@ gram_u8_kernel(GramArgs g) {
         }
       }
     }
-    in_segment += kT;
-    if (in_segment >= kGramSegment || t_base + kT >= g.n_samp_sub) {
+    if constexpr (kSeg) {
+      in_segment += kT;
+      if (in_segment >= kGramSegment || t_base + kT >= g.n_samp_sub) {
 #pragma unroll
-      for (int j = 0; j < TPT; ++j)
+        for (int j = 0; j < TPT; ++j)
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          tot[j][e] += acc[j][e];
-          acc[j][e] = 0;
-        }
-      in_segment = 0;
+          for (int e = 0; e < 16; ++e) {
+            tot[j][e] += acc[j][e];
+            acc[j][e] = 0;
+          }
+        in_segment = 0;
+      }
     }
   }
 
@@ -186,7 +192,9 @@ gram_u8_kernel(GramArgs g) {
       for (int k = 0; k < 4; ++k) {
         const int a = 4 * (tij & 0xff) + i;
         const int b = 4 * (tij >> 8) + k;
-        if (a <= b && b < N1) out[a * N1 - a * (a - 1) / 2 + (b - a)] = (int64_t)tot[j][4 * i + k];
+        if (a <= b && b < N1)
+          out[a * N1 - a * (a - 1) / 2 + (b - a)] =
+              kSeg ? (int64_t)tot[kSeg ? j : 0][4 * i + k] : (int64_t)acc[j][4 * i + k];
       }
   }
 }
@@ -278,19 +286,26 @@ cudaError_t launch_gram_u8(const mraid_plan_s* pl, const uint8_t* d_data, int su
   dim3 grid((g.n_chan + cpb - 1) / cpb, n_sub);
   const int tpt = (g.ntask + kGramThreads - 1) / kGramThreads;
   cudaError_t e = cudaSuccess;
-#define MRAID_GRAM_LAUNCH(T, V)                                                                   \
+#define MRAID_GRAM_LAUNCH(T, V, S)                                                                \
   do {                                                                                            \
-    e = cudaFuncSetAttribute(gram_u8_kernel<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                             (int)smem);                                                          \
-    if (e == cudaSuccess) gram_u8_kernel<T, V><<<grid, kGramThreads, smem, pl->stream>>>(g);       \
+    e = cudaFuncSetAttribute(gram_u8_kernel<T, V, S>,                                             \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);             \
+    if (e == cudaSuccess) gram_u8_kernel<T, V, S><<<grid, kGramThreads, smem, pl->stream>>>(g);    \
   } while (0)
-  if (tpt <= 1) {
-    if (vec4) MRAID_GRAM_LAUNCH(1, true); else MRAID_GRAM_LAUNCH(1, false);
-  } else if (tpt == 2) {
-    if (vec4) MRAID_GRAM_LAUNCH(2, true); else MRAID_GRAM_LAUNCH(2, false);
-  } else {
-    if (vec4) MRAID_GRAM_LAUNCH(4, true); else MRAID_GRAM_LAUNCH(4, false);
-  }
+#define MRAID_GRAM_TPT(T)                                                                         \
+  do {                                                                                            \
+    if (seg) {                                                                                    \
+      if (vec4) MRAID_GRAM_LAUNCH(T, true, true); else MRAID_GRAM_LAUNCH(T, false, true);          \
+    } else {                                                                                      \
+      if (vec4) MRAID_GRAM_LAUNCH(T, true, false); else MRAID_GRAM_LAUNCH(T, false, false);        \
+    }                                                                                             \
+  } while (0)
+  const bool seg = g.n_samp_sub > kGramSegment;
+  if (tpt <= 1) MRAID_GRAM_TPT(1);
+  else if (tpt == 2) MRAID_GRAM_TPT(2);
+  else if (tpt == 3) MRAID_GRAM_TPT(3);
+  else MRAID_GRAM_TPT(4);
+#undef MRAID_GRAM_TPT
 #undef MRAID_GRAM_LAUNCH
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
