@@ -295,6 +295,7 @@ def bench_batched(m, torch, stream, steps):
     torch.cuda.synchronize()
     ms_p = e0.elapsed_time(e1) / steps
     inst, upd = batch.graph_stats()
+    packing, ms_conc, ms_chain = batch.packing()
     for plan in plans:
         plan.close()
     batch.close()
@@ -305,7 +306,10 @@ def bench_batched(m, torch, stream, steps):
             "ms_per_pass": ms_b, "cells_per_s": cells / (ms_b / 1000.0),
             "plain_ms_per_pass": ms_p, "plain_cells_per_s": cells / (ms_p / 1000.0),
             "graph_instantiations": inst, "graph_updates": upd,
-            "note": "plain = one mraid_run per block, sequential on one stream; default Gram tiles in both"}
+            "packing": {"chosen": "chained" if packing == 1 else "concurrent",
+                        "ms_concurrent": ms_conc, "ms_chained": ms_chain},
+            "note": "plain = one mraid_run per block, sequential on one stream; default variants "
+                    "in both; the batch's first run timed both packings"}
 
 
 def bench_served(m, torch, seconds, rates=(1.0, 2.0, 4.0)):

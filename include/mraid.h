@@ -213,11 +213,13 @@ mraid_status mraid_set_eig_variant(mraid_plan_t plan, int32_t variant);
 /* ------------------------------------------------------------------------
  * Batched form: blocks of uneven receiver shapes (different N_beam, N_s,
  * channel counts; e.g. 13-, 19-, 36- and 72-beam systems, Section 5) in one
- * pass. Cells are independent (Section 3.3), so the units run concurrently
- * on the GPU; the masking statistics stay per unit (each unit is its own
- * observation). The pass is captured once into a CUDA graph on the batch's
- * stream; a later call with different buffers rebinds them through a graph
- * update instead of a new instantiation.
+ * pass. Cells are independent (Section 3.3); the masking statistics stay per
+ * unit (each unit is its own observation). The pass is captured into a CUDA
+ * graph on the batch's stream, with the units either as concurrent branches
+ * or chained one after another: the first mraid_batch_run times both
+ * packings on the caller's buffers (so that call waits for the GPU) and
+ * keeps the faster. A later call with different buffers rebinds them
+ * through a graph update instead of a new instantiation.
  */
 typedef struct mraid_batch_s* mraid_batch_t;
 
@@ -246,6 +248,12 @@ mraid_status mraid_batch_sync(mraid_batch_t batch);
  * with new buffers is an update, not an instantiation). */
 mraid_status mraid_batch_graph_stats(mraid_batch_t batch, int32_t* instantiations,
                                      int32_t* updates);
+
+/* The packing the first run chose (*packing: 0 = concurrent branches,
+ * 1 = chained; -1 before the first run) and the measured pass time of each
+ * in milliseconds (-1 if not measured). The times may be NULL. */
+mraid_status mraid_batch_packing(mraid_batch_t batch, int32_t* packing, float* ms_concurrent,
+                                 float* ms_chained);
 
 void mraid_batch_destroy(mraid_batch_t batch);
 

@@ -23,6 +23,7 @@ __all__ = [
     "mraid_destroy", "mraid_status_string", "mraid_last_error", "mraid_abi_version",
     "mraid_profile_enable", "mraid_profile_read", "mraid_profile_reset", "mraid_ccm_noalloc",
     "mraid_batch_plan", "mraid_batch_run", "mraid_batch_sync", "mraid_batch_graph_stats",
+    "mraid_batch_packing",
     "mraid_batch_destroy", "UnitIO", "Batch", "mraid_serve_open", "mraid_serve_submit",
     "mraid_serve_poll", "mraid_serve_drain", "mraid_serve_close", "StreamDesc", "BlockResult",
     "Server", "mraid_autotune", "mraid_set_variant", "mraid_set_eig_variant", "tune",
@@ -143,6 +144,8 @@ def load():
         "mraid_batch_run": (ctypes.c_int, [vp, ctypes.POINTER(UnitIO), ctypes.POINTER(FlagInfo)]),
         "mraid_batch_sync": (ctypes.c_int, [vp]),
         "mraid_batch_graph_stats": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "mraid_batch_packing": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float),
+                                               ctypes.POINTER(ctypes.c_float)]),
         "mraid_batch_destroy": (None, [vp]),
         "mraid_serve_open": (ctypes.c_int, [ctypes.POINTER(StreamDesc), i32, ctypes.c_int64, i32,
                                             ctypes.POINTER(vp)]),
@@ -300,6 +303,16 @@ def mraid_batch_graph_stats(batch: int):
     _check(load().mraid_batch_graph_stats(batch, ctypes.byref(a), ctypes.byref(b)),
            "mraid_batch_graph_stats")
     return a.value, b.value
+
+
+def mraid_batch_packing(batch: int):
+    """(packing, ms concurrent, ms chained): 0 = concurrent branches,
+    1 = chained, -1 before the first run."""
+    p = ctypes.c_int32(0)
+    a, b = ctypes.c_float(0), ctypes.c_float(0)
+    _check(load().mraid_batch_packing(batch, ctypes.byref(p), ctypes.byref(a), ctypes.byref(b)),
+           "mraid_batch_packing")
+    return p.value, a.value, b.value
 
 
 def mraid_batch_destroy(batch: int):
@@ -547,6 +560,9 @@ class Batch:
 
     def graph_stats(self):
         return mraid_batch_graph_stats(self.handle)
+
+    def packing(self):
+        return mraid_batch_packing(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -4,11 +4,13 @@
 // Each unit owns a plan (its buffers are allocated at mraid_batch_plan, so
 // nothing allocates during capture) bound to a side stream forked from the
 // batch stream. The whole pass - every unit's Gram, eigen and masking
-// kernels, and the info copies - is captured once into a CUDA graph; units
-// are independent branches, so the GPU runs them concurrently and their
-// kernels fill each other's idle SMs. A call with different buffers
-// re-captures and rebinds them into the existing executable graph with
-// cudaGraphExecUpdate.
+// kernels, and the info copies - is captured once into a CUDA graph. Two
+// packings exist: the units as independent branches (the GPU runs them
+// concurrently, so small units fill the SMs large ones leave idle) or
+// chained one after another (no contention when every unit fills the GPU
+// on its own); the first call times both and keeps the faster. A call with
+// different buffers re-captures and rebinds them into the existing
+// executable graph with cudaGraphExecUpdate.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -30,6 +32,8 @@ struct mraid_batch_s {
   std::vector<mraid_unit_io> bound;
   std::vector<mraid_flag_info*> infos;
   int instantiations = 0, updates = 0;
+  int packing = -1;                     // 0 concurrent branches, 1 chained; -1 not yet tuned
+  float packing_ms[2] = {-1.f, -1.f};   // measured pass time of each packing
 };
 
 using namespace mraid;
@@ -42,13 +46,14 @@ bool same_io(const std::vector<mraid_unit_io>& a, const mraid_unit_io* b) {
   return true;
 }
 
-mraid_status capture(mraid_batch_s* bt, const mraid_unit_io* io, cudaGraph_t* graph) {
+mraid_status capture(mraid_batch_s* bt, const mraid_unit_io* io, int packing, cudaGraph_t* graph) {
   cudaError_t e = cudaStreamBeginCapture(bt->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(e, "batch capture begin");
   mraid_status st = MRAID_OK;
   e = cudaEventRecord(bt->fork, bt->stream);
   for (size_t i = 0; i < bt->plans.size() && e == cudaSuccess && st == MRAID_OK; ++i) {
-    e = cudaStreamWaitEvent(bt->side[i], bt->fork, 0);
+    // concurrent: every unit starts at the fork; chained: after the previous unit
+    e = cudaStreamWaitEvent(bt->side[i], (packing == 1 && i > 0) ? bt->join[i - 1] : bt->fork, 0);
     if (e != cudaSuccess) break;
     st = mraid_run(bt->plans[i], io[i].d_data, io[i].d_evals, io[i].d_q1, io[i].d_stat,
                    io[i].d_flags, nullptr);
@@ -68,6 +73,50 @@ mraid_status capture(mraid_batch_s* bt, const mraid_unit_io* io, cudaGraph_t* gr
   }
   *graph = g;
   return MRAID_OK;
+}
+
+// Time both packings on the caller's buffers (one warm-up and two timed
+// launches each, after the caller's stream) and keep the faster; its
+// executable graph becomes the batch's.
+mraid_status tune_packing(mraid_batch_s* bt, const mraid_unit_io* io) {
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaError_t e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  if (e == cudaSuccess) e = cudaEventRecord(bt->ev_in, bt->user);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(bt->stream, bt->ev_in, 0);
+  cudaGraphExec_t ex[2] = {nullptr, nullptr};
+  mraid_status st = MRAID_OK;
+  for (int p = 0; p < 2 && e == cudaSuccess && st == MRAID_OK; ++p) {
+    cudaGraph_t g = nullptr;
+    st = capture(bt, io, p, &g);
+    if (st != MRAID_OK) break;
+    e = cudaGraphInstantiate(&ex[p], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) break;
+    ++bt->instantiations;
+    e = cudaGraphLaunch(ex[p], bt->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(t0, bt->stream);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = cudaGraphLaunch(ex[p], bt->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(t1, bt->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    bt->packing_ms[p] = ms / 2.f;
+  }
+  if (e == cudaSuccess && st == MRAID_OK) {
+    const int best = bt->packing_ms[1] < bt->packing_ms[0] ? 1 : 0;
+    bt->packing = best;
+    if (bt->exec) cudaGraphExecDestroy(bt->exec);
+    bt->exec = ex[best];
+    ex[best] = nullptr;
+    bt->bound.assign(io, io + bt->plans.size());
+  }
+  for (auto x : ex)
+    if (x) cudaGraphExecDestroy(x);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (st != MRAID_OK) return st;
+  return e == cudaSuccess ? MRAID_OK : cuda_fail(e, "batch packing");
 }
 
 }  // namespace
@@ -138,9 +187,13 @@ mraid_status mraid_batch_run(mraid_batch_t bt, const mraid_unit_io* io, mraid_fl
   }
   cudaError_t e = cudaSetDevice(bt->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  if (bt->packing < 0) {
+    mraid_status st = tune_packing(bt, io);
+    if (st != MRAID_OK) return st;
+  }
   if (!bt->exec || !same_io(bt->bound, io)) {
     cudaGraph_t g = nullptr;
-    mraid_status st = capture(bt, io, &g);
+    mraid_status st = capture(bt, io, bt->packing, &g);
     if (st != MRAID_OK) return st;
     bool updated = false;
     if (bt->exec) {
@@ -201,6 +254,18 @@ mraid_status mraid_batch_graph_stats(mraid_batch_t bt, int32_t* instantiations, 
   }
   *instantiations = bt->instantiations;
   *updates = bt->updates;
+  return MRAID_OK;
+}
+
+mraid_status mraid_batch_packing(mraid_batch_t bt, int32_t* packing, float* ms_concurrent,
+                                 float* ms_chained) {
+  if (!bt || !packing) {
+    set_error("mraid_batch_packing: bad arguments");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  *packing = bt->packing;
+  if (ms_concurrent) *ms_concurrent = bt->packing_ms[0];
+  if (ms_chained) *ms_chained = bt->packing_ms[1];
   return MRAID_OK;
 }
 

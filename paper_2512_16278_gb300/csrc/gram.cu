@@ -18,6 +18,11 @@ namespace {
 constexpr int kGramThreads = 256;
 constexpr int kT = 32;          // samples staged per chunk
 constexpr int kTW = kT / 4;     // 32-bit words per staged row
+// Staged row stride in words: one more than a row, so the rows of the
+// 4-row tiles that a warp's lanes read at once fall in different banks
+// (a stride of kTW = 8 words put every tile's rows 32 words apart, on the
+// same bank).
+constexpr int kRS = kTW + 1;
 
 struct GramArgs {
   const uint8_t* data;
@@ -28,7 +33,7 @@ struct GramArgs {
   int cpb;      // channels per block
   int tiles;    // 4x4 row tiles in the upper triangle: T1(T1+1)/2, T1 = R/4
   int ntask;    // cpb * tiles
-  int cs;       // staged words per channel: R * kTW + 1 (odd: no bank conflicts)
+  int cs;       // staged words per channel: R * kRS + 1 (odd: channels in different banks)
   int psum;     // (N+1)(N+2)/2
   int64_t* sums;
 };
@@ -39,7 +44,7 @@ __device__ __forceinline__ uint32_t ones_word(int valid) {
 }
 
 // Stage kT samples x R rows x cpb channels, time-contiguous per (channel,
-// row): word xs[c*cs + row*kTW + t/4] holds samples t..t+3 of that row.
+// row): word xs[c*cs + row*kRS + t/4] holds samples t..t+3 of that row.
 template <bool VEC4>
 __device__ __forceinline__ void stage_chunk(const GramArgs& g, uint32_t* xs, int sub,
                                             int c0, int t_base) {
@@ -68,7 +73,7 @@ __device__ __forceinline__ void stage_chunk(const GramArgs& g, uint32_t* xs, int
       const uint32_t hi01 = __byte_perm(v[0], v[1], 0x7362);
       const uint32_t lo23 = __byte_perm(v[2], v[3], 0x5140);
       const uint32_t hi23 = __byte_perm(v[2], v[3], 0x7362);
-      uint32_t* dst = xs + (4 * c4) * g.cs + b * kTW + t4;
+      uint32_t* dst = xs + (4 * c4) * g.cs + b * kRS + t4;
       dst[0] = __byte_perm(lo01, lo23, 0x5410);
       dst[g.cs] = __byte_perm(lo01, lo23, 0x7632);
       dst[2 * g.cs] = __byte_perm(hi01, hi23, 0x5410);
@@ -85,7 +90,7 @@ __device__ __forceinline__ void stage_chunk(const GramArgs& g, uint32_t* xs, int
       uint8_t x = 0;
       if (t < nv && c0 + c < g.n_chan)
         x = __ldg(g.data + b * g.beam_stride + (t_abs0 + t) * g.n_chan + c0 + c);
-      xb[4 * (c * g.cs + b * kTW + t / 4) + (t & 3)] = x;
+      xb[4 * (c * g.cs + b * kRS + t / 4) + (t & 3)] = x;
     }
   }
   // ones row (index N) and zero padding rows
@@ -95,7 +100,7 @@ __device__ __forceinline__ void stage_chunk(const GramArgs& g, uint32_t* xs, int
     const int rt = w / g.cpb;
     const int t4 = rt % kTW;
     const int row = g.n_beam + rt / kTW;
-    xs[c * g.cs + row * kTW + t4] = (row == g.n_beam) ? ones_word(nv - 4 * t4) : 0u;
+    xs[c * g.cs + row * kRS + t4] = (row == g.n_beam) ? ones_word(nv - 4 * t4) : 0u;
   }
 }
 
@@ -144,15 +149,15 @@ gram_u8_kernel(GramArgs g) {
       if (task < g.ntask) {
         const int c = task % g.cpb;
         const uint16_t tij = tile_ij[task / g.cpb];
-        const uint32_t* ra = xs + c * g.cs + 4 * (tij & 0xff) * kTW;
-        const uint32_t* rb = xs + c * g.cs + 4 * (tij >> 8) * kTW;
+        const uint32_t* ra = xs + c * g.cs + 4 * (tij & 0xff) * kRS;
+        const uint32_t* rb = xs + c * g.cs + 4 * (tij >> 8) * kRS;
 #pragma unroll
         for (int t4 = 0; t4 < kTW; ++t4) {
           uint32_t a[4], b[4];
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            a[i] = ra[i * kTW + t4];
-            b[i] = rb[i * kTW + t4];
+            a[i] = ra[i * kRS + t4];
+            b[i] = rb[i * kRS + t4];
           }
 #pragma unroll
           for (int i = 0; i < 4; ++i)
@@ -277,7 +282,8 @@ cudaError_t launch_gram_u8(const mraid_plan_s* pl, const uint8_t* d_data, int su
   if (cpb > g.n_chan) cpb = g.n_chan;
   g.cpb = cpb;
   g.ntask = cpb * g.tiles;
-  g.cs = g.R * kTW + 1;
+  g.cs = g.R * kRS + 1;
+  if ((g.cs & 1) == 0) ++g.cs;
   g.psum = pl->psum;
   g.sums = d_sums;
   const bool vec4 = (cpb % 4 == 0) && (g.n_chan % 4 == 0) && (g.beam_stride % 4 == 0) &&

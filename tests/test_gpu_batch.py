@@ -56,8 +56,13 @@ def test_batch_equals_alone_and_oracle():
         for o, o2 in zip(outs, outs2):
             for k in ("evals", "q1", "stat", "flags"):
                 assert torch.equal(o[k], o2[k])
+        # the first run instantiated both packings (concurrent, chained) to
+        # time them and kept one; the replay with new buffers is an update
         inst, upd = batch.graph_stats()
-        assert inst == 1 and upd == 1
+        assert inst == 2 and upd == 1
+        packing, ms_c, ms_s = batch.packing()
+        assert packing in (0, 1) and ms_c > 0 and ms_s > 0
+        assert (ms_s < ms_c) == (packing == 1)
         # replay with the same buffers: neither
         batch.run(d_dev, outs2)
-        assert batch.graph_stats() == (1, 1)
+        assert batch.graph_stats() == (2, 1)
