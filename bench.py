@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-sub", type=int, default=0,
                     help="shrink the block to this many sub-integrations (profiling runs)")
+    ap.add_argument("--f32-subs", type=int, default=20,
+                    help="sub-integrations of the float32-input variant (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3,
                     help="timed passes of the batched form (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
@@ -250,6 +252,60 @@ def torch_index(idx):
 
 
 # ------------------------------------------------------------- main arms
+
+def bench_f32(m, torch, d_u8, cfg, stream, n_sub):
+    """Float32-input variant (beamformer output, bit_depth 32) on the first
+    n_sub sub-integrations of the same block, converted on the device to
+    (x - 128) / 20 (zero-mean, unit-variance noise with the same RFI): cells/s
+    of the whole path, and its eigenvalue error against the oracle (FP64
+    covariance of the float32 samples) on a sample of cells."""
+    import numpy as np
+    import oracle
+    N, C, S = cfg.n_beam, cfg.n_chan, cfg.n_samp_sub
+    T = n_sub * S
+    x = d_u8.view(N, cfg.n_time, C)[:, :T, :].float().sub_(128.0).div_(20.0).contiguous()
+    cells = n_sub * C
+    with torch.cuda.stream(stream):
+        plan = m.Plan(N, C, S, n_sub, bit_depth=32, stream=stream)
+        ev = torch.empty(cells, N, dtype=torch.float32, device="cuda")
+        q = torch.empty(cells, N, dtype=torch.float32, device="cuda")
+        st = torch.empty(cells, dtype=torch.float32, device="cuda")
+        fl = torch.empty(cells, dtype=torch.uint8, device="cuda")
+    info = m.FlagInfo()
+    for _ in range(3):
+        m.mraid_run(plan.handle, x, ev, q, st, fl, info)
+    m.mraid_sync(plan.handle)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        m.mraid_run(plan.handle, x, ev, q, st, fl, info)
+    e1.record(stream)
+    m.mraid_sync(plan.handle)
+    ms = e0.elapsed_time(e1) / 5
+    rng = np.random.default_rng(7)
+    idx = rng.integers(0, cells, size=256)
+    evh = ev.cpu().numpy()
+    err = []
+    for i in idx:
+        k, c = int(i // C), int(i % C)
+        # this cell's samples as a one-channel block [beam][time][1]
+        cell = x[:, k * S:(k + 1) * S, c:c + 1].contiguous().cpu().numpy()
+        r, _ = oracle.corr_from_cov(oracle.cell_cov_f32(cell, S, 0, 0))
+        eo = oracle.jacobi(r)[0]
+        err.append(float(np.abs(evh[i] - eo).max() / np.abs(eo).max()))
+    plan.close()
+    del x
+    torch.cuda.empty_cache()
+    return {"workload": f"float32 [19][{T}][{C}] ({n_sub} sub-integrations, "
+                        f"{N * T * C * 4 / 1e9:.2f} GB)",
+            "ms_per_step": ms, "cells_per_s": cells / (ms / 1e3),
+            "gbs": N * T * C * 4 / (ms / 1e3) / 1e9,
+            "eig_err_rel_max": max(err), "eig_err_rel_p99": float(np.percentile(err, 99)),
+            "sampled_cells": len(err),
+            "path": "FP32 sums of per-beam shifted samples on CUDA cores, FP32 eigensolver "
+                    "(the 8-bit path's error is in sampled_parity)"}
+
 
 def bench_batched(m, torch, stream, steps):
     """Four receivers of 5 s each (13/19/36/72 beams) in one graph-captured
@@ -565,6 +621,28 @@ def run_mraid(args):
     if rank == 0 and not args.no_cpu_baseline:
         cpu, sample = cpu_baseline(cfg, h.data_ptr(), args.cpu_seconds)
         parity = sampled_parity(sample, evals, q1, stat)
+
+    # eigenvector refinement (per-beam bits) on the timed run's outputs
+    refine = None
+    if world == 1:
+        W = (N + 31) // 32
+        bits = torch.empty(cells, W, dtype=torch.int32, device="cuda")
+        ms_b = torch.empty(N, 2, dtype=torch.float64, device="cuda")
+        m.mraid_refine(plan.handle, q1, flags, bits, ms_b)
+        m.mraid_sync(plan.handle)
+        r0 = torch.cuda.Event(enable_timing=True)
+        r1 = torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        for _ in range(5):
+            m.mraid_refine(plan.handle, q1, flags, bits, ms_b)
+        r1.record(stream)
+        m.mraid_sync(plan.handle)
+        refine = {"ms": r0.elapsed_time(r1) / 5,
+                  "beam_bits_set": int(sum(bin(int(x) & 0xffffffff).count("1")
+                                           for x in bits.view(-1).cpu().tolist()))}
+    precision = None
+    if world == 1 and args.f32_subs > 0:
+        precision = bench_f32(m, torch, d, cfg, stream, args.f32_subs)
     plan.close()
     del d, h
     torch.cuda.empty_cache()
@@ -600,6 +678,8 @@ def run_mraid(args):
             "eig_iterations": {"per_cell": info.jacobi_sweeps / cells,
                                "per_warp": info.jacobi_warp_sweeps / max(1, (cells + 31) // 32),
                                "unit": "QR steps" if variants[1] >= 2 else "Jacobi sweeps"},
+            "refine": refine,
+            "precision_f32": precision,
             "batched": batched,
             "served": served,
         }

@@ -12,6 +12,7 @@
 namespace mraid {
 
 constexpr int kMaxBeam = 128;
+constexpr int kRefBlocks = 4096;  // eigenvector refinement: partial-sum blocks
 constexpr int kMaxSampSub = 1 << 20;
 constexpr int kMaxClipIter = 1000;
 // Samples per int32 accumulation segment: 32768 * 255^2 < 2^32 (unsigned).
@@ -82,7 +83,7 @@ struct mraid_plan_s {
   int eig_variant = 3;      // register kernels: 0 = Jacobi, looped rounds; 1 = Jacobi,
                             // unrolled sweep; 2 = Householder + implicit QR, one
                             // step copy per level; 3 = the same, one masked copy
-  double* d_refine_part = nullptr;   // eigenvector refinement: [sm][N][3]
+  double* d_refine_part = nullptr;   // eigenvector refinement: [block][N][3]
   float* d_refine_thresh = nullptr;  // [N]
   double* d_refine_ms = nullptr;     // [N][2] when the caller passes none
 };

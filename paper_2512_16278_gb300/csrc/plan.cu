@@ -453,7 +453,7 @@ mraid_status mraid_refine(mraid_plan_t pl, const float* d_q1, const uint8_t* d_f
   }
   cudaError_t e = cudaSuccess;
   if (!pl->d_refine_part) {
-    e = cudaMalloc(&pl->d_refine_part, sizeof(double) * 3 * (size_t)pl->sm_count * kMaxBeam);
+    e = cudaMalloc(&pl->d_refine_part, sizeof(double) * 3 * (size_t)kRefBlocks * kMaxBeam);
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_refine_thresh, sizeof(float) * kMaxBeam);
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_refine_ms, sizeof(double) * 2 * kMaxBeam);
     if (e != cudaSuccess) return cuda_fail(e, "refine buffers");
