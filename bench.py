@@ -39,7 +39,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mraid", "reference"], default="mraid")
-    ap.add_argument("--workload", choices=["fast_block", "small"], default="fast_block")
+    ap.add_argument("--workload", choices=["fast_block", "small", "paf13", "fast19", "paf36", "paf72"],
+                    default="fast_block")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="budget of the oracle CPU baseline sample")
@@ -55,14 +56,22 @@ def parse_args():
     return ap.parse_args()
 
 
+RECEIVERS = {"paf13": 0, "fast19": 1, "paf36": 2, "paf72": 3}   # synth.BATCH_SHAPES index
+
+
 def workload(name, rank, n_sub=0):
     import synth
-    base = synth.FAST_BLOCK if name == "fast_block" else synth.SMALL
+    if name in RECEIVERS:       # one 5 s block of a receiver of the batched form
+        base = synth.BATCH_SHAPES[RECEIVERS[name]]
+        kind = f"{name} receiver block (5 s)"
+    else:
+        base = synth.FAST_BLOCK if name == "fast_block" else synth.SMALL
+        kind = "FAST-shaped block" if name == "fast_block" else "small block"
     cfg = base.replace(seed=base.seed + 7919 * rank)
     if n_sub:
         cfg = cfg.replace(n_sub=n_sub, n_burst=min(cfg.n_burst, max(0, n_sub - 1)),
                           n_spike=min(cfg.n_spike, n_sub * cfg.n_chan // 1000 + 1))
-    desc = (f"FAST-shaped block: {cfg.n_beam} beams x {cfg.n_chan} channels x {cfg.n_sub} "
+    desc = (f"{kind}: {cfg.n_beam} beams x {cfg.n_chan} channels x {cfg.n_sub} "
             f"sub-integrations x {cfg.n_samp_sub} samples, uint8 ({cfg.n_cells} cells, "
             f"{cfg.nbytes / 1e9:.2f} GB)")
     return cfg, desc

@@ -344,7 +344,8 @@ cudaError_t launch_corr_from_sums(const mraid_plan_s* pl, const int64_t* d_sums,
 namespace mraid {
 namespace {
 
-constexpr int kF32T = 16;  // samples staged per chunk
+constexpr int kF32T = 16;       // samples staged per chunk
+constexpr int kF32RS = kF32T + 1;  // staged row stride: a tile's 4 rows in different banks
 
 struct F32Args {
   const float* data;
@@ -358,7 +359,7 @@ struct F32Args {
 
 __global__ void __launch_bounds__(kGramThreads) gram_f32_kernel(F32Args g) {
   extern __shared__ float fsm[];
-  float* xs = fsm;                                 // [cpb][R][kF32T] (+1 pad per channel)
+  float* xs = fsm;                                 // [cpb][R][kF32RS] (+1 pad per channel)
   float* shift = xs + g.cpb * g.cs;                // [cpb][R]
   float* gram = shift + g.cpb * g.R;               // [cpb][R][R] for the epilogue
   uint16_t* tile_ij = reinterpret_cast<uint16_t*>(gram + g.cpb * g.R * g.R);
@@ -401,7 +402,7 @@ __global__ void __launch_bounds__(kGramThreads) gram_f32_kernel(F32Args g) {
         else if (r == g.n_beam)
           v = 1.f;
       }
-      xs[c * g.cs + r * kF32T + t] = v;
+      xs[c * g.cs + r * kF32RS + t] = v;
     }
     __syncthreads();
 #pragma unroll
@@ -410,14 +411,14 @@ __global__ void __launch_bounds__(kGramThreads) gram_f32_kernel(F32Args g) {
       if (task < g.ntask) {
         const int c = task % g.cpb;
         const uint16_t tij = tile_ij[task / g.cpb];
-        const float* ra = xs + c * g.cs + 4 * (tij & 0xff) * kF32T;
-        const float* rb = xs + c * g.cs + 4 * (tij >> 8) * kF32T;
+        const float* ra = xs + c * g.cs + 4 * (tij & 0xff) * kF32RS;
+        const float* rb = xs + c * g.cs + 4 * (tij >> 8) * kF32RS;
         for (int t = 0; t < kF32T; ++t) {
           float a[4], b[4];
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            a[i] = ra[i * kF32T + t];
-            b[i] = rb[i * kF32T + t];
+            a[i] = ra[i * kF32RS + t];
+            b[i] = rb[i * kF32RS + t];
           }
 #pragma unroll
           for (int i = 0; i < 4; ++i)
@@ -492,7 +493,8 @@ cudaError_t launch_gram_f32(const mraid_plan_s* pl, const float* d_data, int sub
   if (cpb > g.n_chan) cpb = g.n_chan;
   g.cpb = cpb;
   g.ntask = cpb * g.tiles;
-  g.cs = g.R * kF32T + 1;
+  g.cs = g.R * kF32RS + 1;
+  if ((g.cs & 1) == 0) ++g.cs;
   g.np = pl->np;
   g.corr = d_corr;
   g.degenerate = pl->d_degenerate;
