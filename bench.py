@@ -667,7 +667,8 @@ def run_mraid(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u8->i32/i64 Gram, f32 Jacobi", "data": "synthetic",
+            "dtype": "u8 (exact Gram: f16 tensor cores, FP32 accumulate), f32 eigensolver",
+            "data": "synthetic",
             "config": config_dict(cfg, desc, world),
             "hbm": {"path_bytes_per_step": in_bytes + out_bytes, "achieved_gbs": path_gbs,
                     "frac_of_measured": path_gbs / peaks["hbm_gbs"],

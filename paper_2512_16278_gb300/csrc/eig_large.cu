@@ -50,36 +50,46 @@ __host__ __device__ __forceinline__ int64_t refl_off(int k, int N) {
 __host__ __device__ __forceinline__ int64_t refl_floats(int N) {
   return N > 2 ? refl_off(N - 2, N) + (N - 2) : 1;
 }
-__host__ __device__ __forceinline__ int row_stride(int N) { return (N & 1) ? N : N + 1; }
+// Row stride of the full matrix in shared memory: a multiple of 4 floats
+// (16-byte rows for vector accesses) with an odd quotient, so the rows of
+// 8 consecutive lanes start in 8 different 4-bank groups and a warp's
+// 16-byte accesses take the minimum 4 wavefronts.
+__host__ __device__ __forceinline__ int row_stride(int N) {
+  const int q = (N + 3) / 4;
+  return 4 * ((q & 1) ? q : q + 1);
+}
 
 // ---------------------------------------------------------------- pass 1
-__global__ void tri_reduce_kernel(const float* __restrict__ corr, int64_t n_cells, int N, float* __restrict__ de,
-                  float* __restrict__ refl) {
-  extern __shared__ float rsm[];
+__global__ void tri_reduce_kernel(const float* __restrict__ corr, int64_t n_cells, int N,
+                                  float* __restrict__ de, float* __restrict__ refl) {
+  extern __shared__ __align__(16) float rsm[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int LD = row_stride(N);
   const int NP = N * (N + 1) / 2;
-  float* A = rsm + (size_t)w * ((size_t)N * LD + 2 * N);
-  float* V = A + (size_t)N * LD;   // current reflector
-  float* W = V + N;                // p, then w = p - K v
+  float* A = rsm + (size_t)w * ((size_t)N * LD + 2 * LD);
+  float* V = A + (size_t)N * LD;   // current reflector, by absolute column (0 outside it)
+  float* W = V + LD;               // p, then w = p - K v, by absolute column
   const uint32_t abase = static_cast<uint32_t>(__cvta_generic_to_shared(A));
   const int64_t RF = refl_floats(N);
   for (int64_t cell = (int64_t)blockIdx.x * nw + w; cell < n_cells;
        cell += (int64_t)gridDim.x * nw) {
     const float* src = corr + cell * NP;
-    // packed upper triangle -> full symmetric matrix
+    // packed upper triangle -> full symmetric matrix; padding columns zero
     for (int a = 0, off = 0; a < N; off += N - a, ++a)
       for (int b = a + lane; b < N; b += 32) {
         cp_async4(abase + 4u * (uint32_t)(a * LD + b), src + off + (b - a));
         if (b != a) cp_async4(abase + 4u * (uint32_t)(b * LD + a), src + off + (b - a));
       }
+    for (int a = 0; a < N; ++a)
+      for (int b = N + lane; b < LD; b += 32) A[a * LD + b] = 0.f;
+    for (int j = lane; j < LD; j += 32) V[j] = W[j] = 0.f;
     cp_async_wait_all();
     __syncwarp();
     float* dcell = de + cell * 2 * N;
     float* rcell = refl + cell * RF;
     for (int k = 0; k < N - 2; ++k) {
       const int m = N - 1 - k;
-      const float* Ak = A + (size_t)(k + 1) * LD + (k + 1);  // trailing block A'
+      const int j0 = (k + 1) & ~3;  // aligned start; V = W = 0 below column k + 1
       float s2 = 0.f;
       for (int i = lane; i < m; i += 32) {
         const float x = A[(size_t)(k + 1 + i) * LD + k];
@@ -92,9 +102,10 @@ __global__ void tri_reduce_kernel(const float* __restrict__ corr, int64_t n_cell
       const float vtv = 2.f * nx * (nx + fabsf(x0));
       const bool reflect = vtv > 1e-30f;
       const float beta = reflect ? 2.f / vtv : 0.f;
+      if (lane == 0) V[k] = 0.f;  // column k leaves the trailing block
       for (int i = lane; i < m; i += 32) {
         const float v = i == 0 ? x0 - alpha : A[(size_t)(k + 1 + i) * LD + k];
-        V[i] = v;
+        V[k + 1 + i] = v;
         rcell[refl_off(k, N) + i] = v;
       }
       if (lane == 0) {
@@ -103,26 +114,46 @@ __global__ void tri_reduce_kernel(const float* __restrict__ corr, int64_t n_cell
         dcell[N + k] = reflect ? alpha : x0;
       }
       __syncwarp();
-      // p = beta A' v, one row per lane
+      // p = beta A' v, one row per lane, 16-byte accesses
       for (int i = lane; i < m; i += 32) {
-        const float* row = Ak + (size_t)i * LD;
-        float acc = 0.f;
-        for (int j = 0; j < m; ++j) acc = fmaf(row[j], V[j], acc);
-        W[i] = beta * acc;
+        const float4* row = reinterpret_cast<const float4*>(A + (size_t)(k + 1 + i) * LD);
+        const float4* v4 = reinterpret_cast<const float4*>(V);
+        float a0 = 0.f, a1 = 0.f;
+#pragma unroll 4
+        for (int j = j0 >> 2; j < (LD >> 2); ++j) {
+          const float4 r = row[j], v = v4[j];
+          a0 = fmaf(r.x, v.x, a0);
+          a1 = fmaf(r.y, v.y, a1);
+          a0 = fmaf(r.z, v.z, a0);
+          a1 = fmaf(r.w, v.w, a1);
+        }
+        W[k + 1 + i] = beta * (a0 + a1);
       }
       __syncwarp();
       float vp = 0.f;
-      for (int i = lane; i < m; i += 32) vp = fmaf(V[i], W[i], vp);
+      for (int i = lane; i < m; i += 32) vp = fmaf(V[k + 1 + i], W[k + 1 + i], vp);
       const float kh = 0.5f * beta * warp_sum(vp);
-      for (int i = lane; i < m; i += 32) W[i] = fmaf(-kh, V[i], W[i]);
+      for (int i = lane; i < m; i += 32) W[k + 1 + i] = fmaf(-kh, V[k + 1 + i], W[k + 1 + i]);
       __syncwarp();
-      // A' -= v w^T + w v^T
+      // A' -= v w^T + w v^T (columns below k + 1 see v = w = 0)
       for (int i = lane; i < m; i += 32) {
-        float* row = const_cast<float*>(Ak) + (size_t)i * LD;
-        const float vi = V[i], wi = W[i];
-        for (int j = 0; j < m; ++j) row[j] = fmaf(-vi, W[j], fmaf(-wi, V[j], row[j]));
+        float4* row = reinterpret_cast<float4*>(A + (size_t)(k + 1 + i) * LD);
+        const float4* v4 = reinterpret_cast<const float4*>(V);
+        const float4* w4 = reinterpret_cast<const float4*>(W);
+        const float vi = V[k + 1 + i], wi = W[k + 1 + i];
+#pragma unroll 4
+        for (int j = j0 >> 2; j < (LD >> 2); ++j) {
+          float4 r = row[j];
+          const float4 a = w4[j], b = v4[j];
+          r.x = fmaf(-vi, a.x, fmaf(-wi, b.x, r.x));
+          r.y = fmaf(-vi, a.y, fmaf(-wi, b.y, r.y));
+          r.z = fmaf(-vi, a.z, fmaf(-wi, b.z, r.z));
+          r.w = fmaf(-vi, a.w, fmaf(-wi, b.w, r.w));
+          row[j] = r;
+        }
       }
       __syncwarp();
+      if (lane == 0) W[k] = 0.f;
     }
     if (lane == 0) {
       dcell[N - 2] = A[(size_t)(N - 2) * LD + (N - 2)];
@@ -143,23 +174,31 @@ __device__ void qr_step_mem(float* d, float* e, int l, int m) {
   const float r2s = fmaf(dl, dl, em * em);
   const float rr = r2s * rsqrtf(r2s);  // em != 0, so r2s > 0
   const float mu = dm - __fdividef(em * em, dl + (dl >= 0.f ? rr : -rr));
-  float x = d[l] - mu, z = e[l];
+  // d[k] and e[k] of the current step travel in registers (each is
+  // rewritten by the step before), so memory stays off the rotation chain
+  float dk = d[l], ek = e[l];
+  float x = dk - mu, z = ek;
   for (int k = l; k < m; ++k) {
+    const float dk1 = d[k + 1];
+    const float ek1 = (k < m - 1) ? e[k + 1] : 0.f;
     const float r2 = fmaf(x, x, z * z);
     const bool nz = r2 > 1e-37f;
     const float ri = nz ? rsqrtf(r2) : 0.f;
     const float c = nz ? x * ri : 1.f, s = nz ? z * ri : 0.f;
     if (k > l) e[k - 1] = r2 * ri;
-    const float dk = d[k], ek = e[k], dk1 = d[k + 1];
     const float cc = c * c, ss = s * s, cs2 = 2.f * c * s * ek;
     d[k] = fmaf(cc, dk, fmaf(ss, dk1, cs2));
-    d[k + 1] = fmaf(ss, dk, fmaf(cc, dk1, -cs2));
+    const float dnext = fmaf(ss, dk, fmaf(cc, dk1, -cs2));
     const float ekn = fmaf(c * s, dk1 - dk, (cc - ss) * ek);
-    e[k] = ekn;
     if (k < m - 1) {
-      z = s * e[k + 1];
-      e[k + 1] *= c;
+      z = s * ek1;
+      ek = c * ek1;   // e[k+1] after this rotation: next step's e[k]
+      e[k] = ekn;
+    } else {
+      e[k] = ekn;
+      d[k + 1] = dnext;
     }
+    dk = dnext;
     x = ekn;
   }
 }
@@ -324,7 +363,7 @@ cudaError_t launch_eig_large(const mraid_plan_s* pl, const float* d_corr, int64_
   float* y = refl + (size_t)n_cells * refl_floats(N);
   const int64_t cap = (int64_t)pl->sm_count * 16;
   // pass 1: as many warps per block (up to 4) as 200 KB of shared memory holds
-  const size_t per_warp = sizeof(float) * ((size_t)N * row_stride(N) + 2 * N);
+  const size_t per_warp = sizeof(float) * ((size_t)N * row_stride(N) + 2 * row_stride(N));
   int nw = (int)((200u << 10) / per_warp);
   nw = nw < 1 ? 1 : (nw > kRedWarps ? kRedWarps : nw);
   const size_t smem1 = per_warp * nw;

@@ -6,8 +6,8 @@
 // the cells the eigenvalue mask left unflagged (and not preserved); a
 // flagged cell marks beam b when |q1_b| > mu_b + t sigma_b. Three launches:
 // per-block partial sums (FP32 over 256-cell chunks, folded into FP64), one
-// block that combines them in a fixed order (a warp per beam), and a
-// per-cell bit writer.
+// warp per beam that combines them in a fixed order, and a per-cell bit
+// writer.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -76,13 +76,14 @@ refine_partials(const float* __restrict__ q1, const uint8_t* __restrict__ flags,
   }
 }
 
-// One warp per beam: lane l sums the partials of blocks l, l + 32, ... in
-// order, then a fixed shuffle tree; deterministic for a given block count.
+// One warp per beam (a block of one warp each): lane l sums the partials of
+// blocks l, l + 32, ... in order, then a fixed shuffle tree; deterministic
+// for a given block count.
 __global__ void __launch_bounds__(kRefThreads)
 refine_finalize(const double* __restrict__ part, int blocks, int n_beam, double t,
                 double* __restrict__ mu_sigma, float* __restrict__ thresh) {
-  const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
-  for (int b = threadIdx.x >> 5; b < n_beam; b += warps) {
+  const int lane = threadIdx.x & 31, warps = (blockDim.x >> 5) * gridDim.x;
+  for (int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < n_beam; b += warps) {
     double cnt = 0.0, s1 = 0.0, s2 = 0.0;
     for (int k = lane; k < blocks; k += 32) {
       const double* o = part + ((size_t)k * n_beam + b) * 3;
@@ -137,7 +138,7 @@ cudaError_t launch_refine(mraid_plan_s* pl, const float* d_q1, const uint8_t* d_
   const int blocks = (int)(want < kRefBlocks ? (want < 1 ? 1 : want) : kRefBlocks);
   refine_partials<<<blocks, kRefThreads, 0, pl->stream>>>(d_q1, d_flags, pl->n_cells, pl->p.n_chan,
                                                           pl->d_keep, pl->p.n_beam, pl->d_refine_part);
-  refine_finalize<<<1, kRefThreads, 0, pl->stream>>>(pl->d_refine_part, blocks, pl->p.n_beam,
+  refine_finalize<<<pl->p.n_beam, 32, 0, pl->stream>>>(pl->d_refine_part, blocks, pl->p.n_beam,
                                                       pl->p.vec_t, d_mu_sigma, pl->d_refine_thresh);
   const int64_t g = (pl->n_cells + 255) / 256;
   refine_bits<<<(unsigned)(g < (int64_t)pl->sm_count * 16 ? g : (int64_t)pl->sm_count * 16), 256, 0,
