@@ -17,12 +17,15 @@
 //             transaction count), so streaming continues through epilogues;
 //   warps 4-7 convert each box to centred f16 operand tiles in the
 //             MN-major canonical layout (8 channels x 8 samples per core
-//             matrix), one tile per 8-channel group, into a 2-deep ring;
+//             matrix) into a 2-deep ring. A slot is one beam (slot N is the
+//             row of ones) across the 8 channels of a group; the slots are
+//             laid out as [g0 0..15][g0 16..N][g1 16..N][g1 0..15];
 //   warp 1    one thread issues tcgen05.mma (kind::f16, FP32 accumulate in
-//             TMEM): per group D1 = A(slots 0..15) x B(slots 0..N)^T and,
-//             for N >= 16, D2 = A(slots 16..31) x B(slots 16..N)^T; a slot is
-//             one beam (slot N is the row of ones) across 8 channels, so the
-//             useful entries of D are those with equal channel;
+//             TMEM): per group D1 = A(slots 0..15) x B(slots 0..N)^T, and
+//             for N >= 16 one D2 = A x B^T over the two groups' slots
+//             16..N together (the layout puts them side by side), so the
+//             extra rows cost one MMA instead of two half-empty ones; the
+//             useful entries of D are those with equal channel and group;
 //   warps 8-11 read TMEM (tcgen05.ld), keep each row's own-channel entries,
 //             and write the packed correlation (and optionally the sums).
 // Every wait is bounded (~2 s on the global timer); on expiry the kernel
@@ -31,7 +34,6 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
-#include <stdlib.h>
 
 #include <type_traits>
 
@@ -41,8 +43,8 @@ namespace mraid {
 namespace {
 
 constexpr int kBoxCh = 16;             // channels per TMA box (16 bytes)
-constexpr int kGroupSlots = 24;        // slots laid out per 8-channel group
-constexpr int kSlack = 8;              // slots after group 1 (A2 rows 24..31)
+constexpr int kGroupSlots = 24;        // slots of an 8-channel group at most (N + 1 <= 24)
+constexpr int kSlack = 8;              // spare zero slots after the two groups
 constexpr int kMaxNU = 16;             // u8 ring depth bound (sized at launch)
 constexpr int kMaxNF = 4;              // f16 ring depth bound
 constexpr size_t kSmemBudget = 227 * 1024;
@@ -53,7 +55,6 @@ struct TcCfg {
   static constexpr int kT = T_;
   static constexpr int kNF = NF_;
   static constexpr int kSlotBytes = kT * 16;  // one slot: kT samples x 8 channels x f16
-  static constexpr int kGroupBytes = kGroupSlots * kSlotBytes;
   static constexpr int kF16StageBytes = (2 * kGroupSlots + kSlack) * kSlotBytes;
   static_assert(kT % 16 == 0 && NF_ <= kMaxNF, "bad variant");
 };
@@ -66,9 +67,9 @@ constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 struct TcArgs {
   int n_beam, n_chan, n_samp_sub, sub0, n_sub;
   int n_u8;  // u8 ring depth (stages), fixed at launch with the shared-memory size
-  int rb;   // slots in B of the first MMA (N+1 rounded up to even)
-  int r2;   // slots in B of the second MMA (0 if N+1 <= 16), even
-  int swap_ls;  // nonzero: exchange the LBO / SBO fields of the descriptors
+  int R;    // slots per group: N + 1
+  int R2;   // slots 16..N per group (0 if N + 1 <= 16)
+  int rb;   // slots in B of the first MMAs (R rounded up to even)
   int64_t* sums;
   float* corr;
   unsigned long long* degenerate;
@@ -191,6 +192,16 @@ __device__ __forceinline__ void pick4(const uint32_t (&v)[32], int c, float* out
   }
 }
 
+// Slot position in an f16 stage: [g0 0..15][g0 16..R-1][g1 16..R-1][g1 0..15].
+__device__ __forceinline__ int slot_pos(int grp, int slot, int R, int R2) {
+  return grp == 0 ? slot : (slot < 16 ? R + R2 + slot : R + slot - 16);
+}
+// Beam slot of column block j of a group's first MMA (B = positions
+// 0..R-1 for group 0, R..2R-1 for group 1).
+__device__ __forceinline__ int d1_slot(int grp, int j, int R2) {
+  return grp == 0 ? j : (j < R2 ? 16 + j : j - R2);
+}
+
 struct Smem {
   uint64_t u8_full[kMaxNU], u8_empty[kMaxNU];
   uint64_t f16_full[kMaxNF], f16_empty[kMaxNF];
@@ -224,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
   using C = TcCfg<T_, NF_>;
   constexpr int kT = C::kT, kNF = C::kNF, kSlotBytes = C::kSlotBytes;
-  constexpr int kGroupBytes = C::kGroupBytes, kF16StageBytes = C::kF16StageBytes;
+  constexpr int kF16StageBytes = C::kF16StageBytes;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -254,18 +265,16 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
     mbar_init(&s->drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // constant slots of every f16 stage: the row of ones (slot N), zero rows
-  // above it, and the slack after group 1
+  // constant slots of every f16 stage: the rows of ones (slot N of each
+  // group) and zeros everywhere the converter does not write
   const uint32_t one2 = 0x3c003c00u;  // f16x2 (1.0, 1.0)
+  const int p_one0 = slot_pos(0, N, g.R, g.R2), p_one1 = slot_pos(1, N, g.R, g.R2);
   for (int st = 0; st < kNF; ++st) {
     uint32_t* w = reinterpret_cast<uint32_t*>(f16 + (size_t)st * kF16StageBytes);
-    for (int grp = 0; grp < 2; ++grp)
-      for (int i = threadIdx.x; i < (kGroupSlots - N) * kSlotBytes / 4; i += blockDim.x) {
-        const int slot = N + i / (kSlotBytes / 4);
-        w[(grp * kGroupBytes + N * kSlotBytes) / 4 + i] = (slot == N) ? one2 : 0u;
-      }
-    for (int i = threadIdx.x; i < kSlack * kSlotBytes / 4; i += blockDim.x)
-      w[(2 * kGroupBytes) / 4 + i] = 0u;
+    for (int i = threadIdx.x; i < kF16StageBytes / 4; i += blockDim.x) {
+      const int pos = i / (kSlotBytes / 4);
+      w[i] = (pos == p_one0 || pos == p_one1) ? one2 : 0u;
+    }
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if (warp == 2) {
@@ -304,10 +313,12 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
     if (lane == 0) {
       const uint32_t f16_base = smem_u32(f16);
       const uint32_t id1 = idesc_f16(128, 8 * g.rb);
-      const uint32_t id2 = idesc_f16(128, g.r2 > 0 ? 8 * g.r2 : 16);
+      const uint32_t id2 = idesc_f16(128, g.R2 > 0 ? 16 * g.R2 : 16);
+      const uint32_t pa1 = (uint32_t)(g.R + g.R2) * kSlotBytes;  // group 1: A1 and B1
+      const uint32_t pb1 = (uint32_t)g.R * kSlotBytes;
       // no-swizzle canonical layout: K-adjacent core matrices 128 B apart,
       // MN-adjacent (next slot) kSlotBytes apart
-      const uint32_t lbo = g.swap_ls ? kSlotBytes : 128, sbo = g.swap_ls ? 128 : kSlotBytes;
+      const uint32_t lbo = 128, sbo = kSlotBytes;
       uint32_t fcnt = 0, item_iter = 0;
       bool ok = true;
       for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x, ++item_iter) {
@@ -321,21 +332,17 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
           }
           fence_after();
           const uint32_t stage_addr = f16_base + (uint32_t)(fs * kF16StageBytes);
+          // TMEM: D1 of group 0 at column 0, of group 1 at 192, D2 at 384
 #pragma unroll
-          for (int grp = 0; grp < 2; ++grp) {
-            const uint32_t gaddr = stage_addr + grp * kGroupBytes;
-            const uint32_t d1 = tmem + grp * 256;
-            const uint32_t d2 = tmem + grp * 256 + 192;
-#pragma unroll
-            for (int ks = 0; ks < kT / 16; ++ks) {
-              const uint32_t koff = ks * 256;  // 16 samples = two 128-byte core matrices
-              const uint32_t acc = (st > 0 || ks > 0) ? 1u : 0u;
-              mma_f16(d1, smem_desc(gaddr + koff, lbo, sbo), smem_desc(gaddr + koff, lbo, sbo), id1,
-                      acc);
-              if (g.r2 > 0)
-                mma_f16(d2, smem_desc(gaddr + 16 * kSlotBytes + koff, lbo, sbo),
-                        smem_desc(gaddr + 16 * kSlotBytes + koff, lbo, sbo), id2, acc);
-            }
+          for (int ks = 0; ks < kT / 16; ++ks) {
+            const uint32_t a = stage_addr + ks * 256;  // 16 samples = two 128-byte core matrices
+            const uint32_t acc = (st > 0 || ks > 0) ? 1u : 0u;
+            mma_f16(tmem, smem_desc(a, lbo, sbo), smem_desc(a, lbo, sbo), id1, acc);
+            mma_f16(tmem + 192, smem_desc(a + pa1, lbo, sbo), smem_desc(a + pb1, lbo, sbo), id1,
+                    acc);
+            if (g.R2 > 0)
+              mma_f16(tmem + 384, smem_desc(a + 16 * kSlotBytes, lbo, sbo),
+                      smem_desc(a + 16 * kSlotBytes, lbo, sbo), id2, acc);
           }
           mma_commit(&s->f16_empty[fs]);  // stage buffer free once these MMAs finish
           if (st == stages - 1) mma_commit(&s->acc_full);
@@ -362,7 +369,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
         for (int r = ct; r < N * kT; r += kConvThreads) {
           const uint4 w = src[r];  // 16 channels of beam b at sample t
           const int b = r / kT, t = r % kT;
-          const uint32_t off = b * kSlotBytes + (t / 8) * 128 + (t % 8) * 16;
+          const uint32_t off = (t / 8) * 128 + (t % 8) * 16;
+          const uint32_t off0 = (uint32_t)b * kSlotBytes + off;
+          const uint32_t off1 = (uint32_t)slot_pos(1, b, g.R, g.R2) * kSlotBytes + off;
           uint4 o0, o1;
           asm("sub.f16x2 %0, %1, %2;" : "=r"(o0.x) : "r"(__byte_perm(w.x, magic, 0x4140)), "r"(bias));
           asm("sub.f16x2 %0, %1, %2;" : "=r"(o0.y) : "r"(__byte_perm(w.x, magic, 0x4342)), "r"(bias));
@@ -372,8 +381,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
           asm("sub.f16x2 %0, %1, %2;" : "=r"(o1.y) : "r"(__byte_perm(w.z, magic, 0x4342)), "r"(bias));
           asm("sub.f16x2 %0, %1, %2;" : "=r"(o1.z) : "r"(__byte_perm(w.w, magic, 0x4140)), "r"(bias));
           asm("sub.f16x2 %0, %1, %2;" : "=r"(o1.w) : "r"(__byte_perm(w.w, magic, 0x4342)), "r"(bias));
-          *reinterpret_cast<uint4*>(dst + off) = o0;
-          *reinterpret_cast<uint4*>(dst + kGroupBytes + off) = o1;
+          *reinterpret_cast<uint4*>(dst + off0) = o0;
+          *reinterpret_cast<uint4*>(dst + off1) = o1;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&s->u8_empty[us]);
@@ -384,26 +393,30 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
     // ------------------------------------------------------------ epilogue
     const int q = warp - 8;              // TMEM lane quarter (warp % 4)
     const int c = lane % 8;              // channel within the group
-    const int slot = 4 * q + lane / 8;   // D1 row slot (beam a, 0..15)
-    const int slot2 = 16 + 4 * q + lane / 8;  // D2 row slot (TMEM lane 32q + lane)
+    const int slot = 4 * q + lane / 8;   // D1 row slot (beam a, 0..15), both groups
+    // D2 row of this lane: stage position 16 + 4q + lane/8, which holds
+    // slot 16.. of group 0, then slot 16.. of group 1, then nothing useful
+    const int p2 = 4 * q + lane / 8;     // position - 16
+    const int g2 = p2 < g.R2 ? 0 : (p2 < 2 * g.R2 ? 1 : -1);
+    const int slot2 = 16 + (g2 == 1 ? p2 - g.R2 : p2);
     const int64_t n = g.n_samp_sub;
+    const int R = g.R, R2 = g.R2;
     uint32_t item_iter = 0;
     bool ok = true;
     for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x, ++item_iter) {
       ok = mbar_wait(&s->acc_full, item_iter & 1, g.error);
       if (!ok) break;
       fence_after();
-      float row[2][kGroupSlots];   // D1 row `slot`: G[slot][0..rb)
-      float row2[2][8];            // D2 row `slot2`: G[slot2][16..16+r2)
+      float row[2][kGroupSlots];   // D1 row `slot` of each group, by column block
+      float row2[16];              // D2 row `slot2`, by column block
 #pragma unroll
       for (int grp = 0; grp < 2; ++grp) {
-        // D1 row: chunks of 32 columns (4 slots x 8 channels), one load in
-        // flight per wait to keep the register count low
+        // chunks of 32 columns (4 blocks x 8 channels), one load in flight
 #pragma unroll
         for (int ch = 0; ch < kGroupSlots / 4; ++ch) {
           if (ch * 4 < g.rb) {
             uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + grp * 256 + ch * 32, v);
+            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + grp * 192 + ch * 32, v);
             tmem_wait_ld();
             pick4(v, c, &row[grp][4 * ch]);
           } else {
@@ -411,131 +424,112 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
             for (int u = 0; u < 4; ++u) row[grp][4 * ch + u] = 0.f;
           }
         }
+      }
 #pragma unroll
-        for (int ch = 0; ch < 2; ++ch) {
-          if (g.r2 > 4 * ch) {
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + grp * 256 + 192 + ch * 32, v);
-            tmem_wait_ld();
-            pick4(v, c, &row2[grp][4 * ch]);
-          } else {
+      for (int ch = 0; ch < 4; ++ch) {
+        if (2 * R2 > 4 * ch) {
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + 384 + ch * 32, v);
+          tmem_wait_ld();
+          pick4(v, c, &row2[4 * ch]);
+        } else {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) row2[grp][4 * ch + u] = 0.f;
-          }
+          for (int u = 0; u < 4; ++u) row2[4 * ch + u] = 0.f;
         }
       }
       fence_before();
       mbar_arrive(&s->acc_empty);  // accumulators may be overwritten now
-      // entries at runtime positions, fetched with compile-time indices:
-      // G[a][N] (row sum) and G[a][a] for the D1 row and the D2 row
-      float sumN[2], diag[2], sumN2[2], diag2[2];
+      // G[a][N] (row sum) and G[a][a] from each row, picked with
+      // compile-time register indices and runtime block -> slot maps
+      float sumN[2], diag[2], sumN2 = 0.f, diag2 = 0.f;
 #pragma unroll
       for (int grp = 0; grp < 2; ++grp) {
-        sumN[grp] = diag[grp] = sumN2[grp] = diag2[grp] = 0.f;
+        sumN[grp] = diag[grp] = 0.f;
 #pragma unroll
-        for (int b = 0; b < kGroupSlots; ++b) {
-          if (b == N) sumN[grp] = row[grp][b];
-          if (b == slot) diag[grp] = row[grp][b];
+        for (int jb = 0; jb < kGroupSlots; ++jb) {
+          const int b = d1_slot(grp, jb, R2);
+          if (jb < R && b == N) sumN[grp] = row[grp][jb];
+          if (jb < R && b == slot) diag[grp] = row[grp][jb];
         }
+      }
+      // D2 columns: blocks 0..R2-1 are group 0 slots 16.., then group 1's
+      const int jb2 = g2 == 1 ? R2 : 0;
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          if (b == N - 16) sumN2[grp] = row2[grp][b];
-          if (b == slot2 - 16) diag2[grp] = row2[grp][b];
-        }
+      for (int jb = 0; jb < 16; ++jb) {
+        if (jb - jb2 == N - 16) sumN2 = row2[jb];
+        if (jb - jb2 == slot2 - 16) diag2 = row2[jb];
       }
 
       const int k = (int)(it / chunks), ch0 = (int)(it % chunks) * kBoxCh;
       // row sums and inverse standard deviations, shared through smem
+      auto table = [&](int grp, int a, float sum_a, float diag_a) {
+        const int64_t sa = (int64_t)sum_a;
+        const int64_t var = n * (int64_t)diag_a - sa * sa;
+        s->s_sum[grp][c][a] = (int32_t)sa;
+        float inv = 0.f;
+        if (a < N) {
+          if (var > 0) {
+            const float vf = (float)var;
+            inv = rsqrtf(vf);
+            inv = inv * (1.5f - 0.5f * vf * inv * inv);
+          } else {
+            atomicAdd(g.degenerate, 1ull);
+          }
+        }
+        s->s_inv[grp][c][a] = inv;
+      };
 #pragma unroll
-      for (int grp = 0; grp < 2; ++grp) {
-        if (slot < N + 1) {
-          const int64_t sa = (int64_t)sumN[grp];
-          const int64_t var = n * (int64_t)diag[grp] - sa * sa;
-          s->s_sum[grp][c][slot] = (int32_t)sa;
-          float inv = 0.f;
-          if (slot < N) {
-            if (var > 0) {
-              const float vf = (float)var;
-              inv = rsqrtf(vf);
-              inv = inv * (1.5f - 0.5f * vf * inv * inv);
-            } else {
-              atomicAdd(g.degenerate, 1ull);
-            }
-          }
-          s->s_inv[grp][c][slot] = inv;
-        }
-        if (g.r2 > 0 && slot2 < N + 1) {
-          const int64_t sa = (int64_t)sumN2[grp];
-          const int64_t var = n * (int64_t)diag2[grp] - sa * sa;
-          s->s_sum[grp][c][slot2] = (int32_t)sa;
-          float inv = 0.f;
-          if (slot2 < N) {
-            if (var > 0) {
-              const float vf = (float)var;
-              inv = rsqrtf(vf);
-              inv = inv * (1.5f - 0.5f * vf * inv * inv);
-            } else {
-              atomicAdd(g.degenerate, 1ull);
-            }
-          }
-          s->s_inv[grp][c][slot2] = inv;
-        }
-      }
+      for (int grp = 0; grp < 2; ++grp)
+        if (slot < N + 1) table(grp, slot, sumN[grp], diag[grp]);
+      if (g2 >= 0 && slot2 < N + 1) table(g2, slot2, sumN2, diag2);
       named_sync(1, kEpiThreads);
-#pragma unroll
-      for (int grp = 0; grp < 2; ++grp) {
+      // one packed output row: a, its group, its values by column block and
+      // the slot of each block (b < 0: not this group's)
+      auto emit = [&](int grp, int a, const float* rv, auto nb_c, auto slot_of) {
+        constexpr int NB = decltype(nb_c)::value;
         const int64_t cell = (int64_t)k * g.n_chan + ch0 + grp * 8 + c;
-        // row a of the packed outputs from the D1 row (a = slot, b in
-        // [0, rb)) or the D2 row (a = slot2, b in [16, 16 + r2)); the row
-        // values have compile-time indices, so the two passes are separate
-        // instantiations
-        auto emit = [&](auto pass_c, const float(&rv)[kGroupSlots], int nb) {
-          constexpr int pass = decltype(pass_c)::value;
-          constexpr int b0 = pass == 0 ? 0 : 16;
-          const int a = pass == 0 ? slot : slot2;
-          if (a > N) return;
-          const int64_t sa = s->s_sum[grp][c][a];
-          const float inva = s->s_inv[grp][c][a];
-          if (g.corr && a < N) {
-            float* dst = g.corr + cell * (int64_t)(N * (N + 1) / 2) + (a * N - a * (a - 1) / 2);
+        const int64_t sa = s->s_sum[grp][c][a];
+        const float inva = s->s_inv[grp][c][a];
+        if (g.corr && a < N) {
+          float* dst = g.corr + cell * (int64_t)(N * (N + 1) / 2) + (a * N - a * (a - 1) / 2);
 #pragma unroll
-            for (int j = 0; j < kGroupSlots; ++j) {
-              const int b = b0 + j;
-              if (b < a || b >= N || j >= nb) continue;
-              float r;
-              if (b == a) {
-                r = 1.f;
-              } else {
-                const int64_t cov = n * (int64_t)rv[j] - sa * (int64_t)s->s_sum[grp][c][b];
-                r = (float)cov * inva * s->s_inv[grp][c][b];
-              }
-              dst[b - a] = r;
+          for (int jb = 0; jb < NB; ++jb) {
+            const int b = slot_of(jb);
+            if (b < a || b >= N) continue;
+            float r;
+            if (b == a) {
+              r = 1.f;
+            } else {
+              const int64_t cov = n * (int64_t)rv[jb] - sa * (int64_t)s->s_sum[grp][c][b];
+              r = (float)cov * inva * s->s_inv[grp][c][b];
             }
+            dst[b - a] = r;
           }
-          if (g.sums) {
-            const int N1 = N + 1;
-            int64_t* dst = g.sums + cell * (int64_t)(N1 * (N1 + 1) / 2) + (a * N1 - a * (a - 1) / 2);
-#pragma unroll
-            for (int j = 0; j < kGroupSlots; ++j) {
-              const int b = b0 + j;
-              if (b < a || b > N || j >= nb) continue;
-              const int64_t gab = (int64_t)rv[j];
-              int64_t v;
-              if (a == N) v = n;                                  // (N, N): sample count
-              else if (b == N) v = gab + 128 * n;                 // S_a
-              else v = gab + 128 * (sa + (int64_t)s->s_sum[grp][c][b]) + 16384 * n;
-              dst[b - a] = v;
-            }
-          }
-        };
-        emit(std::integral_constant<int, 0>{}, row[grp], g.rb);
-        if (g.r2 > 0) {
-          float r2v[kGroupSlots];
-#pragma unroll
-          for (int j = 0; j < kGroupSlots; ++j) r2v[j] = j < 8 ? row2[grp][j] : 0.f;
-          emit(std::integral_constant<int, 1>{}, r2v, g.r2);
         }
-      }
+        if (g.sums) {
+          const int N1 = N + 1;
+          int64_t* dst = g.sums + cell * (int64_t)(N1 * (N1 + 1) / 2) + (a * N1 - a * (a - 1) / 2);
+#pragma unroll
+          for (int jb = 0; jb < NB; ++jb) {
+            const int b = slot_of(jb);
+            if (b < a || b > N) continue;
+            const int64_t gab = (int64_t)rv[jb];
+            int64_t v;
+            if (a == N) v = n;                                  // (N, N): sample count
+            else if (b == N) v = gab + 128 * n;                 // S_a
+            else v = gab + 128 * (sa + (int64_t)s->s_sum[grp][c][b]) + 16384 * n;
+            dst[b - a] = v;
+          }
+        }
+      };
+#pragma unroll
+      for (int grp = 0; grp < 2; ++grp)
+        if (slot <= N)
+          emit(grp, slot, row[grp], std::integral_constant<int, kGroupSlots>{},
+               [&](int jb) { return jb < R ? d1_slot(grp, jb, R2) : -1; });
+      if (g2 >= 0 && slot2 <= N)
+        emit(g2, slot2, row2, std::integral_constant<int, 16>{},
+             [&](int jb) { return (jb >= jb2 && jb < jb2 + R2) ? 16 + jb - jb2 : -1; });
       named_sync(1, kEpiThreads);  // smem tables reused by the next item
     }
   }
@@ -571,18 +565,6 @@ EncodeTiledFn encode_fn() {
 // 2 f16 stages}, 1 = {32, 4}, 2 = {32, 2}.
 int tc_variant_samples(int v) { return (v == 1 || v == 2) ? 32 : 64; }
 
-namespace {
-
-int tc_swap_ls() {
-  static int v = -1;
-  if (v < 0) {
-    const char* e = getenv("MRAID_TC_SWAP_LS");
-    v = (e && e[0] == '1') ? 1 : 0;
-  }
-  return v;
-}
-
-}  // namespace
 
 bool gram_tc_supported(const mraid_plan_s* pl, const void* d_data) {
   const mraid_params& p = pl->p;
@@ -616,9 +598,9 @@ cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int su
   a.sub0 = sub0;
   a.n_sub = n_sub;
   const int R = p.n_beam + 1;              // beams + the row of ones
-  a.rb = (R + 1) / 2 * 2;                  // B of the first MMA: slots 0..R-1, even count
-  a.r2 = R > 16 ? ((R - 16) + 1) / 2 * 2 : 0;
-  a.swap_ls = tc_swap_ls();
+  a.R = R;
+  a.R2 = R > 16 ? R - 16 : 0;
+  a.rb = (R + 1) / 2 * 2;                  // B of the first MMAs: R slots, even count
   a.sums = d_sums;
   a.corr = d_corr;
   a.degenerate = pl->d_degenerate;
