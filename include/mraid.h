@@ -187,19 +187,19 @@ mraid_status mraid_run_host(mraid_plan_t plan, const void* h_data, float* h_stat
 
 /* Autotuner (the paper has no counterpart; it picks among this library's
  * kernel variants). Times, `reps` runs each on d_data, every Gram variant
- * that fits the plan's shape (tensor-core tiles of 64 samples x 2 stages,
- * 32 x 4 and 32 x 2, and the CUDA-core Gram) and the three register
+ * that fits the plan's shape (eight tensor-core variants over samples per
+ * stage, f16 stages and converter unrolling, and the CUDA-core Gram) and the register
  * eigensolvers (Jacobi rounds in a loop; the Jacobi sweep unrolled;
  * Householder tridiagonalisation + implicit QR in two code layouts), and
  * keeps the fastest of each for this plan. *gram_choice: -1 = CUDA-core,
- * 0..2 tiles; *eig_choice: 0..3. report (may be NULL) receives "g<id>:ms;e<id>:ms;...".
+ * 0..7 tensor-core variants; *eig_choice: 0..3. report (may be NULL) receives "g<id>:ms;e<id>:ms;...".
  * Synchronous. */
 mraid_status mraid_autotune(mraid_plan_t plan, const void* d_data, int32_t reps,
                             int32_t* gram_choice, int32_t* eig_choice, char* report,
                             int32_t report_len);
 
 /* Select variants by id (e.g. from a tuning cache). Gram: -1 = CUDA-core,
- * 0..2 tensor-core tiles (ignored where the shape does not fit).
+ * 0..7 tensor-core variants (ignored where the shape does not fit).
  * Eigensolver (beam counts with a one-thread-per-matrix kernel: 2, 3, 4, 13,
  * 19; other counts always use the warp-per-matrix Jacobi): 0 = Jacobi,
  * looped rounds; 1 = Jacobi, unrolled sweep; 2 = Householder reduction to

@@ -4,7 +4,8 @@
 //
 // One cooperative launch runs the whole iteration on the device: every pass
 // masks the cells above the previous threshold, reduces (count, sum s,
-// sum s^2) over the cells still unmasked and unpreserved in FP64, and
+// sum s^2) over the cells still unmasked and unpreserved (per thread in
+// FP32 over its ~10 cells, then in FP64), and
 // derives mu, sigma (population) and mu + k sigma. The fit stops when a
 // pass masks nothing new (the unmasked count is unchanged) or after
 // max_clip_iter fits. Block partial sums are combined in a fixed order by
@@ -101,21 +102,25 @@ __global__ void __launch_bounds__(kFlagThreads) flag_kernel(FlagArgs f) {
   double prev_count = -1.0, used = 0.0;
   int fits = 0, converged = 0;
   for (int pass = 0;; ++pass) {
-    double cnt = 0.0, s1 = 0.0, s2 = 0.0;
+    // a thread's few cells sum in FP32 (GB300 runs FP64 at a small fraction
+    // of the FP32 rate); blocks and the grid combine in FP64, fixed order
+    int cnt_t = 0;
+    float s1_t = 0.f, s2_t = 0.f;
     for (int64_t i = tid; i < f.n_cells; i += nthr) {
       if (f.keep && f.keep[(uint32_t)i % (uint32_t)f.n_chan]) continue;
-      const double v = (double)f.stat[i];
+      const float v = f.stat[i];
       uint8_t m = f.flags[i];
-      if (!m && v > thresh) {
+      if (!m && (double)v > thresh) {
         m = 1;
         f.flags[i] = 1;
       }
       if (!m) {
-        cnt += 1.0;
-        s1 += v;
-        s2 = fma(v, v, s2);
+        ++cnt_t;
+        s1_t += v;
+        s2_t = fmaf(v, v, s2_t);
       }
     }
+    double cnt = (double)cnt_t, s1 = (double)s1_t, s2 = (double)s2_t;
     block_sum3(cnt, s1, s2, red);
     double* part = f.partials + (size_t)(pass & 1) * gridDim.x * 3;
     if (threadIdx.x == 0) {

@@ -44,18 +44,17 @@ namespace {
 
 constexpr int kBoxCh = 16;             // channels per TMA box (16 bytes)
 constexpr int kGroupSlots = 24;        // slots of an 8-channel group at most (N + 1 <= 24)
-constexpr int kSlack = 8;              // spare zero slots after the two groups
 constexpr int kMaxNU = 16;             // u8 ring depth bound (sized at launch)
 constexpr int kMaxNF = 4;              // f16 ring depth bound
 constexpr size_t kSmemBudget = 227 * 1024;
 
 // Tile shape of one kernel variant: T samples per stage, NF f16 stages.
-template <int T_, int NF_>
+template <int T_, int NF_, int U_ = 1>
 struct TcCfg {
   static constexpr int kT = T_;
   static constexpr int kNF = NF_;
+  static constexpr int kUnroll = U_;  // converter loop unrolling
   static constexpr int kSlotBytes = kT * 16;  // one slot: kT samples x 8 channels x f16
-  static constexpr int kF16StageBytes = (2 * kGroupSlots + kSlack) * kSlotBytes;
   static_assert(kT % 16 == 0 && NF_ <= kMaxNF, "bad variant");
 };
 constexpr int kThreads = 384;
@@ -211,14 +210,23 @@ struct Smem {
   float s_inv[2][8][kGroupSlots];     // 1/sqrt(var_a), 0 if var_a == 0
 };
 
-// u8 ring depth for n_beam beams: as deep as the shared memory allows
-// (less `reserve` bytes left for a kernel running beside this one), so TMA
-// keeps streaming while the MMAs pause for an epilogue
+// Slots of one f16 stage for n_beam beams: both groups (2R positions, one
+// more for the even B width when R is odd) and at least the 32 positions
+// the extra-slot MMA reads.
+__host__ __device__ constexpr int stage_slots(int n_beam) {
+  return (2 * (n_beam + 1) + ((n_beam + 1) & 1)) > 32 ? (2 * (n_beam + 1) + ((n_beam + 1) & 1)) : 32;
+}
 template <class C>
-__host__ __device__ constexpr int u8_ring_depth(int n_beam, size_t reserve) {
-  return (int)((kSmemBudget - reserve - 1024 - (size_t)C::kNF * C::kF16StageBytes - sizeof(Smem)) /
+__host__ __device__ constexpr size_t f16_stage_bytes(int n_beam) {
+  return (size_t)stage_slots(n_beam) * C::kSlotBytes;
+}
+// u8 ring depth for n_beam beams: as deep as the shared memory allows, so
+// TMA keeps streaming while the MMAs pause for an epilogue
+template <class C>
+__host__ __device__ constexpr int u8_ring_depth(int n_beam) {
+  return (int)((kSmemBudget - 1024 - (size_t)C::kNF * f16_stage_bytes<C>(n_beam) - sizeof(Smem)) /
                ((size_t)n_beam * C::kT * kBoxCh)) < kMaxNU
-             ? (int)((kSmemBudget - reserve - 1024 - (size_t)C::kNF * C::kF16StageBytes -
+             ? (int)((kSmemBudget - 1024 - (size_t)C::kNF * f16_stage_bytes<C>(n_beam) -
                       sizeof(Smem)) /
                      ((size_t)n_beam * C::kT * kBoxCh))
              : kMaxNU;
@@ -226,16 +234,16 @@ __host__ __device__ constexpr int u8_ring_depth(int n_beam, size_t reserve) {
 // dynamic shared memory for n_beam beams and a ring of n_u8 stages
 template <class C>
 __host__ __device__ constexpr size_t smem_bytes(int n_beam, int n_u8) {
-  return 1024 /* alignment slack */ + (size_t)C::kNF * C::kF16StageBytes +
+  return 1024 /* alignment slack */ + (size_t)C::kNF * f16_stage_bytes<C>(n_beam) +
          (size_t)n_u8 * n_beam * C::kT * kBoxCh + sizeof(Smem);
 }
 
-template <int T_, int NF_>
+template <int T_, int NF_, int U_>
 __global__ void __launch_bounds__(kThreads, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
-  using C = TcCfg<T_, NF_>;
+  using C = TcCfg<T_, NF_, U_>;
   constexpr int kT = C::kT, kNF = C::kNF, kSlotBytes = C::kSlotBytes;
-  constexpr int kF16StageBytes = C::kF16StageBytes;
+  const int kF16StageBytes = (int)f16_stage_bytes<C>(g.n_beam);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -366,6 +374,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
         if (!ok) break;
         const uint4* src = reinterpret_cast<const uint4*>(u8 + (size_t)us * u8_stage_bytes);
         unsigned char* dst = f16 + (size_t)fs * kF16StageBytes;
+#pragma unroll C::kUnroll
         for (int r = ct; r < N * kT; r += kConvThreads) {
           const uint4 w = src[r];  // 16 channels of beam b at sample t
           const int b = r / kT, t = r % kT;
@@ -561,9 +570,18 @@ EncodeTiledFn encode_fn() {
 
 }  // namespace
 
-// Stage length (samples) of tensor-core Gram variant v: 0 = {64 samples,
-// 2 f16 stages}, 1 = {32, 4}, 2 = {32, 2}.
+// Tensor-core Gram variants {samples per stage, f16 stages, converter
+// unrolling}: 0 = {64, 2, 1}, 1 = {32, 4, 1}, 2 = {32, 2, 1}, 3 = {64, 3, 1},
+// 4 = {64, 2, 2}, 5 = {64, 3, 2}, 6 = {64, 4, 1}, 7 = {64, 4, 2}.
 int tc_variant_samples(int v) { return (v == 1 || v == 2) ? 32 : 64; }
+
+// Untuned default: four f16 stages of 64 samples where that still leaves
+// an u8 ring of at least three stages (measured fastest for 19 beams),
+// else two.
+int tc_default_variant(int n_beam) {
+  if (n_beam < 2 || n_beam + 1 > kGroupSlots) return 0;
+  return u8_ring_depth<TcCfg<64, 4, 1>>(n_beam) >= 3 ? 6 : 0;
+}
 
 
 bool gram_tc_supported(const mraid_plan_s* pl, const void* d_data) {
@@ -608,21 +626,26 @@ cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int su
   const int64_t items = (int64_t)n_sub * (p.n_chan / kBoxCh);
   const int grid = (int)(items < pl->sm_count ? items : pl->sm_count);
   cudaError_t e = cudaSuccess;
-#define MRAID_TC_LAUNCH(T, NF)                                                                   \
+#define MRAID_TC_LAUNCH(T, NF, U)                                                                 \
   do {                                                                                           \
-    using C_ = TcCfg<T, NF>;                                                                     \
-    const int n_u8 = u8_ring_depth<C_>(p.n_beam, 0);                                             \
+    using C_ = TcCfg<T, NF, U>;                                                                     \
+    const int n_u8 = u8_ring_depth<C_>(p.n_beam);                                                \
     a.n_u8 = n_u8;                                                                               \
     const size_t smem = smem_bytes<C_>(p.n_beam, n_u8);                                          \
-    e = cudaFuncSetAttribute(gram_tc_kernel<T, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+    e = cudaFuncSetAttribute(gram_tc_kernel<T, NF, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              (int)smem);                                                         \
     if (e == cudaSuccess && grid > 0)                                                            \
-      gram_tc_kernel<T, NF><<<grid, kThreads, smem, pl->stream>>>(map, a);                       \
+      gram_tc_kernel<T, NF, U><<<grid, kThreads, smem, pl->stream>>>(map, a);                       \
   } while (0)
   switch (pl->tc_variant) {
-    case 1: MRAID_TC_LAUNCH(32, 4); break;
-    case 2: MRAID_TC_LAUNCH(32, 2); break;
-    default: MRAID_TC_LAUNCH(64, 2); break;
+    case 1: MRAID_TC_LAUNCH(32, 4, 1); break;
+    case 2: MRAID_TC_LAUNCH(32, 2, 1); break;
+    case 3: MRAID_TC_LAUNCH(64, 3, 1); break;
+    case 4: MRAID_TC_LAUNCH(64, 2, 2); break;
+    case 5: MRAID_TC_LAUNCH(64, 3, 2); break;
+    case 6: MRAID_TC_LAUNCH(64, 4, 1); break;
+    case 7: MRAID_TC_LAUNCH(64, 4, 2); break;
+    default: MRAID_TC_LAUNCH(64, 2, 1); break;
   }
 #undef MRAID_TC_LAUNCH
   if (e != cudaSuccess) return e;

@@ -79,7 +79,7 @@ struct mraid_plan_s {
   cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
   mraid::Profiler prof;
   bool force_dp4a = false;  // use the CUDA-core Gram even where tcgen05 fits
-  int tc_variant = 0;       // tensor-core Gram tile variant (autotuned)
+  int tc_variant = 0;       // tensor-core Gram variant (tc_default_variant, or autotuned)
   int eig_variant = 3;      // register kernels: 0 = Jacobi, looped rounds; 1 = Jacobi,
                             // unrolled sweep; 2 = Householder + implicit QR, one
                             // step copy per level; 3 = the same, one masked copy
@@ -113,7 +113,8 @@ cudaError_t launch_gram_f32(const mraid_plan_s* pl, const float* d_data, int sub
 // may be null. cudaErrorNotSupported when the shape or layout does not fit.
 bool gram_tc_supported(const mraid_plan_s* pl, const void* d_data);
 int tc_variant_samples(int v);
-constexpr int kTcVariants = 3;
+int tc_default_variant(int n_beam);
+constexpr int kTcVariants = 8;
 constexpr int kEigVariants = 4;  // register eigensolvers (see eig_variant)
 cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int sub0, int n_sub,
                            int64_t* d_sums, float* d_corr);

@@ -364,6 +364,7 @@ mraid_status mraid_plan(const mraid_params* p, void* stream, mraid_plan_t* out) 
   }
   pl->p = *p;
   pl->p.keep = nullptr;
+  pl->tc_variant = tc_default_variant(p->n_beam);
   pl->stream = static_cast<cudaStream_t>(stream);
   pl->n_cells = (int64_t)p->n_sub * p->n_chan;
   pl->beam_stride = p->beam_stride ? p->beam_stride : (int64_t)p->n_sub * p->n_samp_sub * p->n_chan;
