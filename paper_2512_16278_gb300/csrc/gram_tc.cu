@@ -104,14 +104,27 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// The same with a suspend-time hint: a thread whose phase has not completed
+// sleeps in hardware (woken when it completes, or after about 2 us), so
+// waiting warps do not take issue slots from the working ones.
+__device__ __forceinline__ bool mbar_try_suspend(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(2000u)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait for the phase of `parity` to complete; false on timeout or
 // when another role already reported an error.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* error) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = gtimer();
   for (uint32_t i = 0;; ++i) {
-    if (mbar_try(bar, parity)) return true;
-    if ((i & 255) == 255) {
+    if (mbar_try_suspend(bar, parity)) return true;
+    if ((i & 15) == 15) {
       if (*(volatile unsigned*)error) return false;
       if (gtimer() - t0 > kWaitNs) {
         atomicOr(error, 1u);
