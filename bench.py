@@ -262,12 +262,14 @@ def torch_index(idx):
 
 # ------------------------------------------------------------- main arms
 
-def bench_f32(m, torch, d_u8, cfg, stream, n_sub):
+def bench_f32(m, torch, d_u8, cfg, stream, n_sub, peaks):
     """Float32-input variant (beamformer output, bit_depth 32) on the first
     n_sub sub-integrations of the same block, converted on the device to
     (x - 128) / 20 (zero-mean, unit-variance noise with the same RFI): cells/s
-    of the whole path, and its eigenvalue error against the oracle (FP64
-    covariance of the float32 samples) on a sample of cells."""
+    of the whole path with the tensor-core Gram (split-bf16 products) and
+    with the CUDA-core FP32 Gram, the tensor-core kernel's HBM roofline, and
+    the eigenvalue error of both against the oracle (FP64 covariance of the
+    float32 samples) on a sample of cells."""
     import numpy as np
     import oracle
     N, C, S = cfg.n_beam, cfg.n_chan, cfg.n_samp_sub
@@ -281,39 +283,60 @@ def bench_f32(m, torch, d_u8, cfg, stream, n_sub):
         st = torch.empty(cells, dtype=torch.float32, device="cuda")
         fl = torch.empty(cells, dtype=torch.uint8, device="cuda")
     info = m.FlagInfo()
-    for _ in range(3):
-        m.mraid_run(plan.handle, x, ev, q, st, fl, info)
-    m.mraid_sync(plan.handle)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(5):
-        m.mraid_run(plan.handle, x, ev, q, st, fl, info)
-    e1.record(stream)
-    m.mraid_sync(plan.handle)
-    ms = e0.elapsed_time(e1) / 5
     rng = np.random.default_rng(7)
     idx = rng.integers(0, cells, size=256)
-    evh = ev.cpu().numpy()
-    err = []
+    ref = {}
     for i in idx:
         k, c = int(i // C), int(i % C)
         # this cell's samples as a one-channel block [beam][time][1]
         cell = x[:, k * S:(k + 1) * S, c:c + 1].contiguous().cpu().numpy()
         r, _ = oracle.corr_from_cov(oracle.cell_cov_f32(cell, S, 0, 0))
-        eo = oracle.jacobi(r)[0]
-        err.append(float(np.abs(evh[i] - eo).max() / np.abs(eo).max()))
+        ref[int(i)] = oracle.jacobi(r)[0]
+    in_bytes = N * T * C * 4
+    out = {"workload": f"float32 [{N}][{T}][{C}] ({n_sub} sub-integrations, "
+                       f"{in_bytes / 1e9:.2f} GB)", "sampled_cells": len(idx)}
+    for gram, tag in ((0, "tensor_cores"), (-1, "cuda_cores")):
+        m.mraid_set_variant(plan.handle, gram)
+        for _ in range(3):
+            m.mraid_run(plan.handle, x, ev, q, st, fl, info)
+        m.mraid_sync(plan.handle)
+        m.mraid_profile_reset(plan.handle)
+        m.mraid_profile_enable(plan.handle, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            m.mraid_run(plan.handle, x, ev, q, st, fl, info)
+        e1.record(stream)
+        m.mraid_sync(plan.handle)
+        m.mraid_profile_enable(plan.handle, False)
+        prof = m.mraid_profile_read(plan.handle)
+        ms = e0.elapsed_time(e1) / 5
+        evh = ev.cpu().numpy()
+        err = [float(np.abs(evh[i] - eo).max() / np.abs(eo).max()) for i, eo in ref.items()]
+        kern = "gram_tc_f32" if gram == 0 else "gram_f32"
+        n_l, tot = prof.get(kern, (0, 0.0))
+        res = {"ms_per_step": ms, "cells_per_s": cells / (ms / 1e3),
+               "gbs": in_bytes / (ms / 1e3) / 1e9,
+               "eig_err_rel_max": max(err), "eig_err_rel_p99": float(np.percentile(err, 99)),
+               "gram_kernel": kern, "gram_launches": n_l}
+        if n_l > 0:
+            kms = tot / n_l
+            b = in_bytes + cells * 4 * (N * (N + 1) // 2)      # samples in, r out
+            a = b / (kms / 1e3) / 1e9
+            res["gram_roofline"] = {"bound": "hbm", "kernel": kern, "achieved": a,
+                                    "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                    "frac": a / peaks["hbm_gbs"],
+                                    "traffic": kernel_traffic(kern),
+                                    "work_per_launch": b, "ms_per_launch": kms}
+        out[tag] = res
+    out["path"] = ("Gram of per-beam shifted samples: tensor cores with bf16 hi/lo products "
+                   "(four MMAs per 16 samples) or FP32 CUDA cores; FP32 eigensolver "
+                   "(the 8-bit path's error is in sampled_parity)")
     plan.close()
     del x
     torch.cuda.empty_cache()
-    return {"workload": f"float32 [19][{T}][{C}] ({n_sub} sub-integrations, "
-                        f"{N * T * C * 4 / 1e9:.2f} GB)",
-            "ms_per_step": ms, "cells_per_s": cells / (ms / 1e3),
-            "gbs": N * T * C * 4 / (ms / 1e3) / 1e9,
-            "eig_err_rel_max": max(err), "eig_err_rel_p99": float(np.percentile(err, 99)),
-            "sampled_cells": len(err),
-            "path": "FP32 sums of per-beam shifted samples on CUDA cores, FP32 eigensolver "
-                    "(the 8-bit path's error is in sampled_parity)"}
+    return out
 
 
 def bench_batched(m, torch, stream, steps):
@@ -651,7 +674,7 @@ def run_mraid(args):
                                            for x in bits.view(-1).cpu().tolist()))}
     precision = None
     if world == 1 and args.f32_subs > 0:
-        precision = bench_f32(m, torch, d, cfg, stream, args.f32_subs)
+        precision = bench_f32(m, torch, d, cfg, stream, args.f32_subs, peaks)
     plan.close()
     del d, h
     torch.cuda.empty_cache()

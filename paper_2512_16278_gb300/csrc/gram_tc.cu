@@ -32,6 +32,7 @@
 // records an error word, drains its in-flight copies and MMAs (again
 // bounded), frees its TMEM and returns.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -563,6 +564,363 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Float32 samples (beamformer output) on the same tensor cores. Each sample,
+// shifted by its cell's first sample of the same beam and channel (the
+// covariance does not depend on a per-beam shift, and the shift keeps the
+// sums near zero mean so that n G_ab - G_a G_b does not cancel), is split
+// into bf16 parts hi = RN(x) and lo = RN(x - hi), so x = hi + lo to a
+// relative 2^-16. The four products hi hi^T, hi lo^T, lo hi^T and lo lo^T
+// accumulate in FP32 in TMEM, which leaves the representation error of the
+// split as the only loss beyond FP32 accumulation. Roles, stage layout,
+// MMA shapes and the epilogue's walk over TMEM follow the 8-bit kernel; the
+// TMA box is 16 channels x 32 samples x N beams of float32, one bf16 stage
+// holds a hi tile and a lo tile of the 8-bit kernel's layout, and the
+// covariance and variances are formed in FP64 from the FP32 sums.
+constexpr int kF32T = 32;              // samples per stage
+constexpr int kF32NF = 2;              // bf16 stages (hi + lo tiles each)
+constexpr int kF32SlotBytes = kF32T * 16;
+constexpr int kF32MaxNU = 8;           // float32 ring depth bound
+constexpr int kF32Products = 4;
+
+struct SmemF {
+  uint64_t in_full[kF32MaxNU], in_empty[kF32MaxNU];
+  uint64_t bf_full[kF32NF], bf_empty[kF32NF];
+  uint64_t shift_full[2];
+  uint64_t acc_full, acc_empty, drain;
+  uint32_t tmem_base;
+  alignas(16) float shift[2][kGroupSlots][kBoxCh];  // by item parity: [beam][channel]
+  float s_sum[2][8][kGroupSlots];                   // row sums G_a of the shifted samples
+  float s_inv[2][8][kGroupSlots];                   // 1/sqrt(var_a), 0 if var_a <= 0
+};
+
+// one bf16 stage: the hi tile, then the lo tile
+__host__ __device__ constexpr size_t bf_stage_bytes(int n_beam) {
+  return 2 * (size_t)stage_slots(n_beam) * kF32SlotBytes;
+}
+__host__ __device__ constexpr size_t f32_in_stage_bytes(int n_beam) {
+  return (size_t)n_beam * kF32T * kBoxCh * 4;
+}
+__host__ __device__ constexpr int f32_ring_depth(int n_beam) {
+  return (int)((kSmemBudget - 1024 - kF32NF * bf_stage_bytes(n_beam) - sizeof(SmemF)) /
+               f32_in_stage_bytes(n_beam)) < kF32MaxNU
+             ? (int)((kSmemBudget - 1024 - kF32NF * bf_stage_bytes(n_beam) - sizeof(SmemF)) /
+                     f32_in_stage_bytes(n_beam))
+             : kF32MaxNU;
+}
+__host__ __device__ constexpr size_t f32_smem_bytes(int n_beam, int n_in) {
+  return 1024 + kF32NF * bf_stage_bytes(n_beam) + (size_t)n_in * f32_in_stage_bytes(n_beam) +
+         sizeof(SmemF);
+}
+// Instruction descriptor, kind::f16 with bf16 A and B, f32 D, both MN-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+__device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 h) {
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+gram_tc_f32_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
+  const int kBfStageBytes = (int)bf_stage_bytes(g.n_beam);
+  const int kTileBytes = kBfStageBytes / 2;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int kNU = g.n_u8;
+  const int in_stage_bytes = (int)f32_in_stage_bytes(g.n_beam);
+  unsigned char* bf = base;                                  // kF32NF stages
+  unsigned char* in = bf + (size_t)kF32NF * kBfStageBytes;   // kNU stages of float32
+  SmemF* s = reinterpret_cast<SmemF*>(in + (size_t)kNU * in_stage_bytes);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int N = g.n_beam;
+  const int chunks = g.n_chan / kBoxCh;
+  const int64_t items = (int64_t)g.n_sub * chunks;
+  const int stages = g.n_samp_sub / kF32T;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kNU; ++i) {
+      mbar_init(&s->in_full[i], 1);
+      mbar_init(&s->in_empty[i], kConvThreads);
+    }
+    for (int i = 0; i < kF32NF; ++i) {
+      mbar_init(&s->bf_full[i], kConvThreads);
+      mbar_init(&s->bf_empty[i], 1);
+    }
+    mbar_init(&s->shift_full[0], 4);
+    mbar_init(&s->shift_full[1], 4);
+    mbar_init(&s->acc_full, 1);
+    mbar_init(&s->acc_empty, kEpiThreads);
+    mbar_init(&s->drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // constant slots: the rows of ones in the hi tile (bf16 1.0), zeros in
+  // the lo tile and everywhere the converter does not write
+  const uint32_t one2 = 0x3f803f80u;  // bf16x2 (1.0, 1.0)
+  const int p_one0 = slot_pos(0, N, g.R, g.R2), p_one1 = slot_pos(1, N, g.R, g.R2);
+  for (int st = 0; st < kF32NF; ++st) {
+    uint32_t* w = reinterpret_cast<uint32_t*>(bf + (size_t)st * kBfStageBytes);
+    for (int i = threadIdx.x; i < kBfStageBytes / 4; i += blockDim.x) {
+      const int byte = i * 4;
+      const int pos = byte / kF32SlotBytes;  // < stage_slots in the hi tile
+      w[i] = (byte < kTileBytes && (pos == p_one0 || pos == p_one1)) ? one2 : 0u;
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s->tmem_base)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = s->tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA
+    if (lane == 0) {
+      uint32_t cnt = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        const int k = (int)(it / chunks), ch0 = (int)(it % chunks) * kBoxCh;
+        const int64_t t_item = (int64_t)(g.sub0 + k) * g.n_samp_sub;
+        for (int st = 0; st < stages && ok; ++st, ++cnt) {
+          const int slot = cnt % kNU;
+          ok = mbar_wait(&s->in_empty[slot], ((cnt / kNU) & 1) ^ 1, g.error);
+          if (!ok) break;
+          mbar_expect_tx(&s->in_full[slot], (uint32_t)in_stage_bytes);
+          tma_load_3d(in + (size_t)slot * in_stage_bytes, &tmap, ch0, (int)(t_item + st * kF32T), 0,
+                      &s->in_full[slot]);
+        }
+      }
+      for (uint32_t d = cnt > (uint32_t)kNU ? cnt - kNU : 0; d < cnt; ++d)
+        mbar_wait(&s->in_full[d % kNU], (d / kNU) & 1, g.error);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA
+    if (lane == 0) {
+      const uint32_t bf_base = smem_u32(bf);
+      const uint32_t id1 = idesc_bf16(128, 8 * g.rb);
+      const uint32_t id2 = idesc_bf16(128, g.R2 > 0 ? 16 * g.R2 : 16);
+      const uint32_t pa1 = (uint32_t)(g.R + g.R2) * kF32SlotBytes;  // group 1: A1 and B1
+      const uint32_t pb1 = (uint32_t)g.R * kF32SlotBytes;
+      const uint32_t lbo = 128, sbo = kF32SlotBytes;
+      uint32_t fcnt = 0, item_iter = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x, ++item_iter) {
+        for (int st = 0; st < stages && ok; ++st, ++fcnt) {
+          const int fs = fcnt % kF32NF;
+          ok = mbar_wait(&s->bf_full[fs], (fcnt / kF32NF) & 1, g.error);
+          if (!ok) break;
+          if (st == 0 && item_iter > 0) {
+            ok = mbar_wait(&s->acc_empty, (item_iter - 1) & 1, g.error);
+            if (!ok) break;
+          }
+          fence_after();
+          const uint32_t hi = bf_base + (uint32_t)(fs * kBfStageBytes);
+          const uint32_t lo = hi + (uint32_t)kTileBytes;
+#pragma unroll
+          for (int ks = 0; ks < kF32T / 16; ++ks) {
+            // (A, B) = (hi, hi), (hi, lo), (lo, hi), (lo, lo)
+#pragma unroll
+            for (int pr = 0; pr < kF32Products; ++pr) {
+              const uint32_t ta = ((pr & 2) ? lo : hi) + ks * 256;
+              const uint32_t tb = ((pr & 1) ? lo : hi) + ks * 256;
+              const uint32_t acc = (st > 0 || ks > 0 || pr > 0) ? 1u : 0u;
+              mma_f16(tmem, smem_desc(ta, lbo, sbo), smem_desc(tb, lbo, sbo), id1, acc);
+              mma_f16(tmem + 192, smem_desc(ta + pa1, lbo, sbo), smem_desc(tb + pb1, lbo, sbo), id1,
+                      acc);
+              if (g.R2 > 0)
+                mma_f16(tmem + 384, smem_desc(ta + 16 * kF32SlotBytes, lbo, sbo),
+                        smem_desc(tb + 16 * kF32SlotBytes, lbo, sbo), id2, acc);
+            }
+          }
+          mma_commit(&s->bf_empty[fs]);
+          if (st == stages - 1) mma_commit(&s->acc_full);
+        }
+      }
+      mma_commit(&s->drain);
+      mbar_wait(&s->drain, 0, g.error);
+    }
+  } else if (warp >= 4 && warp < 8) {
+    // ------------------------------------------------------------ convert
+    // Thread ct converts, for every beam, sample t = ct / 4 of the stage
+    // and channels 4q..4q+3, q = ct % 4 (one float4 of the box, so a warp
+    // reads 512 contiguous bytes); its 4 values go to 8 bytes of the hi
+    // tile and 8 bytes of the lo tile in channel group q / 2.
+    const int ct = threadIdx.x - 4 * 32;
+    const int t = ct / 4, q = ct % 4, grp = q / 2, half = q % 2;
+    const uint32_t t_off = (uint32_t)((t / 8) * 128 + (t % 8) * 16 + half * 8);
+    uint32_t cnt = 0, item_iter = 0;
+    bool ok = true;
+    for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x, ++item_iter) {
+      const int par = item_iter & 1;
+      const float4* sh = reinterpret_cast<const float4*>(&s->shift[par][0][0]);
+      for (int st = 0; st < stages && ok; ++st, ++cnt) {
+        const int us = cnt % kNU, fs = cnt % kF32NF;
+        ok = mbar_wait(&s->in_full[us], (cnt / kNU) & 1, g.error);
+        if (ok) ok = mbar_wait(&s->bf_empty[fs], ((cnt / kF32NF) & 1) ^ 1, g.error);
+        if (!ok) break;
+        const float4* src = reinterpret_cast<const float4*>(in + (size_t)us * in_stage_bytes);
+        if (st == 0) {
+          // the item's shifts are its first samples: the threads holding
+          // sample 0 publish them. The table of this parity was last read
+          // two items ago, and all converter threads finished that item
+          // before the bf16 stage waited on above could be free again.
+          if (t == 0) {
+            float4* shw = reinterpret_cast<float4*>(&s->shift[par][0][0]);
+            for (int b = 0; b < N; ++b) shw[b * 4 + q] = src[b * kF32T * 4 + q];
+            mbar_arrive(&s->shift_full[par]);
+          }
+          ok = mbar_wait(&s->shift_full[par], (item_iter >> 1) & 1, g.error);
+          if (!ok) break;
+        }
+        unsigned char* hi = bf + (size_t)fs * kBfStageBytes;
+        unsigned char* lo = hi + kTileBytes;
+        for (int b = 0; b < N; ++b) {
+          const float4 v = src[b * kF32T * 4 + ct];
+          const float4 z = sh[b * 4 + q];
+          const float x0 = v.x - z.x, x1 = v.y - z.y, x2 = v.z - z.z, x3 = v.w - z.w;
+          const __nv_bfloat162 h01 = __floats2bfloat162_rn(x0, x1);
+          const __nv_bfloat162 h23 = __floats2bfloat162_rn(x2, x3);
+          const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+          const __nv_bfloat162 l01 = __floats2bfloat162_rn(x0 - f01.x, x1 - f01.y);
+          const __nv_bfloat162 l23 = __floats2bfloat162_rn(x2 - f23.x, x3 - f23.y);
+          const uint32_t off =
+              (uint32_t)(grp == 0 ? b : slot_pos(1, b, g.R, g.R2)) * kF32SlotBytes + t_off;
+          *reinterpret_cast<uint2*>(hi + off) = make_uint2(bf16x2_bits(h01), bf16x2_bits(h23));
+          *reinterpret_cast<uint2*>(lo + off) = make_uint2(bf16x2_bits(l01), bf16x2_bits(l23));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&s->in_empty[us]);
+        mbar_arrive(&s->bf_full[fs]);
+      }
+    }
+  } else if (warp >= 8) {
+    // ------------------------------------------------------------ epilogue
+    const int qw = warp - 8;
+    const int c = lane % 8;
+    const int slot = 4 * qw + lane / 8;
+    const int p2 = 4 * qw + lane / 8;
+    const int g2 = p2 < g.R2 ? 0 : (p2 < 2 * g.R2 ? 1 : -1);
+    const int slot2 = 16 + (g2 == 1 ? p2 - g.R2 : p2);
+    const double n = (double)g.n_samp_sub;
+    const int R = g.R, R2 = g.R2;
+    uint32_t item_iter = 0;
+    bool ok = true;
+    for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x, ++item_iter) {
+      ok = mbar_wait(&s->acc_full, item_iter & 1, g.error);
+      if (!ok) break;
+      fence_after();
+      float row[2][kGroupSlots];
+      float row2[16];
+#pragma unroll
+      for (int gi = 0; gi < 2; ++gi) {
+#pragma unroll
+        for (int ch = 0; ch < kGroupSlots / 4; ++ch) {
+          if (ch * 4 < g.rb) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * qw) << 16) + gi * 192 + ch * 32, v);
+            tmem_wait_ld();
+            pick4(v, c, &row[gi][4 * ch]);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) row[gi][4 * ch + u] = 0.f;
+          }
+        }
+      }
+#pragma unroll
+      for (int ch = 0; ch < 4; ++ch) {
+        if (2 * R2 > 4 * ch) {
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(32 * qw) << 16) + 384 + ch * 32, v);
+          tmem_wait_ld();
+          pick4(v, c, &row2[4 * ch]);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) row2[4 * ch + u] = 0.f;
+        }
+      }
+      fence_before();
+      mbar_arrive(&s->acc_empty);
+      float sumN[2], diag[2], sumN2 = 0.f, diag2 = 0.f;
+#pragma unroll
+      for (int gi = 0; gi < 2; ++gi) {
+        sumN[gi] = diag[gi] = 0.f;
+#pragma unroll
+        for (int jb = 0; jb < kGroupSlots; ++jb) {
+          const int b = d1_slot(gi, jb, R2);
+          if (jb < R && b == N) sumN[gi] = row[gi][jb];
+          if (jb < R && b == slot) diag[gi] = row[gi][jb];
+        }
+      }
+      const int jb2 = g2 == 1 ? R2 : 0;
+#pragma unroll
+      for (int jb = 0; jb < 16; ++jb) {
+        if (jb - jb2 == N - 16) sumN2 = row2[jb];
+        if (jb - jb2 == slot2 - 16) diag2 = row2[jb];
+      }
+      const int k = (int)(it / chunks), ch0 = (int)(it % chunks) * kBoxCh;
+      auto table = [&](int gi, int a, float sum_a, float diag_a) {
+        const double sa = (double)sum_a;
+        const double var = n * (double)diag_a - sa * sa;
+        s->s_sum[gi][c][a] = sum_a;
+        float inv = 0.f;
+        if (a < N) {
+          if (var > 0.0) inv = (float)(1.0 / sqrt(var));
+          else atomicAdd(g.degenerate, 1ull);
+        }
+        s->s_inv[gi][c][a] = inv;
+      };
+#pragma unroll
+      for (int gi = 0; gi < 2; ++gi)
+        if (slot < N + 1) table(gi, slot, sumN[gi], diag[gi]);
+      if (g2 >= 0 && slot2 < N + 1) table(g2, slot2, sumN2, diag2);
+      named_sync(1, kEpiThreads);
+      auto emit = [&](int gi, int a, const float* rv, auto nb_c, auto slot_of) {
+        constexpr int NB = decltype(nb_c)::value;
+        if (a >= N) return;
+        const int64_t cell = (int64_t)k * g.n_chan + ch0 + gi * 8 + c;
+        const double sa = (double)s->s_sum[gi][c][a];
+        const float inva = s->s_inv[gi][c][a];
+        float* dst = g.corr + cell * (int64_t)(N * (N + 1) / 2) + (a * N - a * (a - 1) / 2);
+#pragma unroll
+        for (int jb = 0; jb < NB; ++jb) {
+          const int b = slot_of(jb);
+          if (b < a || b >= N) continue;
+          float r;
+          if (b == a) {
+            r = 1.f;
+          } else {
+            const double cov = n * (double)rv[jb] - sa * (double)s->s_sum[gi][c][b];
+            r = (float)cov * inva * s->s_inv[gi][c][b];
+          }
+          dst[b - a] = r;
+        }
+      };
+#pragma unroll
+      for (int gi = 0; gi < 2; ++gi)
+        if (slot <= N)
+          emit(gi, slot, row[gi], std::integral_constant<int, kGroupSlots>{},
+               [&](int jb) { return jb < R ? d1_slot(gi, jb, R2) : -1; });
+      if (g2 >= 0 && slot2 <= N)
+        emit(g2, slot2, row2, std::integral_constant<int, 16>{},
+             [&](int jb) { return (jb >= jb2 && jb < jb2 + R2) ? 16 + jb - jb2 : -1; });
+      named_sync(1, kEpiThreads);
+    }
+  }
+  __syncthreads();
+  if (warp == 2) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols));
+  }
+}
+
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -603,6 +961,7 @@ bool gram_tc_supported(const mraid_plan_s* pl, const void* d_data) {
   return p.bit_depth == 8 && p.n_beam >= 2 && p.n_beam + 1 <= kGroupSlots &&
          p.n_samp_sub % t == 0 && p.n_samp_sub <= 1024 && p.n_chan % kBoxCh == 0 &&
          pl->beam_stride % 16 == 0 && (reinterpret_cast<uintptr_t>(d_data) & 15) == 0 &&
+         (int64_t)p.n_sub * p.n_samp_sub <= 2147483647ll /* TMA time coordinate */ &&
          encode_fn() != nullptr;
 }
 
@@ -662,6 +1021,54 @@ cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int su
   }
 #undef MRAID_TC_LAUNCH
   if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+bool gram_tc_f32_supported(const mraid_plan_s* pl, const void* d_data) {
+  const mraid_params& p = pl->p;
+  return p.bit_depth == 32 && p.n_beam >= 2 && p.n_beam + 1 <= kGroupSlots &&
+         p.n_samp_sub % kF32T == 0 && p.n_chan % kBoxCh == 0 && pl->beam_stride % 4 == 0 &&
+         (reinterpret_cast<uintptr_t>(d_data) & 15) == 0 && f32_ring_depth(p.n_beam) >= 2 &&
+         (int64_t)p.n_sub * p.n_samp_sub <= 2147483647ll && encode_fn() != nullptr;
+}
+
+cudaError_t launch_gram_tc_f32(const mraid_plan_s* pl, const float* d_data, int sub0, int n_sub,
+                               float* d_corr) {
+  const mraid_params& p = pl->p;
+  if (!gram_tc_f32_supported(pl, d_data) || !d_corr) return cudaErrorNotSupported;
+  CUtensorMap map;
+  const cuuint64_t n_time = (cuuint64_t)(sub0 + n_sub) * p.n_samp_sub;
+  cuuint64_t dims[3] = {(cuuint64_t)p.n_chan, n_time, (cuuint64_t)p.n_beam};
+  cuuint64_t strides[2] = {(cuuint64_t)p.n_chan * 4, (cuuint64_t)pl->beam_stride * 4};
+  cuuint32_t box[3] = {(cuuint32_t)kBoxCh, (cuuint32_t)kF32T, (cuuint32_t)p.n_beam};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(d_data),
+                           dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  TcArgs a;
+  a.n_beam = p.n_beam;
+  a.n_chan = p.n_chan;
+  a.n_samp_sub = p.n_samp_sub;
+  a.sub0 = sub0;
+  a.n_sub = n_sub;
+  const int R = p.n_beam + 1;
+  a.R = R;
+  a.R2 = R > 16 ? R - 16 : 0;
+  a.rb = (R + 1) / 2 * 2;
+  a.sums = nullptr;
+  a.corr = d_corr;
+  a.degenerate = pl->d_degenerate;
+  a.error = pl->d_error;
+  a.n_u8 = f32_ring_depth(p.n_beam);
+  const size_t smem = f32_smem_bytes(p.n_beam, a.n_u8);
+  const int64_t items = (int64_t)n_sub * (p.n_chan / kBoxCh);
+  const int grid = (int)(items < pl->sm_count ? items : pl->sm_count);
+  cudaError_t e = cudaFuncSetAttribute(gram_tc_f32_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (grid > 0) gram_tc_f32_kernel<<<grid, kThreads, smem, pl->stream>>>(map, a);
   return cudaGetLastError();
 }
 

@@ -22,7 +22,7 @@ struct FlagDev {  // device image of mraid_flag_info
   mraid_flag_info info;
 };
 
-enum KernelId { K_GRAM = 0, K_CORR, K_EIG, K_FLAG, K_GRAM_TC, K_COUNT };
+enum KernelId { K_GRAM = 0, K_CORR, K_EIG, K_FLAG, K_GRAM_TC, K_GRAM_F32, K_GRAM_TC_F32, K_COUNT };
 const char* kernel_name(int id);
 
 struct Profiler {
@@ -118,6 +118,11 @@ constexpr int kTcVariants = 8;
 constexpr int kEigVariants = 4;  // register eigensolvers (see eig_variant)
 cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int sub0, int n_sub,
                            int64_t* d_sums, float* d_corr);
+// float32 samples on the tensor cores (split-bf16 products, gram_tc.cu):
+// correlation only, d_corr relative to sub0
+bool gram_tc_f32_supported(const mraid_plan_s* pl, const void* d_data);
+cudaError_t launch_gram_tc_f32(const mraid_plan_s* pl, const float* d_data, int sub0, int n_sub,
+                               float* d_corr);
 cudaError_t launch_corr_from_sums(const mraid_plan_s* pl, const int64_t* d_sums,
                                   int64_t n_cells, float* d_corr);
 // eig.cu

@@ -34,6 +34,8 @@ const char* kernel_name(int id) {
     case K_EIG: return "eig";
     case K_FLAG: return "flag_clip";
     case K_GRAM_TC: return "gram_tc";
+    case K_GRAM_F32: return "gram_f32";
+    case K_GRAM_TC_F32: return "gram_tc_f32";
   }
   return "unknown";
 }
@@ -179,9 +181,15 @@ mraid_status ccm_range(mraid_plan_s* pl, const void* d_data, int sub0, int n_sub
       return MRAID_ERR_INVALID_ARG;
     }
     if (!d_corr) return MRAID_OK;
+    if (!pl->force_dp4a && gram_tc_f32_supported(pl, d_data)) {
+      cudaError_t e = MRAID_PROF(pl, K_GRAM_TC_F32,
+                                 launch_gram_tc_f32(pl, static_cast<const float*>(d_data), sub0,
+                                                    n_sub, d_corr));
+      return e == cudaSuccess ? MRAID_OK : cuda_fail(e, "gram_tc_f32 launch");
+    }
     for (int s = 0; s < n_sub; s += kMaxSubPerLaunch) {
       const int ns = (n_sub - s) < kMaxSubPerLaunch ? (n_sub - s) : kMaxSubPerLaunch;
-      cudaError_t e = MRAID_PROF(pl, K_GRAM,
+      cudaError_t e = MRAID_PROF(pl, K_GRAM_F32,
                                  launch_gram_f32(pl, static_cast<const float*>(d_data), sub0 + s, ns,
                                                  d_corr + (int64_t)s * pl->p.n_chan * pl->np));
       if (e != cudaSuccess) return cuda_fail(e, "gram_f32 launch");
@@ -674,7 +682,10 @@ mraid_status mraid_autotune(mraid_plan_t pl, const void* d_data, int32_t reps, i
   for (int v = -1; v < kTcVariants && st == MRAID_OK; ++v) {
     pl->force_dp4a = v < 0;
     pl->tc_variant = v < 0 ? 0 : v;
-    if (v >= 0 && !gram_tc_supported(pl, d_data)) continue;
+    // float32 samples have one tensor-core kernel, timed as variant 0
+    if (v >= 0 && (pl->p.bit_depth == 32 ? (v > 0 || !gram_tc_f32_supported(pl, d_data))
+                                         : !gram_tc_supported(pl, d_data)))
+      continue;
     float ms = 0.f;
     st = time_runs(pl, reps, e0, e1,
                    [&] { return ccm_range(pl, d_data, 0, pl->p.n_sub, nullptr, pl->ws.corr); }, &ms);
