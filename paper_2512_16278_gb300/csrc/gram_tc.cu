@@ -31,6 +31,9 @@
 // Every wait is bounded (~2 s on the global timer); on expiry the kernel
 // records an error word, drains its in-flight copies and MMAs (again
 // bounded), frees its TMEM and returns.
+//
+// gram_tc_f32_kernel (below) runs the same pipeline on float32 samples,
+// split into bf16 high and low parts on the way into shared memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -576,16 +579,19 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
 // MMA shapes and the epilogue's walk over TMEM follow the 8-bit kernel; the
 // TMA box is 16 channels x 32 samples x N beams of float32, one bf16 stage
 // holds a hi tile and a lo tile of the 8-bit kernel's layout, and the
-// covariance and variances are formed in FP64 from the FP32 sums.
+// covariance and variances are formed in FP64 from the FP32 sums. Three
+// bf16 stages where the shared memory still leaves two float32 stages
+// (up to 21 beams), else two; the converter handles four beams per loop
+// trip so that their shared-memory loads overlap.
 constexpr int kF32T = 32;              // samples per stage
-constexpr int kF32NF = 2;              // bf16 stages (hi + lo tiles each)
+constexpr int kF32MaxNF = 3;           // bf16 stages (hi + lo tiles each)
 constexpr int kF32SlotBytes = kF32T * 16;
 constexpr int kF32MaxNU = 8;           // float32 ring depth bound
 constexpr int kF32Products = 4;
 
 struct SmemF {
   uint64_t in_full[kF32MaxNU], in_empty[kF32MaxNU];
-  uint64_t bf_full[kF32NF], bf_empty[kF32NF];
+  uint64_t bf_full[kF32MaxNF], bf_empty[kF32MaxNF];
   uint64_t shift_full[2];
   uint64_t acc_full, acc_empty, drain;
   uint32_t tmem_base;
@@ -601,15 +607,19 @@ __host__ __device__ constexpr size_t bf_stage_bytes(int n_beam) {
 __host__ __device__ constexpr size_t f32_in_stage_bytes(int n_beam) {
   return (size_t)n_beam * kF32T * kBoxCh * 4;
 }
-__host__ __device__ constexpr int f32_ring_depth(int n_beam) {
-  return (int)((kSmemBudget - 1024 - kF32NF * bf_stage_bytes(n_beam) - sizeof(SmemF)) /
+// float32 ring depth for n_beam beams and nf bf16 stages
+__host__ __device__ constexpr int f32_ring_depth(int n_beam, int nf) {
+  return (int)((kSmemBudget - 1024 - nf * bf_stage_bytes(n_beam) - sizeof(SmemF)) /
                f32_in_stage_bytes(n_beam)) < kF32MaxNU
-             ? (int)((kSmemBudget - 1024 - kF32NF * bf_stage_bytes(n_beam) - sizeof(SmemF)) /
+             ? (int)((kSmemBudget - 1024 - nf * bf_stage_bytes(n_beam) - sizeof(SmemF)) /
                      f32_in_stage_bytes(n_beam))
              : kF32MaxNU;
 }
-__host__ __device__ constexpr size_t f32_smem_bytes(int n_beam, int n_in) {
-  return 1024 + kF32NF * bf_stage_bytes(n_beam) + (size_t)n_in * f32_in_stage_bytes(n_beam) +
+__host__ __device__ constexpr int f32_stages(int n_beam) {
+  return f32_ring_depth(n_beam, 3) >= 2 ? 3 : 2;
+}
+__host__ __device__ constexpr size_t f32_smem_bytes(int n_beam, int nf, int n_in) {
+  return 1024 + nf * bf_stage_bytes(n_beam) + (size_t)n_in * f32_in_stage_bytes(n_beam) +
          sizeof(SmemF);
 }
 // Instruction descriptor, kind::f16 with bf16 A and B, f32 D, both MN-major.
@@ -621,17 +631,19 @@ __device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 h) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
+template <int NF>
 __global__ void __launch_bounds__(kThreads, 1)
 gram_tc_f32_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
   const int kBfStageBytes = (int)bf_stage_bytes(g.n_beam);
   const int kTileBytes = kBfStageBytes / 2;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* base =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // offset from the shared array itself (not through an integer), so the
+  // compiler keeps every derived access in the shared state space
+  unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int kNU = g.n_u8;
   const int in_stage_bytes = (int)f32_in_stage_bytes(g.n_beam);
-  unsigned char* bf = base;                                  // kF32NF stages
-  unsigned char* in = bf + (size_t)kF32NF * kBfStageBytes;   // kNU stages of float32
+  unsigned char* bf = base;                                  // NF stages
+  unsigned char* in = bf + (size_t)NF * kBfStageBytes;   // kNU stages of float32
   SmemF* s = reinterpret_cast<SmemF*>(in + (size_t)kNU * in_stage_bytes);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -645,7 +657,7 @@ gram_tc_f32_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
       mbar_init(&s->in_full[i], 1);
       mbar_init(&s->in_empty[i], kConvThreads);
     }
-    for (int i = 0; i < kF32NF; ++i) {
+    for (int i = 0; i < NF; ++i) {
       mbar_init(&s->bf_full[i], kConvThreads);
       mbar_init(&s->bf_empty[i], 1);
     }
@@ -660,7 +672,7 @@ gram_tc_f32_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
   // the lo tile and everywhere the converter does not write
   const uint32_t one2 = 0x3f803f80u;  // bf16x2 (1.0, 1.0)
   const int p_one0 = slot_pos(0, N, g.R, g.R2), p_one1 = slot_pos(1, N, g.R, g.R2);
-  for (int st = 0; st < kF32NF; ++st) {
+  for (int st = 0; st < NF; ++st) {
     uint32_t* w = reinterpret_cast<uint32_t*>(bf + (size_t)st * kBfStageBytes);
     for (int i = threadIdx.x; i < kBfStageBytes / 4; i += blockDim.x) {
       const int byte = i * 4;
@@ -712,8 +724,8 @@ gram_tc_f32_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
       bool ok = true;
       for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x, ++item_iter) {
         for (int st = 0; st < stages && ok; ++st, ++fcnt) {
-          const int fs = fcnt % kF32NF;
-          ok = mbar_wait(&s->bf_full[fs], (fcnt / kF32NF) & 1, g.error);
+          const int fs = fcnt % NF;
+          ok = mbar_wait(&s->bf_full[fs], (fcnt / NF) & 1, g.error);
           if (!ok) break;
           if (st == 0 && item_iter > 0) {
             ok = mbar_wait(&s->acc_empty, (item_iter - 1) & 1, g.error);
@@ -760,9 +772,9 @@ gram_tc_f32_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
       const int par = item_iter & 1;
       const float4* sh = reinterpret_cast<const float4*>(&s->shift[par][0][0]);
       for (int st = 0; st < stages && ok; ++st, ++cnt) {
-        const int us = cnt % kNU, fs = cnt % kF32NF;
+        const int us = cnt % kNU, fs = cnt % NF;
         ok = mbar_wait(&s->in_full[us], (cnt / kNU) & 1, g.error);
-        if (ok) ok = mbar_wait(&s->bf_empty[fs], ((cnt / kF32NF) & 1) ^ 1, g.error);
+        if (ok) ok = mbar_wait(&s->bf_empty[fs], ((cnt / NF) & 1) ^ 1, g.error);
         if (!ok) break;
         const float4* src = reinterpret_cast<const float4*>(in + (size_t)us * in_stage_bytes);
         if (st == 0) {
@@ -780,6 +792,7 @@ gram_tc_f32_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
         }
         unsigned char* hi = bf + (size_t)fs * kBfStageBytes;
         unsigned char* lo = hi + kTileBytes;
+#pragma unroll 4
         for (int b = 0; b < N; ++b) {
           const float4 v = src[b * kF32T * 4 + ct];
           const float4 z = sh[b * 4 + q];
@@ -1028,7 +1041,7 @@ bool gram_tc_f32_supported(const mraid_plan_s* pl, const void* d_data) {
   const mraid_params& p = pl->p;
   return p.bit_depth == 32 && p.n_beam >= 2 && p.n_beam + 1 <= kGroupSlots &&
          p.n_samp_sub % kF32T == 0 && p.n_chan % kBoxCh == 0 && pl->beam_stride % 4 == 0 &&
-         (reinterpret_cast<uintptr_t>(d_data) & 15) == 0 && f32_ring_depth(p.n_beam) >= 2 &&
+         (reinterpret_cast<uintptr_t>(d_data) & 15) == 0 && f32_ring_depth(p.n_beam, 2) >= 2 &&
          (int64_t)p.n_sub * p.n_samp_sub <= 2147483647ll && encode_fn() != nullptr;
 }
 
@@ -1061,14 +1074,16 @@ cudaError_t launch_gram_tc_f32(const mraid_plan_s* pl, const float* d_data, int 
   a.corr = d_corr;
   a.degenerate = pl->d_degenerate;
   a.error = pl->d_error;
-  a.n_u8 = f32_ring_depth(p.n_beam);
-  const size_t smem = f32_smem_bytes(p.n_beam, a.n_u8);
+  const int nf = f32_stages(p.n_beam);
+  a.n_u8 = f32_ring_depth(p.n_beam, nf);
+  const size_t smem = f32_smem_bytes(p.n_beam, nf, a.n_u8);
   const int64_t items = (int64_t)n_sub * (p.n_chan / kBoxCh);
   const int grid = (int)(items < pl->sm_count ? items : pl->sm_count);
-  cudaError_t e = cudaFuncSetAttribute(gram_tc_f32_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = nf == 3 ? gram_tc_f32_kernel<3> : gram_tc_f32_kernel<2>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (grid > 0) gram_tc_f32_kernel<<<grid, kThreads, smem, pl->stream>>>(map, a);
+  if (grid > 0) kern<<<grid, kThreads, smem, pl->stream>>>(map, a);
   return cudaGetLastError();
 }
 
