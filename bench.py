@@ -49,6 +49,8 @@ def parse_args():
                     help="shrink the block to this many sub-integrations (profiling runs)")
     ap.add_argument("--f32-subs", type=int, default=20,
                     help="sub-integrations of the float32-input variant (0: skip)")
+    ap.add_argument("--multires-steps", type=int, default=3,
+                    help="timed calls of the seven-timescale pass (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3,
                     help="timed passes of the batched form (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
@@ -337,6 +339,84 @@ def bench_f32(m, torch, d_u8, cfg, stream, n_sub, peaks):
     del x
     torch.cuda.empty_cache()
     return out
+
+
+# sub-interval lengths of Table 1 (0.05 s to 10 s) in 1024-sample
+# sub-integrations of 49.152 us: 0.05, 0.2, 0.5, 1, 2, 5, 10 s
+MULTIRES_FACTORS = (1, 4, 10, 20, 40, 100, 200)
+
+
+def bench_multires(m, torch, d, cfg, stream, steps, peaks):
+    """All seven timescales of Table 1 in one mraid_multires call on the
+    block (one pass over the samples), against mraid_run once per timescale
+    (seven passes); per-level masking rate, and the aggregation kernel's HBM
+    roofline."""
+    N, C, S, K = cfg.n_beam, cfg.n_chan, cfg.n_samp_sub, cfg.n_sub
+    factors = [f for f in MULTIRES_FACTORS if f <= K]
+    with torch.cuda.stream(stream):
+        plan = m.Plan(N, C, S, K, stream=stream)
+        stats = [torch.empty((K // f) * C, dtype=torch.float32, device="cuda") for f in factors]
+        flags = [torch.empty((K // f) * C, dtype=torch.uint8, device="cuda") for f in factors]
+    infos = (m.FlagInfo * len(factors))()
+    m.mraid_multires(plan.handle, d, factors, stats, flags, infos)
+    m.mraid_sync(plan.handle)
+    m.mraid_profile_reset(plan.handle)
+    m.mraid_profile_enable(plan.handle, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        m.mraid_multires(plan.handle, d, factors, stats, flags, infos)
+    e1.record(stream)
+    m.mraid_sync(plan.handle)
+    m.mraid_profile_enable(plan.handle, False)
+    prof = m.mraid_profile_read(plan.handle)
+    ms = e0.elapsed_time(e1) / steps
+    kt = {k: (n // steps, tot / steps) for k, (n, tot) in prof.items() if n > 0}
+    levels = []
+    for i, f in enumerate(factors):
+        info = infos[i].as_dict()
+        levels.append({"factor": f, "seconds": round(f * S * 49.152e-6, 3),
+                       "cells": (K // f) * C, "masked_fraction": info["n_flagged"] / ((K // f) * C),
+                       "iterations": info["iterations"], "threshold": info["thresh"]})
+    plan.close()
+    # one mraid_run per timescale, each a plan with the longer sub-integration
+    sep = 0.0
+    for f in factors:
+        n_f = K // f
+        with torch.cuda.stream(stream):
+            p2 = m.Plan(N, C, f * S, n_f, beam_stride=cfg.n_time * C, stream=stream)
+            st = torch.empty(n_f * C, dtype=torch.float32, device="cuda")
+            fl = torch.empty(n_f * C, dtype=torch.uint8, device="cuda")
+        m.mraid_run(p2.handle, d, None, None, st, fl)
+        m.mraid_sync(p2.handle)
+        e0.record(stream)
+        m.mraid_run(p2.handle, d, None, None, st, fl)
+        e1.record(stream)
+        m.mraid_sync(p2.handle)
+        sep += e0.elapsed_time(e1)
+        p2.close()
+    psum = (N + 1) * (N + 2) // 2
+    agg = None
+    if "gram_aggregate" in kt:
+        n_l, tot = kt["gram_aggregate"]
+        # bytes over all levels of one call: every level reads its source
+        # sums once and writes its own (sources as chosen by the library)
+        done, b = [1], 0
+        for f in factors[1:]:
+            g = max(x for x in done if f % x == 0)
+            b += 8 * psum * C * ((K // f) * f // g + K // f)
+            done.append(f)
+        a = b / (tot / 1e3) / 1e9
+        agg = {"bound": "hbm", "kernel": "gram_aggregate", "achieved": a, "peak": peaks["hbm_gbs"],
+               "unit": "GB/s", "frac": a / peaks["hbm_gbs"], "launches": n_l,
+               "work_per_call": b, "ms_per_call": tot}
+    return {"workload": f"{cfg.n_beam} beams x {C} channels x {K} x {S} samples (uint8), "
+                        f"timescales {factors} sub-integrations",
+            "ms_per_call": ms, "ms_separate_runs": sep,
+            "cells_per_s_all_levels": sum((K // f) * C for f in factors) / (ms / 1e3),
+            "kernels_ms_per_call": {k: v[1] for k, v in kt.items()},
+            "aggregate_roofline": agg, "levels": levels}
 
 
 def bench_batched(m, torch, stream, steps):
@@ -672,6 +752,9 @@ def run_mraid(args):
         refine = {"ms": r0.elapsed_time(r1) / 5,
                   "beam_bits_set": int(sum(bin(int(x) & 0xffffffff).count("1")
                                            for x in bits.view(-1).cpu().tolist()))}
+    multires = None
+    if world == 1 and args.multires_steps > 0:
+        multires = bench_multires(m, torch, d, cfg, stream, args.multires_steps, peaks)
     precision = None
     if world == 1 and args.f32_subs > 0:
         precision = bench_f32(m, torch, d, cfg, stream, args.f32_subs, peaks)
@@ -713,6 +796,7 @@ def run_mraid(args):
                                "unit": "QR steps" if variants[1] >= 2 else "Jacobi sweeps"},
             "refine": refine,
             "precision_f32": precision,
+            "multires": multires,
             "batched": batched,
             "served": served,
         }

@@ -185,6 +185,33 @@ mraid_status mraid_run(mraid_plan_t plan, const void* d_data, float* d_evals,
 mraid_status mraid_run_host(mraid_plan_t plan, const void* h_data, float* h_stat,
                             uint8_t* h_flags, mraid_flag_info* info);
 
+/* Several timescales in one pass (Section 4.4, Table 1 and Fig. 7 run the
+ * method at sub-interval lengths from 0.05 s to 10 s). Level i uses
+ * sub-intervals of factors[i] consecutive sub-integrations of the plan
+ * (factors[i] * n_samp_sub samples each): the whole path (Eq. 1, Eq. 2,
+ * masking with its own Gaussian fit over that level's cells) as mraid_run
+ * would give for a plan with n_samp_sub * factors[i] samples per
+ * sub-integration over the first (n_sub / factors[i]) * factors[i]
+ * sub-integrations (integer division: trailing sub-integrations that do
+ * not fill a sub-interval are left out of that level). The samples are read
+ * once: the Gram sums of the plan's sub-integrations are formed, and each
+ * longer sub-interval's sums are the exact int64 sum of shorter ones.
+ *   d_data:    8-bit samples (bit_depth 8), layout as for mraid_run.
+ *   n_levels:  1..16.
+ *   factors:   host, n_levels distinct values in 1..n_sub, any order.
+ *   d_stats:   host array of n_levels device pointers, float32
+ *              [(n_sub / factors[i]) * n_chan], cell = sub-interval * n_chan
+ *              + chan. Required.
+ *   d_flags:   host array of n_levels device pointers, uint8, same cells.
+ *              Required.
+ *   infos:     host, n_levels entries filled at mraid_sync (may be NULL);
+ *              n_degenerate and jacobi_sweeps count that level's cells.
+ * Work buffers (the Gram sums of every level) are allocated on first use
+ * and kept by the plan. */
+mraid_status mraid_multires(mraid_plan_t plan, const void* d_data, int32_t n_levels,
+                            const int32_t* factors, float* const* d_stats,
+                            uint8_t* const* d_flags, mraid_flag_info* infos);
+
 /* Autotuner (the paper has no counterpart; it picks among this library's
  * kernel variants). Times, `reps` runs each on d_data, every Gram variant
  * that fits the plan's shape (eight tensor-core variants over samples per

@@ -27,7 +27,7 @@ __all__ = [
     "mraid_batch_destroy", "UnitIO", "Batch", "mraid_serve_open", "mraid_serve_submit",
     "mraid_serve_poll", "mraid_serve_drain", "mraid_serve_close", "StreamDesc", "BlockResult",
     "Server", "mraid_autotune", "mraid_set_variant", "mraid_set_eig_variant", "tune",
-    "mraid_refine", "STATUS",
+    "mraid_refine", "mraid_multires", "STATUS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -159,6 +159,8 @@ def load():
         "mraid_set_variant": (ctypes.c_int, [vp, i32]),
         "mraid_set_eig_variant": (ctypes.c_int, [vp, i32]),
         "mraid_refine": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "mraid_multires": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(vp),
+                                          ctypes.POINTER(vp), ctypes.POINTER(FlagInfo)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -238,6 +240,20 @@ def mraid_run_host(plan: int, h_data, h_stat, h_flags, info: Optional[FlagInfo] 
     _check(load().mraid_run_host(plan, _ptr(h_data), _ptr(h_stat), _ptr(h_flags),
                                  ctypes.byref(info) if info is not None else None),
            "mraid_run_host")
+
+
+def mraid_multires(plan: int, d_data, factors, d_stats, d_flags, infos=None):
+    """Several timescales in one pass: level i uses sub-intervals of
+    factors[i] sub-integrations; d_stats[i] / d_flags[i] hold its
+    (n_sub // factors[i]) * n_chan cells. infos, if given, is a ctypes array
+    of len(factors) FlagInfo filled at mraid_sync (keep it alive until then)."""
+    n = len(factors)
+    if len(d_stats) != n or len(d_flags) != n or (infos is not None and len(infos) != n):
+        raise ValueError("one stat, flag (and info) buffer per factor")
+    f = (ctypes.c_int32 * n)(*factors)
+    st = (ctypes.c_void_p * n)(*[_ptr(x) for x in d_stats])
+    fl = (ctypes.c_void_p * n)(*[_ptr(x) for x in d_flags])
+    _check(load().mraid_multires(plan, _ptr(d_data), n, f, st, fl, infos), "mraid_multires")
 
 
 def mraid_sync(plan: int):
@@ -509,6 +525,18 @@ class Plan:
         mraid_run_host(self.handle, h_data, h_stat, h_flags, info)
         mraid_sync(self.handle)
         return h_flags, info.as_dict()
+
+    def multires(self, data, factors):
+        """Stat, flags and masking report per timescale: one dict per factor
+        (sub-intervals of `factor` sub-integrations), in the given order."""
+        t = self.torch
+        stats = [self._empty((self.n_sub // f) * self.n_chan, dtype=t.float32) for f in factors]
+        flags = [self._empty((self.n_sub // f) * self.n_chan, dtype=t.uint8) for f in factors]
+        infos = (FlagInfo * len(factors))()
+        mraid_multires(self.handle, data, list(factors), stats, flags, infos)
+        mraid_sync(self.handle)
+        return [{"factor": f, "stat": stats[i], "flags": flags[i], "info": infos[i].as_dict()}
+                for i, f in enumerate(factors)]
 
     def sync(self):
         mraid_sync(self.handle)

@@ -197,17 +197,18 @@ int flag_grid_blocks(int device, int sm_count) {
   return sm_count;  // one block per SM: fewer partials to combine
 }
 
-cudaError_t launch_flag(mraid_plan_s* pl, const float* d_stat, uint8_t* d_flags) {
+cudaError_t launch_flag(mraid_plan_s* pl, const float* d_stat, uint8_t* d_flags, int64_t n_cells,
+                        mraid_flag_info* d_info) {
   FlagArgs f;
   f.stat = d_stat;
-  f.n_cells = pl->n_cells;
+  f.n_cells = n_cells >= 0 ? n_cells : pl->n_cells;
   f.n_chan = pl->p.n_chan;
   f.keep = pl->d_keep;
   f.k_sigma = pl->p.eig_k;
   f.max_iter = pl->p.max_clip_iter;
   f.flags = d_flags;
   f.partials = pl->d_partials;
-  f.info = pl->d_info;
+  f.info = d_info ? d_info : pl->d_info;
   // cooperative launch (all blocks co-resident for the grid barrier), in the
   // form that stream capture accepts
   cudaLaunchConfig_t cfg = {};

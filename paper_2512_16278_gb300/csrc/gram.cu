@@ -207,7 +207,7 @@ gram_u8_kernel(GramArgs g) {
 // Pearson correlation from the exact sums: one warp per cell.
 __global__ void corr_from_sums_kernel(const int64_t* __restrict__ sums, int64_t n_cells,
                                       int n_beam, int psum, int np, float* __restrict__ corr,
-                                      unsigned long long* degenerate) {
+                                      unsigned long long* degenerate, int interleaved) {
   extern __shared__ unsigned char sm_raw[];
   const int warps = blockDim.x / 32;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -217,8 +217,13 @@ __global__ void corr_from_sums_kernel(const int64_t* __restrict__ sums, int64_t 
   const int64_t cell = (int64_t)blockIdx.x * warps + warp;
   if (cell >= n_cells) return;
   const int N1 = n_beam + 1;
-  const int64_t* src = sums + cell * psum;
-  for (int e = lane; e < psum; e += 32) S[e] = src[e];
+  if (interleaved) {  // [cell / 8][P][cell % 8]
+    const int64_t* src = sums + (cell >> 3) * psum * 8 + (cell & 7);
+    for (int e = lane; e < psum; e += 32) S[e] = src[(int64_t)e * 8];
+  } else {
+    const int64_t* src = sums + cell * psum;
+    for (int e = lane; e < psum; e += 32) S[e] = src[e];
+  }
   __syncwarp();
   const int64_t n = S[psum - 1];
   int deg = 0;
@@ -318,7 +323,7 @@ cudaError_t launch_gram_u8(const mraid_plan_s* pl, const uint8_t* d_data, int su
 }
 
 cudaError_t launch_corr_from_sums(const mraid_plan_s* pl, const int64_t* d_sums, int64_t n_cells,
-                                  float* d_corr) {
+                                  float* d_corr, bool interleaved) {
   const int psum = pl->psum;
   int warps = (int)(40960 / ((size_t)psum * 8 + kMaxBeam * 4));
   warps = warps < 1 ? 1 : (warps > 8 ? 8 : warps);
@@ -329,7 +334,8 @@ cudaError_t launch_corr_from_sums(const mraid_plan_s* pl, const int64_t* d_sums,
   const int64_t blocks = (n_cells + warps - 1) / warps;
   if (blocks > 0)
     corr_from_sums_kernel<<<(unsigned)blocks, warps * 32, smem, pl->stream>>>(
-        d_sums, n_cells, pl->p.n_beam, psum, pl->np, d_corr, pl->d_degenerate);
+        d_sums, n_cells, pl->p.n_beam, psum, pl->np, d_corr, pl->d_degenerate,
+        interleaved ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -74,6 +74,7 @@ struct TcArgs {
   int R2;   // slots 16..N per group (0 if N + 1 <= 16)
   int rb;   // slots in B of the first MMAs (R rounded up to even)
   int64_t* sums;
+  int64_t* sums8;  // the same sums as [cell / 8][P][cell % 8] (internal layout)
   float* corr;
   unsigned long long* degenerate;
   unsigned* error;
@@ -532,9 +533,16 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
             dst[b - a] = r;
           }
         }
-        if (g.sums) {
+        if (g.sums || g.sums8) {
           const int N1 = N + 1;
-          int64_t* dst = g.sums + cell * (int64_t)(N1 * (N1 + 1) / 2) + (a * N1 - a * (a - 1) / 2);
+          const int64_t P = N1 * (N1 + 1) / 2;
+          const int row = a * N1 - a * (a - 1) / 2;
+          // public layout: one cell's entries contiguous; interleaved: the
+          // 8 channels of a group side by side, so a warp's 8-byte stores
+          // fill 64-byte runs
+          int64_t* dst = g.sums8 ? g.sums8 + ((cell >> 3) * P + row) * 8 + (cell & 7)
+                                 : g.sums + cell * P + row;
+          const int step = g.sums8 ? 8 : 1;
 #pragma unroll
           for (int jb = 0; jb < NB; ++jb) {
             const int b = slot_of(jb);
@@ -544,7 +552,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
             if (a == N) v = n;                                  // (N, N): sample count
             else if (b == N) v = gab + 128 * n;                 // S_a
             else v = gab + 128 * (sa + (int64_t)s->s_sum[grp][c][b]) + 16384 * n;
-            dst[b - a] = v;
+            dst[(b - a) * step] = v;
           }
         }
       };
@@ -979,7 +987,7 @@ bool gram_tc_supported(const mraid_plan_s* pl, const void* d_data) {
 }
 
 cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int sub0, int n_sub,
-                           int64_t* d_sums, float* d_corr) {
+                           int64_t* d_sums, float* d_corr, int64_t* d_sums8) {
   const mraid_params& p = pl->p;
   if (!gram_tc_supported(pl, d_data)) return cudaErrorNotSupported;
   CUtensorMap map;
@@ -1004,7 +1012,8 @@ cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int su
   a.R = R;
   a.R2 = R > 16 ? R - 16 : 0;
   a.rb = (R + 1) / 2 * 2;                  // B of the first MMAs: R slots, even count
-  a.sums = d_sums;
+  a.sums = d_sums8 ? nullptr : d_sums;
+  a.sums8 = d_sums8;
   a.corr = d_corr;
   a.degenerate = pl->d_degenerate;
   a.error = pl->d_error;
@@ -1071,6 +1080,7 @@ cudaError_t launch_gram_tc_f32(const mraid_plan_s* pl, const float* d_data, int 
   a.R2 = R > 16 ? R - 16 : 0;
   a.rb = (R + 1) / 2 * 2;
   a.sums = nullptr;
+  a.sums8 = nullptr;
   a.corr = d_corr;
   a.degenerate = pl->d_degenerate;
   a.error = pl->d_error;

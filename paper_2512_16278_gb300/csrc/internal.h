@@ -15,6 +15,7 @@ constexpr int kMaxBeam = 128;
 constexpr int kRefBlocks = 4096;  // eigenvector refinement: partial-sum blocks
 constexpr int kMaxSampSub = 1 << 20;
 constexpr int kMaxClipIter = 1000;
+constexpr int kMaxLevels = 16;  // timescales in one mraid_multires call
 // Samples per int32 accumulation segment: 32768 * 255^2 < 2^32 (unsigned).
 constexpr int kGramSegment = 32768;
 
@@ -22,7 +23,7 @@ struct FlagDev {  // device image of mraid_flag_info
   mraid_flag_info info;
 };
 
-enum KernelId { K_GRAM = 0, K_CORR, K_EIG, K_FLAG, K_GRAM_TC, K_GRAM_F32, K_GRAM_TC_F32, K_COUNT };
+enum KernelId { K_GRAM = 0, K_CORR, K_EIG, K_FLAG, K_GRAM_TC, K_GRAM_F32, K_GRAM_TC_F32, K_AGG, K_COUNT };
 const char* kernel_name(int id);
 
 struct Profiler {
@@ -86,6 +87,14 @@ struct mraid_plan_s {
   double* d_refine_part = nullptr;   // eigenvector refinement: [block][N][3]
   float* d_refine_thresh = nullptr;  // [N]
   double* d_refine_ms = nullptr;     // [N][2] when the caller passes none
+  // several timescales (mraid_multires): Gram sums of the longer levels,
+  // per-level flag reports on the device and pinned staging
+  int64_t* ml_sums = nullptr;
+  size_t ml_sums_elems = 0;
+  mraid_flag_info* d_ml_info = nullptr;  // [kMaxLevels]
+  mraid_flag_info* h_ml_info = nullptr;  // [kMaxLevels], pinned
+  mraid_flag_info* pending_ml = nullptr;
+  int pending_ml_n = 0;
 };
 
 namespace mraid {
@@ -116,15 +125,18 @@ int tc_variant_samples(int v);
 int tc_default_variant(int n_beam);
 constexpr int kTcVariants = 8;
 constexpr int kEigVariants = 4;  // register eigensolvers (see eig_variant)
+// d_sums8 (instead of d_sums): the sums in the interleaved layout
+// [cell / 8][P][cell % 8], which the kernel writes in 64-byte runs
 cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int sub0, int n_sub,
-                           int64_t* d_sums, float* d_corr);
+                           int64_t* d_sums, float* d_corr, int64_t* d_sums8 = nullptr);
 // float32 samples on the tensor cores (split-bf16 products, gram_tc.cu):
 // correlation only, d_corr relative to sub0
 bool gram_tc_f32_supported(const mraid_plan_s* pl, const void* d_data);
 cudaError_t launch_gram_tc_f32(const mraid_plan_s* pl, const float* d_data, int sub0, int n_sub,
                                float* d_corr);
+// interleaved: d_sums in the [cell / 8][P][cell % 8] layout
 cudaError_t launch_corr_from_sums(const mraid_plan_s* pl, const int64_t* d_sums,
-                                  int64_t n_cells, float* d_corr);
+                                  int64_t n_cells, float* d_corr, bool interleaved = false);
 // eig.cu
 cudaError_t launch_eig(const mraid_plan_s* pl, const float* d_corr, int64_t n_cells,
                        float* d_evals, float* d_q1, float* d_stat);
@@ -145,8 +157,14 @@ bool eig_q1_needs_evals(int n_beam);
 // refine.cu
 cudaError_t launch_refine(mraid_plan_s* pl, const float* d_q1, const uint8_t* d_flags,
                           uint32_t* d_bits, double* d_mu_sigma);
-// flag.cu
-cudaError_t launch_flag(mraid_plan_s* pl, const float* d_stat, uint8_t* d_flags);
+// flag.cu: over the plan's cells into its device report, or over n_cells
+// cells into d_info when those are given
+cudaError_t launch_flag(mraid_plan_s* pl, const float* d_stat, uint8_t* d_flags,
+                        int64_t n_cells = -1, mraid_flag_info* d_info = nullptr);
+// multires.cu: d_dst[k] = sum_{j < m} d_src[k m + j] over the int64 Gram
+// sums of n_out_sub sub-intervals (n_chan cells each)
+cudaError_t launch_gram_aggregate(const mraid_plan_s* pl, const int64_t* d_src, int64_t* d_dst,
+                                  int n_out_sub, int m);
 int flag_grid_blocks(int device, int sm_count);
 
 }  // namespace mraid
