@@ -66,9 +66,17 @@ def _load():
         lib.orc_cells_u8.argtypes = [_P, i32, i64, i32, i32, i64, _P, _P, i32, _P, _P, _P, _P]
         lib.orc_flag.argtypes = [_P, i64, i32, _P, dbl, i32, _P, ctypes.POINTER(FlagInfo)]
         lib.orc_beam_flags.argtypes = [_P, _P, i64, i32, _P, i32, dbl, _P, _P]
+        lib.orc_whittaker.argtypes = [_P, _P, i32, dbl, _P]
+        lib.orc_arpls.argtypes = [_P, i32, dbl, dbl, i32, _P]
+        lib.orc_bandpass_input_u8.argtypes = [_P, i32, i64, i32, i32, i32, i32, i32, _P]
+        lib.orc_cell_ccm_bandpass_u8.argtypes = [_P, i32, i64, i32, i32, i32, i32, _P, _P]
+        lib.orc_block_bandpass_u8.argtypes = [_P, i32, i64, i32, i32, i32, i32, dbl, dbl, i32,
+                                              i32, _P, _P, _P, _P]
         for f in ("orc_cell_gram_u8", "orc_cell_cov_f32", "orc_corr_from_gram",
                   "orc_corr_from_cov", "orc_jacobi", "orc_cell_u8", "orc_block_u8",
-                  "orc_cells_u8", "orc_flag", "orc_beam_flags"):
+                  "orc_cells_u8", "orc_flag", "orc_beam_flags", "orc_whittaker", "orc_arpls",
+                  "orc_bandpass_input_u8", "orc_cell_ccm_bandpass_u8",
+                  "orc_block_bandpass_u8"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -223,3 +231,60 @@ def beam_flags(q1: np.ndarray, flags: np.ndarray, n_chan: int, keep: Optional[np
     _check(_load().orc_beam_flags(_ptr(q1), _ptr(flags), n_cells, n_chan, _ptr(kp), n_beam, t,
                                   _ptr(bits), _ptr(ms)), "beam_flags")
     return bits, ms
+
+
+# ------------------------------------------------------------------ bandpass
+# Section 3.1 (ArPLS bandpass; Baek, Park, Ahn and Ahn 2015) and the
+# bandpass-centred reading of Eq. 1.
+
+def whittaker(y: np.ndarray, w: np.ndarray, lam: float) -> np.ndarray:
+    """z solving (W + lam D^T D) z = W y (D: second differences), FP64."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    z = np.zeros_like(y)
+    _check(_load().orc_whittaker(_ptr(y), _ptr(w), y.shape[0], lam, _ptr(z)), "whittaker")
+    return z
+
+
+def arpls(y: np.ndarray, lam: float, ratio: float, itermax: int):
+    """(baseline z, solves) of the ArPLS fit of y."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    z = np.zeros_like(y)
+    it = _check(_load().orc_arpls(_ptr(y), y.shape[0], lam, ratio, itermax, _ptr(z)), "arpls")
+    return z, it
+
+
+def bandpass_input(data: np.ndarray, n_samp_sub: int, sub0: int, n_subs: int, beam: int):
+    """Time-aggregated spectrum of one beam over [sub0, sub0 + n_subs)."""
+    n_beam, bstride, n_chan = _block_view(data)
+    y = np.zeros(n_chan)
+    _check(_load().orc_bandpass_input_u8(_ptr(data), n_beam, bstride, n_chan, n_samp_sub,
+                                         sub0, n_subs, beam, _ptr(y)), "bandpass_input")
+    return y
+
+
+def cell_ccm_bandpass(data: np.ndarray, n_samp_sub: int, sub: int, chan: int, zc) -> np.ndarray:
+    """C (N x N) of one cell about the bandpass values zc[a] (FP64)."""
+    n_beam, bstride, n_chan = _block_view(data)
+    zc = np.ascontiguousarray(zc, dtype=np.float64)
+    C = np.zeros((n_beam, n_beam))
+    _check(_load().orc_cell_ccm_bandpass_u8(_ptr(data), n_beam, bstride, n_chan, n_samp_sub,
+                                            sub, chan, _ptr(zc), _ptr(C)), "ccm_bandpass")
+    return C
+
+
+def block_bandpass(data: np.ndarray, n_samp_sub: int, interval: int, lam: float, ratio: float,
+                   itermax: int, n_threads: int = 1, want_evals: bool = True) -> dict:
+    """Whole block under the bandpass-centred reading: z [interval][beam][chan],
+    iters [interval][beam], evals [cell][N], stat [cell]."""
+    n_beam, bstride, n_chan = _block_view(data)
+    n_sub = data.shape[1] // n_samp_sub
+    n_int = (n_sub + interval - 1) // interval
+    z = np.zeros((n_int, n_beam, n_chan))
+    it = np.zeros((n_int, n_beam), dtype=np.int32)
+    ev = np.zeros((n_sub * n_chan, n_beam)) if want_evals else None
+    st = np.zeros(n_sub * n_chan)
+    _check(_load().orc_block_bandpass_u8(_ptr(data), n_beam, bstride, n_chan, n_samp_sub, n_sub,
+                                         interval, lam, ratio, itermax, n_threads, _ptr(z),
+                                         _ptr(it), _ptr(ev), _ptr(st)), "block_bandpass")
+    return {"z": z, "iters": it, "evals": ev, "stat": st}

@@ -430,3 +430,229 @@ int orc_beam_flags(const double* q1, const uint8_t* flags, int64_t n_cells, int3
   free(sg);
   return 0;
 }
+
+/* ------------------------------------- Section 3.1: bandpass with ArPLS */
+
+int orc_whittaker(const double* y, const double* w, int32_t n, double lam, double* z) {
+  if (!y || !w || !z || n < 3 || !(lam >= 0.0)) return -1;
+  /* A = W + lam D^T D as three bands: A[i][i], A[i][i+1], A[i][i+2].
+   * D^T D is accumulated row by row of D (coefficients 1, -2, 1). */
+  double* a0 = calloc((size_t)n, sizeof(double));
+  double* a1 = calloc((size_t)n, sizeof(double));
+  double* a2 = calloc((size_t)n, sizeof(double));
+  double* l1 = calloc((size_t)n, sizeof(double));
+  double* l2 = calloc((size_t)n, sizeof(double));
+  double* dg = calloc((size_t)n, sizeof(double));
+  double* u = calloc((size_t)n, sizeof(double));
+  int rc = 0;
+  if (!a0 || !a1 || !a2 || !l1 || !l2 || !dg || !u) {
+    rc = -1;
+    goto done;
+  }
+  {
+    const double c[3] = {1.0, -2.0, 1.0};
+    for (int32_t k = 0; k + 2 < n; ++k)
+      for (int p = 0; p < 3; ++p)
+        for (int q = p; q < 3; ++q) {
+          const double v = lam * c[p] * c[q];
+          if (q == p) a0[k + p] += v;
+          else if (q == p + 1) a1[k + p] += v;
+          else a2[k + p] += v;
+        }
+    for (int32_t i = 0; i < n; ++i) a0[i] += w[i];
+    /* A = L diag(dg) L^T, L unit lower with L[i][i-1] = l1[i], L[i][i-2] = l2[i] */
+    for (int32_t i = 0; i < n; ++i) {
+      l2[i] = (i >= 2) ? a2[i - 2] / dg[i - 2] : 0.0;
+      l1[i] = (i >= 1) ? (a1[i - 1] - ((i >= 2) ? l2[i] * dg[i - 2] * l1[i - 1] : 0.0)) / dg[i - 1]
+                       : 0.0;
+      dg[i] = a0[i] - ((i >= 1) ? l1[i] * l1[i] * dg[i - 1] : 0.0) -
+              ((i >= 2) ? l2[i] * l2[i] * dg[i - 2] : 0.0);
+      if (!(dg[i] > 0.0)) {
+        rc = -1;
+        goto done;
+      }
+    }
+    /* L u = W y; then L^T z = u / dg */
+    for (int32_t i = 0; i < n; ++i)
+      u[i] = w[i] * y[i] - ((i >= 1) ? l1[i] * u[i - 1] : 0.0) -
+             ((i >= 2) ? l2[i] * u[i - 2] : 0.0);
+    for (int32_t i = n - 1; i >= 0; --i)
+      z[i] = u[i] / dg[i] - ((i + 1 < n) ? l1[i + 1] * z[i + 1] : 0.0) -
+             ((i + 2 < n) ? l2[i + 2] * z[i + 2] : 0.0);
+  }
+done:
+  free(a0);
+  free(a1);
+  free(a2);
+  free(l1);
+  free(l2);
+  free(dg);
+  free(u);
+  return rc;
+}
+
+int orc_arpls(const double* y, int32_t n, double lam, double ratio, int32_t itermax,
+              double* z) {
+  if (!y || !z || n < 3 || itermax < 1) return -1;
+  double* w = malloc(sizeof(double) * (size_t)n);
+  double* wt = malloc(sizeof(double) * (size_t)n);
+  if (!w || !wt) {
+    free(w);
+    free(wt);
+    return -1;
+  }
+  for (int32_t i = 0; i < n; ++i) w[i] = 1.0;
+  int32_t solves = 0;
+  int rc = 0;
+  while (solves < itermax) {
+    if (orc_whittaker(y, w, n, lam, z) < 0) {
+      rc = -1;
+      break;
+    }
+    ++solves;
+    /* statistics of the negative residuals */
+    double sum = 0.0, sum2 = 0.0;
+    int64_t cnt = 0;
+    for (int32_t i = 0; i < n; ++i) {
+      const double d = y[i] - z[i];
+      if (d < 0.0) {
+        sum += d;
+        ++cnt;
+      }
+    }
+    if (cnt == 0) break;
+    const double m = sum / (double)cnt;
+    for (int32_t i = 0; i < n; ++i) {
+      const double d = y[i] - z[i];
+      if (d < 0.0) sum2 += (d - m) * (d - m);
+    }
+    const double s = sqrt(sum2 / (double)cnt);
+    if (!(s > 0.0)) break;
+    double dw2 = 0.0, w2 = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+      const double d = y[i] - z[i];
+      wt[i] = 1.0 / (1.0 + exp(2.0 * (d - (2.0 * s - m)) / s));
+      dw2 += (w[i] - wt[i]) * (w[i] - wt[i]);
+      w2 += w[i] * w[i];
+    }
+    if (sqrt(dw2) / sqrt(w2) < ratio) break;
+    for (int32_t i = 0; i < n; ++i) w[i] = wt[i];
+  }
+  free(w);
+  free(wt);
+  return rc < 0 ? -1 : solves;
+}
+
+int orc_bandpass_input_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
+                          int32_t n_chan, int32_t n_samp_sub, int32_t sub0, int32_t n_subs,
+                          int32_t beam, double* y) {
+  if (!data || !y || beam < 0 || beam >= n_beam || n_subs < 1 || sub0 < 0) return -1;
+  const int64_t t0 = (int64_t)sub0 * n_samp_sub, nt = (int64_t)n_subs * n_samp_sub;
+  for (int32_t j = 0; j < n_chan; ++j) {
+    int64_t s = 0;
+    for (int64_t t = 0; t < nt; ++t) s += data[beam * beam_stride + (t0 + t) * n_chan + j];
+    y[j] = (double)s / (double)nt;
+  }
+  return 0;
+}
+
+int orc_cell_ccm_bandpass_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
+                             int32_t n_chan, int32_t n_samp_sub, int32_t sub, int32_t chan,
+                             const double* zc, double* C) {
+  if (!data || !zc || !C || n_beam < 1 || chan < 0 || chan >= n_chan || sub < 0) return -1;
+  const int64_t t0 = (int64_t)sub * n_samp_sub;
+  for (int32_t a = 0; a < n_beam; ++a)
+    for (int32_t b = 0; b < n_beam; ++b) {
+      double s = 0.0;
+      for (int32_t t = 0; t < n_samp_sub; ++t) {
+        const double xa = data[a * beam_stride + (t0 + t) * n_chan + chan] - zc[a];
+        const double xb = data[b * beam_stride + (t0 + t) * n_chan + chan] - zc[b];
+        s += xa * xb;
+      }
+      C[a * n_beam + b] = s / (double)n_samp_sub;
+    }
+  return 0;
+}
+
+typedef struct {
+  const uint8_t* data;
+  int32_t n_beam, n_chan, n_samp_sub, interval;
+  int64_t beam_stride;
+  const double* z;
+  int64_t i0, i1;
+  double *evals, *stat;
+  int rc;
+} bp_job;
+
+static void* bp_worker(void* arg) {
+  bp_job* j = (bp_job*)arg;
+  const int32_t N = j->n_beam;
+  double* zc = malloc(sizeof(double) * (size_t)N);
+  double* C = malloc(sizeof(double) * (size_t)N * N);
+  double* ev = malloc(sizeof(double) * (size_t)N);
+  j->rc = (zc && C && ev) ? 0 : -1;
+  for (int64_t i = j->i0; i < j->i1 && j->rc == 0; ++i) {
+    const int32_t sub = (int32_t)(i / j->n_chan), chan = (int32_t)(i % j->n_chan);
+    const int32_t I = sub / j->interval;
+    for (int32_t a = 0; a < N; ++a) zc[a] = j->z[((int64_t)I * N + a) * j->n_chan + chan];
+    if (orc_cell_ccm_bandpass_u8(j->data, N, j->beam_stride, j->n_chan, j->n_samp_sub, sub,
+                                 chan, zc, C) < 0 ||
+        orc_jacobi(C, N, ev, NULL, NULL) < 0) {
+      j->rc = -1;
+      break;
+    }
+    if (j->evals)
+      for (int32_t a = 0; a < N; ++a) j->evals[i * N + a] = ev[a];
+    j->stat[i] = orc_stat(ev, N);
+  }
+  free(zc);
+  free(C);
+  free(ev);
+  return NULL;
+}
+
+int orc_block_bandpass_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
+                          int32_t n_chan, int32_t n_samp_sub, int32_t n_sub, int32_t interval,
+                          double lam, double ratio, int32_t itermax, int32_t n_threads,
+                          double* z, int32_t* iters, double* evals, double* stat) {
+  if (!data || !stat || n_beam < 1 || n_chan < 3 || n_sub < 1 || interval < 1) return -1;
+  const int32_t n_int = (n_sub + interval - 1) / interval;
+  double* zz = z ? z : malloc(sizeof(double) * (size_t)n_int * n_beam * n_chan);
+  double* y = malloc(sizeof(double) * (size_t)n_chan);
+  int rc = (zz && y) ? 0 : -1;
+  for (int32_t I = 0; I < n_int && rc == 0; ++I) {
+    const int32_t s0 = I * interval;
+    const int32_t ns = (n_sub - s0) < interval ? (n_sub - s0) : interval;
+    for (int32_t a = 0; a < n_beam && rc == 0; ++a) {
+      double* za = zz + ((int64_t)I * n_beam + a) * n_chan;
+      if (orc_bandpass_input_u8(data, n_beam, beam_stride, n_chan, n_samp_sub, s0, ns, a, y) < 0)
+        rc = -1;
+      const int it = rc == 0 ? orc_arpls(y, n_chan, lam, ratio, itermax, za) : -1;
+      if (it < 0) rc = -1;
+      if (iters && rc == 0) iters[(int64_t)I * n_beam + a] = it;
+    }
+  }
+  if (rc == 0) {
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 512) n_threads = 512;
+    const int64_t n_cells = (int64_t)n_sub * n_chan;
+    pthread_t th[512];
+    bp_job jobs[512];
+    int created[512];
+    for (int32_t i = 0; i < n_threads; ++i) {
+      bp_job j = {data, n_beam, n_chan, n_samp_sub, interval, beam_stride, zz,
+                  n_cells * i / n_threads, n_cells * (i + 1) / n_threads, evals, stat, -1};
+      jobs[i] = j;
+      created[i] = i > 0 && pthread_create(&th[i], NULL, bp_worker, &jobs[i]) == 0;
+    }
+    for (int32_t i = 0; i < n_threads; ++i)
+      if (!created[i]) bp_worker(&jobs[i]);
+    for (int32_t i = 0; i < n_threads; ++i) {
+      if (created[i]) pthread_join(th[i], NULL);
+      rc |= jobs[i].rc;
+    }
+  }
+  if (!z) free(zz);
+  free(y);
+  return rc;
+}

@@ -110,6 +110,58 @@ int orc_beam_flags(const double* q1, const uint8_t* flags, int64_t n_cells, int3
                    const uint8_t* keep, int32_t n_beam, double t, uint32_t* bits,
                    double* mu_sigma);
 
+/* ------------------------------------------------------------------------
+ * Section 3.1 bandpass and the bandpass-centred reading of Eq. 1.
+ *
+ * The bandpass of one beam over a fit interval is the time-aggregated
+ * spectrum (the mean of each channel over the interval's samples); its
+ * baseline z is fitted over channels with ArPLS (asymmetrically reweighted
+ * penalized least squares, Baek, Park, Ahn and Ahn 2015, the method Section
+ * 3.1 names; parameters lam, ratio, itermax as in Section 4.5's list) and
+ * subtracted from every sample of the channel. Under the bandpass-centred
+ * reading the CCM is C_ab = (1/N_s) sum_t (x_a(t) - z_a)(x_b(t) - z_b)
+ * with no further centring or normalisation. */
+
+/* One weighted Whittaker solve: z minimising sum_i w_i (y_i - z_i)^2 +
+ * lam sum_k (z_k - 2 z_{k+1} + z_{k+2})^2, i.e. (W + lam D^T D) z = W y,
+ * D the (n-2) x n second-difference matrix. The pentadiagonal symmetric
+ * system is factored as L D L^T (unit lower-banded L) and solved by forward
+ * and back substitution, FP64. n >= 3. Returns 0, or -1 on bad arguments or
+ * a non-positive pivot. */
+int orc_whittaker(const double* y, const double* w, int32_t n, double lam, double* z);
+
+/* ArPLS baseline of y (n points): unit weights; then repeatedly z =
+ * orc_whittaker(y, w); d = y - z; m and s = mean and population standard
+ * deviation of the negative d_i; new weights 1 / (1 + exp(2 (d_i - (2 s - m))
+ * / s)); stop when |w_new - w| / |w| < ratio (Euclidean norms), when no d_i
+ * is negative or s == 0, or after itermax solves; z is the last solve.
+ * Returns the number of solves (>= 1), or -1. */
+int orc_arpls(const double* y, int32_t n, double lam, double ratio, int32_t itermax,
+              double* z);
+
+/* Time-aggregated spectrum of beam `beam` over sub-integrations
+ * [sub0, sub0 + n_subs): y[j] = mean of x(t, j) over those samples. */
+int orc_bandpass_input_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
+                          int32_t n_chan, int32_t n_samp_sub, int32_t sub0, int32_t n_subs,
+                          int32_t beam, double* y);
+
+/* C (N x N, FP64) of one cell under the bandpass-centred reading; zc[a] is
+ * beam a's fitted bandpass at this cell's channel. */
+int orc_cell_ccm_bandpass_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
+                             int32_t n_chan, int32_t n_samp_sub, int32_t sub, int32_t chan,
+                             const double* zc, double* C);
+
+/* Whole block under the bandpass-centred reading: fit intervals of
+ * `interval` sub-integrations (the last one may be shorter), per interval
+ * and beam the ArPLS baseline of the time-aggregated spectrum (z out:
+ * [interval][beam][chan], may be NULL; iters out: [interval][beam], may be
+ * NULL), then per cell C, its eigenvalues (FP64 Jacobi) and the statistic.
+ * evals [cell][N] may be NULL; stat [cell] required. Returns 0 or -1. */
+int orc_block_bandpass_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
+                          int32_t n_chan, int32_t n_samp_sub, int32_t n_sub, int32_t interval,
+                          double lam, double ratio, int32_t itermax, int32_t n_threads,
+                          double* z, int32_t* iters, double* evals, double* stat);
+
 #ifdef __cplusplus
 }
 #endif
