@@ -212,6 +212,50 @@ mraid_status mraid_multires(mraid_plan_t plan, const void* d_data, int32_t n_lev
                             const int32_t* factors, float* const* d_stats,
                             uint8_t* const* d_flags, mraid_flag_info* infos);
 
+/* Bandpass normalisation (Section 3.1) with ArPLS, the asymmetrically
+ * reweighted penalized least squares of Baek, Park, Ahn and Ahn (2015) that
+ * the paper uses; Section 4.5 names its three parameters without values. */
+typedef struct {
+  double lam;        /* weight of the second-difference penalty (smoothness), > 0 */
+  double ratio;      /* stop when |w_new - w| / |w| < ratio (Euclidean norms), > 0 */
+  int32_t itermax;   /* bound on weighted solves, 1..1000 */
+  int32_t interval;  /* sub-integrations per bandpass fit interval, >= 1 (the last
+                        interval of a block may be shorter) */
+} mraid_bandpass_params;
+
+/* lam 1e5, ratio 1e-3, itermax 50, interval 20 (about 1 s of 1024-sample
+ * sub-integrations at 49.152 us, Section 3.1's example). Host only. */
+void mraid_default_bandpass_params(mraid_bandpass_params* bp);
+
+/* ArPLS baselines of n_sys spectra on the plan's device and stream: start
+ * with unit weights w; repeat: solve (W + lam D^T D) z = W y (D: second
+ * differences over the n points; FP64, banded LDL^T); d = y - z; m, s =
+ * mean and population standard deviation of the negative d_i; new weights
+ * 1 / (1 + exp(2 (d_i - (2 s - m)) / s)); stop when the weights moved by
+ * less than ratio, when no d_i is negative or s is 0, or after itermax
+ * solves (bp->interval is not used here).
+ *   d_y:     float64 [n_sys][n], device, n >= 3.
+ *   d_z:     float64 [n_sys][n], device: the last solve.
+ *   d_iters: int32 [n_sys] or NULL: solves made, -1 if a pivot of the
+ *            system was not positive (z is then not valid). */
+mraid_status mraid_arpls(mraid_plan_t plan, const double* d_y, int32_t n_sys, int32_t n,
+                         const mraid_bandpass_params* bp, double* d_z, int32_t* d_iters);
+
+/* The whole path under the bandpass-centred reading of Eq. 1: per fit
+ * interval and beam, the time-aggregated spectrum (the mean of each channel
+ * over the interval's samples, exact from the Gram sums) and its ArPLS
+ * baseline z; per cell C_ab = (1/N_s) sum_t (x_a - z_a)(x_b - z_b), the
+ * beams' power with the bandpass subtracted "uniformly across all time
+ * samples" (Section 3.1) and no further centring or normalisation; then
+ * Eq. 2 and the masking as in mraid_run. 8-bit samples.
+ *   d_bandpass: float32 [ceil(n_sub / interval)][N][n_chan] or NULL: z.
+ *   d_evals, d_q1: as in mraid_run (may be NULL); d_stat, d_flags required.
+ *   info: as in mraid_run (n_degenerate is 0: nothing is normalised). */
+mraid_status mraid_run_bandpass(mraid_plan_t plan, const void* d_data,
+                                const mraid_bandpass_params* bp, float* d_bandpass,
+                                float* d_evals, float* d_q1, float* d_stat, uint8_t* d_flags,
+                                mraid_flag_info* info);
+
 /* Autotuner (the paper has no counterpart; it picks among this library's
  * kernel variants). Times, `reps` runs each on d_data, every Gram variant
  * that fits the plan's shape (eight tensor-core variants over samples per

@@ -27,7 +27,8 @@ __all__ = [
     "mraid_batch_destroy", "UnitIO", "Batch", "mraid_serve_open", "mraid_serve_submit",
     "mraid_serve_poll", "mraid_serve_drain", "mraid_serve_close", "StreamDesc", "BlockResult",
     "Server", "mraid_autotune", "mraid_set_variant", "mraid_set_eig_variant", "tune",
-    "mraid_refine", "mraid_multires", "STATUS",
+    "mraid_refine", "mraid_multires", "BandpassParams", "mraid_default_bandpass_params",
+    "mraid_arpls", "mraid_run_bandpass", "STATUS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -41,6 +42,13 @@ class MraidError(RuntimeError):
     def __init__(self, status: int, where: str, detail: str = ""):
         self.status = status
         super().__init__(f"{where}: {STATUS.get(status, status)} ({detail})")
+
+
+class BandpassParams(ctypes.Structure):
+    """mraid_bandpass_params (Section 3.1 ArPLS bandpass; lam, ratio and
+    itermax as Section 4.5 names them; interval in sub-integrations)."""
+    _fields_ = [("lam", ctypes.c_double), ("ratio", ctypes.c_double),
+                ("itermax", ctypes.c_int32), ("interval", ctypes.c_int32)]
 
 
 class Params(ctypes.Structure):
@@ -161,6 +169,10 @@ def load():
         "mraid_refine": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "mraid_multires": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(vp),
                                           ctypes.POINTER(vp), ctypes.POINTER(FlagInfo)]),
+        "mraid_default_bandpass_params": (None, [ctypes.POINTER(BandpassParams)]),
+        "mraid_arpls": (ctypes.c_int, [vp, vp, i32, i32, ctypes.POINTER(BandpassParams), vp, vp]),
+        "mraid_run_bandpass": (ctypes.c_int, [vp, vp, ctypes.POINTER(BandpassParams), vp, vp, vp,
+                                              vp, vp, ctypes.POINTER(FlagInfo)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -254,6 +266,27 @@ def mraid_multires(plan: int, d_data, factors, d_stats, d_flags, infos=None):
     st = (ctypes.c_void_p * n)(*[_ptr(x) for x in d_stats])
     fl = (ctypes.c_void_p * n)(*[_ptr(x) for x in d_flags])
     _check(load().mraid_multires(plan, _ptr(d_data), n, f, st, fl, infos), "mraid_multires")
+
+
+def mraid_default_bandpass_params(**kw) -> BandpassParams:
+    bp = BandpassParams()
+    load().mraid_default_bandpass_params(ctypes.byref(bp))
+    for k, v in kw.items():
+        setattr(bp, k, v)
+    return bp
+
+
+def mraid_arpls(plan: int, d_y, n_sys: int, n: int, bp: BandpassParams, d_z, d_iters=None):
+    _check(load().mraid_arpls(plan, _ptr(d_y), n_sys, n, ctypes.byref(bp), _ptr(d_z),
+                              _ptr(d_iters)), "mraid_arpls")
+
+
+def mraid_run_bandpass(plan: int, d_data, bp: BandpassParams, d_bandpass, d_evals, d_q1, d_stat,
+                       d_flags, info: Optional[FlagInfo] = None):
+    _check(load().mraid_run_bandpass(plan, _ptr(d_data), ctypes.byref(bp), _ptr(d_bandpass),
+                                     _ptr(d_evals), _ptr(d_q1), _ptr(d_stat), _ptr(d_flags),
+                                     ctypes.byref(info) if info is not None else None),
+           "mraid_run_bandpass")
 
 
 def mraid_sync(plan: int):
@@ -537,6 +570,38 @@ class Plan:
         mraid_sync(self.handle)
         return [{"factor": f, "stat": stats[i], "flags": flags[i], "info": infos[i].as_dict()}
                 for i, f in enumerate(factors)]
+
+    def arpls(self, y, **kw):
+        """(z, solves) of the ArPLS baselines of the rows of y (float64
+        [n_sys][n] on the device); keywords override lam, ratio, itermax."""
+        t = self.torch
+        bp = mraid_default_bandpass_params(**kw)
+        z = t.empty_like(y)
+        it = t.empty(y.shape[0], dtype=t.int32, device=self.device)
+        mraid_arpls(self.handle, y, y.shape[0], y.shape[1], bp, z, it)
+        mraid_sync(self.handle)
+        return z, it
+
+    def run_bandpass(self, data, evals: bool = True, q1: bool = False, **kw):
+        """Whole path under the bandpass-centred reading; keywords override
+        lam, ratio, itermax, interval."""
+        t = self.torch
+        bp = mraid_default_bandpass_params(**kw)
+        n_int = (self.n_sub + bp.interval - 1) // bp.interval
+        N = self.n_beam
+        out = {
+            "bandpass": self._empty(n_int, N, self.n_chan, dtype=t.float32),
+            "evals": self._empty(self.n_cells, N, dtype=t.float32) if evals else None,
+            "q1": self._empty(self.n_cells, N, dtype=t.float32) if q1 else None,
+            "stat": self._empty(self.n_cells, dtype=t.float32),
+            "flags": self._empty(self.n_cells, dtype=t.uint8),
+        }
+        info = FlagInfo()
+        mraid_run_bandpass(self.handle, data, bp, out["bandpass"], out["evals"], out["q1"],
+                           out["stat"], out["flags"], info)
+        mraid_sync(self.handle)
+        out["info"] = info.as_dict()
+        return out
 
     def sync(self):
         mraid_sync(self.handle)

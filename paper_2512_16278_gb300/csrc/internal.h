@@ -23,7 +23,10 @@ struct FlagDev {  // device image of mraid_flag_info
   mraid_flag_info info;
 };
 
-enum KernelId { K_GRAM = 0, K_CORR, K_EIG, K_FLAG, K_GRAM_TC, K_GRAM_F32, K_GRAM_TC_F32, K_AGG, K_COUNT };
+enum KernelId {
+  K_GRAM = 0, K_CORR, K_EIG, K_FLAG, K_GRAM_TC, K_GRAM_F32, K_GRAM_TC_F32, K_AGG,
+  K_BP_INPUT, K_ARPLS, K_CCM_BP, K_COUNT
+};
 const char* kernel_name(int id);
 
 struct Profiler {
@@ -95,6 +98,16 @@ struct mraid_plan_s {
   mraid_flag_info* h_ml_info = nullptr;  // [kMaxLevels], pinned
   mraid_flag_info* pending_ml = nullptr;
   int pending_ml_n = 0;
+  // bandpass path (mraid_run_bandpass, mraid_arpls): time-aggregated
+  // spectra and baselines [interval][beam][chan] (FP64), solves per
+  // spectrum, and the ArPLS arrays when they do not fit in shared memory
+  double* bp_y = nullptr;
+  double* bp_z = nullptr;
+  size_t bp_elems = 0;
+  int32_t* bp_iters = nullptr;
+  size_t bp_sys = 0;
+  double* ar_work = nullptr;
+  size_t ar_work_elems = 0;
 };
 
 namespace mraid {
@@ -161,6 +174,19 @@ cudaError_t launch_refine(mraid_plan_s* pl, const float* d_q1, const uint8_t* d_
 // cells into d_info when those are given
 cudaError_t launch_flag(mraid_plan_s* pl, const float* d_stat, uint8_t* d_flags,
                         int64_t n_cells = -1, mraid_flag_info* d_info = nullptr);
+// bandpass.cu: ArPLS baselines of n_sys spectra of n points ([sys][n]
+// FP64; d_zf an optional float copy, d_iters solves per spectrum or -1);
+// d_work holds arpls_work_doubles(n, n_sys) doubles when that is nonzero
+size_t arpls_work_doubles(int n, int n_sys);
+cudaError_t launch_arpls(const mraid_plan_s* pl, const double* d_y, int n_sys, int n, double lam,
+                         double ratio, int itermax, double* d_z, float* d_zf, int32_t* d_iters,
+                         double* d_work);
+// time-aggregated spectra [interval][beam][chan] from the Gram sums
+cudaError_t launch_bandpass_input(const mraid_plan_s* pl, const int64_t* d_sums, bool interleaved,
+                                  int interval, double* d_y);
+// per cell C_ab = cov_ab / n^2 + (mu_a - z_a)(mu_b - z_b), packed, all cells
+cudaError_t launch_ccm_bandpass(const mraid_plan_s* pl, const int64_t* d_sums, bool interleaved,
+                                int interval, const double* d_z, float* d_ccm);
 // multires.cu: d_dst[k] = sum_{j < m} d_src[k m + j] over the int64 Gram
 // sums of n_out_sub sub-intervals (n_chan cells each)
 cudaError_t launch_gram_aggregate(const mraid_plan_s* pl, const int64_t* d_src, int64_t* d_dst,
