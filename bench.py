@@ -49,6 +49,8 @@ def parse_args():
                     help="shrink the block to this many sub-integrations (profiling runs)")
     ap.add_argument("--f32-subs", type=int, default=20,
                     help="sub-integrations of the float32-input variant (0: skip)")
+    ap.add_argument("--bandpass-steps", type=int, default=3,
+                    help="timed runs of the bandpass-centred path (0: skip)")
     ap.add_argument("--multires-steps", type=int, default=3,
                     help="timed calls of the seven-timescale pass (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3,
@@ -419,6 +421,74 @@ def bench_multires(m, torch, d, cfg, stream, steps, peaks):
             "aggregate_roofline": agg, "levels": levels}
 
 
+def bench_bandpass(m, torch, d, h, cfg, stream, steps):
+    """The bandpass-centred path (Section 3.1 ArPLS bandpass, C about it) on
+    the block with the default fit parameters (1 s intervals): time per
+    step, kernel breakdown, ArPLS solves, and a sampled check against the
+    oracle (baselines of three spectra, the statistic of a few cells)."""
+    import numpy as np
+    import oracle
+    N, C, S, K = cfg.n_beam, cfg.n_chan, cfg.n_samp_sub, cfg.n_sub
+    bp = m.mraid_default_bandpass_params()
+    n_int = (K + bp.interval - 1) // bp.interval
+    with torch.cuda.stream(stream):
+        plan = m.Plan(N, C, S, K, stream=stream)
+        band = torch.empty(n_int, N, C, dtype=torch.float32, device="cuda")
+        st = torch.empty(K * C, dtype=torch.float32, device="cuda")
+        fl = torch.empty(K * C, dtype=torch.uint8, device="cuda")
+    info = m.FlagInfo()
+    m.mraid_run_bandpass(plan.handle, d, bp, band, None, None, st, fl, info)
+    m.mraid_sync(plan.handle)
+    m.mraid_profile_reset(plan.handle)
+    m.mraid_profile_enable(plan.handle, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        m.mraid_run_bandpass(plan.handle, d, bp, band, None, None, st, fl, info)
+    e1.record(stream)
+    m.mraid_sync(plan.handle)
+    m.mraid_profile_enable(plan.handle, False)
+    prof = m.mraid_profile_read(plan.handle)
+    ms = e0.elapsed_time(e1) / steps
+    kt = {k: tot / steps for k, (n, tot) in prof.items() if n > 0}
+    # sampled oracle check on the host copy of the block
+    data = h.numpy().reshape(N, cfg.n_time, C)
+    bnd = band.cpu().numpy()
+    stg = st.cpu().numpy()
+    rng = np.random.default_rng(5)
+    z_err = 0.0
+    zo_cache = {}
+    for (I, a) in ((0, 0), (n_int - 1, N - 1), (n_int // 2, N // 2)):
+        s0 = I * bp.interval
+        ns = min(bp.interval, K - s0)
+        y = oracle.bandpass_input(data, S, s0, ns, a)
+        zo, _ = oracle.arpls(y, bp.lam, bp.ratio, bp.itermax)
+        zo_cache[(I, a)] = zo
+        z_err = max(z_err, float(np.abs(bnd[I, a] - zo).max() / np.abs(zo).max()))
+    s_err = 0.0
+    for _ in range(8):
+        k, c = int(rng.integers(0, K)), int(rng.integers(0, C))
+        I = k // bp.interval
+        zc = np.array([bnd[I, a, c] for a in range(N)], dtype=np.float64)
+        Cm = oracle.cell_ccm_bandpass(data, S, k, c, zc)
+        so = oracle.stat(oracle.jacobi(Cm)[0])
+        s_err = max(s_err, abs(float(stg[k * C + c]) - so) / so)
+    plan.close()
+    return {"workload": f"{N} beams x {C} channels x {K} x {S} samples (uint8), "
+                        f"fit intervals of {bp.interval} sub-integrations ({n_int} x {N} spectra)",
+            "params": {"lam": bp.lam, "ratio": bp.ratio, "itermax": bp.itermax,
+                       "interval": bp.interval},
+            "ms_per_step": ms, "cells_per_s": K * C / (ms / 1e3),
+            "kernels_ms_per_step": kt,
+            "masked_fraction": info.n_flagged / (K * C), "mask_iterations": info.iterations,
+            "sampled_parity": {"bandpass_rel_err_max": z_err,
+                               "stat_rel_err_max": s_err,
+                               "note": "3 spectra against the oracle's ArPLS of the oracle's "
+                                       "time-aggregated spectrum; 8 cells' statistic against "
+                                       "the oracle's CCM about the GPU bandpass"}}
+
+
 def bench_batched(m, torch, stream, steps):
     """Four receivers of 5 s each (13/19/36/72 beams) in one graph-captured
     pass, against the plain form (one mraid_run per block, one after the
@@ -752,6 +822,9 @@ def run_mraid(args):
         refine = {"ms": r0.elapsed_time(r1) / 5,
                   "beam_bits_set": int(sum(bin(int(x) & 0xffffffff).count("1")
                                            for x in bits.view(-1).cpu().tolist()))}
+    bandpass = None
+    if world == 1 and args.bandpass_steps > 0 and rank == 0:
+        bandpass = bench_bandpass(m, torch, d, h, cfg, stream, args.bandpass_steps)
     multires = None
     if world == 1 and args.multires_steps > 0:
         multires = bench_multires(m, torch, d, cfg, stream, args.multires_steps, peaks)
@@ -797,6 +870,7 @@ def run_mraid(args):
             "refine": refine,
             "precision_f32": precision,
             "multires": multires,
+            "bandpass": bandpass,
             "batched": batched,
             "served": served,
         }

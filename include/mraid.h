@@ -234,7 +234,7 @@ void mraid_default_bandpass_params(mraid_bandpass_params* bp);
  * 1 / (1 + exp(2 (d_i - (2 s - m)) / s)); stop when the weights moved by
  * less than ratio, when no d_i is negative or s is 0, or after itermax
  * solves (bp->interval is not used here).
- *   d_y:     float64 [n_sys][n], device, n >= 3.
+ *   d_y:     float64 [n_sys][n], device, 3 <= n <= 2^20.
  *   d_z:     float64 [n_sys][n], device: the last solve.
  *   d_iters: int32 [n_sys] or NULL: solves made, -1 if a pivot of the
  *            system was not positive (z is then not valid). */
@@ -247,7 +247,7 @@ mraid_status mraid_arpls(mraid_plan_t plan, const double* d_y, int32_t n_sys, in
  * baseline z; per cell C_ab = (1/N_s) sum_t (x_a - z_a)(x_b - z_b), the
  * beams' power with the bandpass subtracted "uniformly across all time
  * samples" (Section 3.1) and no further centring or normalisation; then
- * Eq. 2 and the masking as in mraid_run. 8-bit samples.
+ * Eq. 2 and the masking as in mraid_run. 8-bit samples, 3 to 2^20 channels.
  *   d_bandpass: float32 [ceil(n_sub / interval)][N][n_chan] or NULL: z.
  *   d_evals, d_q1: as in mraid_run (may be NULL); d_stat, d_flags required.
  *   info: as in mraid_run (n_degenerate is 0: nothing is normalised). */

@@ -28,9 +28,9 @@
 namespace mraid {
 namespace {
 
-constexpr int kArThreads = 256;
+constexpr int kArThreads = 512;
 constexpr int kArWarps = kArThreads / 32;
-constexpr int kArArrays = 6;  // y, z, w, L[i][i-1], L[i][i-2], 1 / D_i
+constexpr int kCrArrays = 13;  // per block row: A (3), C (4), saved left coupling (4), F (2)
 
 // Sum over the block in a fixed order; every thread gets the total.
 __device__ double block_sum(double v, double* red) {
@@ -41,7 +41,7 @@ __device__ double block_sum(double v, double* red) {
   if (lane == 0) red[warp] = v;
   __syncthreads();
   double t = 0.0;
-#pragma unroll
+#pragma unroll 8
   for (int i = 0; i < kArWarps; ++i) t += red[i];
   return t;
 }
@@ -55,87 +55,168 @@ __device__ __forceinline__ double dtd1(int i, int n) {  // (i, i + 1)
   return (i >= 1 && i - 1 <= n - 3 ? -2.0 : 0.0) + (i <= n - 3 ? -2.0 : 0.0);
 }
 
+struct M2 {  // [[a, b], [c, d]]
+  double a, b, c, d;
+};
+__device__ __forceinline__ M2 mm(const M2& x, const M2& y) {
+  return {fma(x.a, y.a, x.b * y.c), fma(x.a, y.b, x.b * y.d), fma(x.c, y.a, x.d * y.c),
+          fma(x.c, y.b, x.d * y.d)};
+}
+__device__ __forceinline__ M2 tr(const M2& x) { return {x.a, x.c, x.b, x.d}; }
+
+struct CrArrays {  // m block rows each
+  double *aa, *ab, *ad;            // A_i = [[aa, ab], [ab, ad]]; the inverse once eliminated
+  double *c00, *c01, *c10, *c11;   // C_i: coupling of row i to the next active row
+  double *l00, *l01, *l10, *l11;   // left coupling of a row, saved when it is eliminated
+  double *f0, *f1;                 // right side, then the solution
+  __device__ CrArrays(double* p, int m)
+      : aa(p), ab(p + m), ad(p + 2 * m), c00(p + 3 * m), c01(p + 4 * m), c10(p + 5 * m),
+        c11(p + 6 * m), l00(p + 7 * m), l01(p + 8 * m), l10(p + 9 * m), l11(p + 10 * m),
+        f0(p + 11 * m), f1(p + 12 * m) {}
+  __device__ M2 C(int i) const { return {c00[i], c01[i], c10[i], c11[i]}; }
+  __device__ M2 A(int i) const { return {aa[i], ab[i], ab[i], ad[i]}; }
+};
+
+// (W + lam D^T D) z = W y by block cyclic reduction. Unknowns in pairs
+// X_i = (z_2i, z_2i+1) make the pentadiagonal matrix block tridiagonal with
+// 2 x 2 blocks (row i: C_{i-1}^T X_{i-1} + A_i X_i + C_i X_{i+1}); m block
+// rows, a power of two (rows past n are identity rows with no coupling).
+// Each level eliminates the odd rows of the active set (stride s) into the
+// even ones; then the single remaining row is solved and the eliminated
+// rows are recovered level by level. It is Gaussian elimination of the
+// symmetric positive definite matrix in an odd-even order, so it needs no
+// pivoting, and every level is parallel over its rows.
+__device__ void cr_solve(const CrArrays& r, int m, const double* w, const double* y, int n,
+                         double lam) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const int r0 = 2 * i, r1 = 2 * i + 1;
+    const bool v0 = r0 < n, v1 = r1 < n;
+    r.aa[i] = v0 ? w[r0] + lam * dtd0(r0, n) : 1.0;
+    r.ab[i] = v1 ? lam * dtd1(r0, n) : 0.0;
+    r.ad[i] = v1 ? w[r1] + lam * dtd0(r1, n) : 1.0;
+    r.c00[i] = r0 + 2 < n ? lam : 0.0;                 // (r0, r0 + 2)
+    r.c01[i] = 0.0;                                     // (r0, r0 + 3)
+    r.c10[i] = r1 + 1 < n ? lam * dtd1(r1, n) : 0.0;    // (r1, r1 + 1)
+    r.c11[i] = r1 + 2 < n ? lam : 0.0;                  // (r1, r1 + 2)
+    r.f0[i] = v0 ? w[r0] * y[r0] : 0.0;
+    r.f1[i] = v1 ? w[r1] * y[r1] : 0.0;
+  }
+  __syncthreads();
+  for (int s = 1; s < m; s *= 2) {
+    // rows leaving at this level: invert A_j, keep their left coupling
+    for (int j = s + 2 * s * threadIdx.x; j < m; j += 2 * s * blockDim.x) {
+      const double a = r.aa[j], b = r.ab[j], d = r.ad[j];
+      const double inv = 1.0 / fma(a, d, -b * b);
+      r.aa[j] = d * inv;
+      r.ab[j] = -b * inv;
+      r.ad[j] = a * inv;
+      const M2 L = tr(r.C(j - s));
+      r.l00[j] = L.a;
+      r.l01[j] = L.b;
+      r.l10[j] = L.c;
+      r.l11[j] = L.d;
+    }
+    __syncthreads();
+    // rows staying: take in both neighbours
+    for (int i = 2 * s * threadIdx.x; i < m; i += 2 * s * blockDim.x) {
+      M2 Ai = r.A(i);
+      double g0 = r.f0[i], g1 = r.f1[i];
+      if (i >= s) {
+        const int j = i - s;
+        const M2 Cj = r.C(j);
+        M2 al = mm(tr(Cj), r.A(j));
+        al = {-al.a, -al.b, -al.c, -al.d};
+        const M2 t = mm(al, Cj);
+        Ai = {Ai.a + t.a, Ai.b + t.b, Ai.c + t.c, Ai.d + t.d};
+        g0 = fma(al.a, r.f0[j], fma(al.b, r.f1[j], g0));
+        g1 = fma(al.c, r.f0[j], fma(al.d, r.f1[j], g1));
+      }
+      M2 Cn = {0.0, 0.0, 0.0, 0.0};
+      if (i + s < m) {
+        const int j = i + s;
+        const M2 Ci = r.C(i);
+        M2 ga = mm(Ci, r.A(j));
+        ga = {-ga.a, -ga.b, -ga.c, -ga.d};
+        const M2 t = mm(ga, tr(Ci));
+        Ai = {Ai.a + t.a, Ai.b + t.b, Ai.c + t.c, Ai.d + t.d};
+        g0 = fma(ga.a, r.f0[j], fma(ga.b, r.f1[j], g0));
+        g1 = fma(ga.c, r.f0[j], fma(ga.d, r.f1[j], g1));
+        Cn = mm(ga, r.C(j));
+      }
+      r.aa[i] = Ai.a;
+      r.ab[i] = 0.5 * (Ai.b + Ai.c);
+      r.ad[i] = Ai.d;
+      r.c00[i] = Cn.a;
+      r.c01[i] = Cn.b;
+      r.c10[i] = Cn.c;
+      r.c11[i] = Cn.d;
+      r.f0[i] = g0;
+      r.f1[i] = g1;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double a = r.aa[0], b = r.ab[0], d = r.ad[0];
+    const double inv = 1.0 / fma(a, d, -b * b);
+    const double g0 = r.f0[0], g1 = r.f1[0];
+    r.f0[0] = (d * g0 - b * g1) * inv;
+    r.f1[0] = (a * g1 - b * g0) * inv;
+  }
+  __syncthreads();
+  for (int s = m / 2; s >= 1; s /= 2) {
+    for (int j = s + 2 * s * threadIdx.x; j < m; j += 2 * s * blockDim.x) {
+      const double x0 = r.f0[j - s], x1 = r.f1[j - s];
+      double g0 = r.f0[j] - fma(r.l00[j], x0, r.l01[j] * x1);
+      double g1 = r.f1[j] - fma(r.l10[j], x0, r.l11[j] * x1);
+      if (j + s < m) {
+        const double y0 = r.f0[j + s], y1 = r.f1[j + s];
+        g0 -= fma(r.c00[j], y0, r.c01[j] * y1);
+        g1 -= fma(r.c10[j], y0, r.c11[j] * y1);
+      }
+      r.f0[j] = fma(r.aa[j], g0, r.ab[j] * g1);
+      r.f1[j] = fma(r.ab[j], g0, r.ad[j] * g1);
+    }
+    __syncthreads();
+  }
+}
+
+__host__ __device__ constexpr int cr_rows(int n) {  // block rows: a power of two >= n / 2
+  int m = 1;
+  while (2 * m < n) m *= 2;
+  return m;
+}
+
 struct ArplsArgs {
   const double* y;   // [sys][n]
   double* z;         // [sys][n]
   float* zf;         // [sys][n] float copy, or null
   int32_t* iters;    // [sys], or null
-  double* work;      // [sys][6][n] when the arrays do not fit in shared memory
-  int n, n_sys, itermax;
+  double* work;      // [sys][n] weights, then [sys][13 m] when not in shared memory
+  int n, n_sys, itermax, in_smem;
   double lam, ratio;
 };
 
-// One CTA per spectrum. Thread 0 factors and solves the pentadiagonal
-// system (a sequential recurrence) from shared memory; all threads share
-// the residual statistics and the reweighting.
-__global__ void __launch_bounds__(kArThreads) arpls_kernel(ArplsArgs g) {
+// One CTA per spectrum: the weighted solves by block cyclic reduction,
+// the residual statistics and the reweighting, all parallel over the CTA.
+__global__ void __launch_bounds__(kArThreads, 1) arpls_kernel(ArplsArgs g) {
   extern __shared__ double ar_sm[];
   __shared__ double red[kArWarps];
-  __shared__ int bad;
-  const int sys = blockIdx.x, n = g.n;
-  double* base = g.work ? g.work + (size_t)sys * kArArrays * n : ar_sm;
-  double* ys = base;
-  double* zs = ys + n;
-  double* w = zs + n;
-  double* l1 = w + n;   // L[i][i-1]; reused for the new weights
-  double* l2 = l1 + n;  // L[i][i-2]
-  double* idg = l2 + n;
+  const int sys = blockIdx.x, n = g.n, m = cr_rows(n);
+  double* w = g.work + (size_t)sys * n;
+  double* cr = g.in_smem ? ar_sm
+                         : g.work + (size_t)g.n_sys * n + (size_t)sys * kCrArrays * m;
+  const CrArrays r(cr, m);
   const double* y = g.y + (size_t)sys * n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    ys[i] = y[i];
-    w[i] = 1.0;
-  }
-  if (threadIdx.x == 0) bad = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] = 1.0;
   __syncthreads();
-  const double lam = g.lam;
   int solves = 0;
   while (solves < g.itermax) {
-    if (threadIdx.x == 0) {
-      // A = W + lam D^T D = L diag(D) L^T; forward substitution L u = W y
-      // along the factorisation (u kept in zs), then L^T z = u / D.
-      double dm1 = 1.0, dm2 = 1.0, l1m1 = 0.0, um1 = 0.0, um2 = 0.0;
-      for (int i = 0; i < n; ++i) {
-        const double a0 = w[i] + lam * dtd0(i, n);
-        double li2 = 0.0, li1 = 0.0;
-        if (i >= 2) li2 = lam / dm2;  // A[i][i-2] = lam
-        if (i >= 1) li1 = (lam * dtd1(i - 1, n) - li2 * dm2 * l1m1) / dm1;
-        double di = a0;
-        if (i >= 1) di -= li1 * li1 * dm1;
-        if (i >= 2) di -= li2 * li2 * dm2;
-        if (!(di > 0.0)) {
-          bad = 1;
-          break;
-        }
-        const double ui = w[i] * ys[i] - li1 * um1 - li2 * um2;
-        l1[i] = li1;
-        l2[i] = li2;
-        idg[i] = 1.0 / di;
-        zs[i] = ui;
-        dm2 = dm1;
-        dm1 = di;
-        l1m1 = li1;
-        um2 = um1;
-        um1 = ui;
-      }
-      if (!bad) {
-        double zp1 = 0.0, zp2 = 0.0;
-        for (int i = n - 1; i >= 0; --i) {
-          double zi = zs[i] * idg[i];
-          if (i + 1 < n) zi -= l1[i + 1] * zp1;
-          if (i + 2 < n) zi -= l2[i + 2] * zp2;
-          zs[i] = zi;
-          zp2 = zp1;
-          zp1 = zi;
-        }
-      }
-    }
-    __syncthreads();
-    if (bad) break;
+    cr_solve(r, m, w, y, n, g.lam);
     ++solves;
-    // mean and population deviation of the negative residuals
+    // z_i is f0 / f1 of block row i / 2
     double sn = 0.0, cn = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const double d = ys[i] - zs[i];
+      const double d = y[i] - ((i & 1) ? r.f1[i >> 1] : r.f0[i >> 1]);
       if (d < 0.0) {
         sn += d;
         cn += 1.0;
@@ -144,37 +225,39 @@ __global__ void __launch_bounds__(kArThreads) arpls_kernel(ArplsArgs g) {
     sn = block_sum(sn, red);
     cn = block_sum(cn, red);
     if (cn == 0.0) break;
-    const double m = sn / cn;
+    const double mneg = sn / cn;
     double s2 = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const double d = ys[i] - zs[i];
-      if (d < 0.0) s2 += (d - m) * (d - m);
+      const double d = y[i] - ((i & 1) ? r.f1[i >> 1] : r.f0[i >> 1]);
+      if (d < 0.0) s2 += (d - mneg) * (d - mneg);
     }
-    const double s = sqrt(block_sum(s2, red) / cn);
-    if (!(s > 0.0)) break;
-    // new weights (into l1) and how far they moved
-    const double thr = 2.0 * s - m;
+    const double sd = sqrt(block_sum(s2, red) / cn);
+    if (!(sd > 0.0)) break;
+    const double thr = 2.0 * sd - mneg;
     double dw2 = 0.0, w2 = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const double d = ys[i] - zs[i];
-      const double wt = 1.0 / (1.0 + exp(2.0 * (d - thr) / s));
+      const double d = y[i] - ((i & 1) ? r.f1[i >> 1] : r.f0[i >> 1]);
+      const double wt = 1.0 / (1.0 + exp(2.0 * (d - thr) / sd));
       dw2 += (w[i] - wt) * (w[i] - wt);
       w2 += w[i] * w[i];
-      l1[i] = wt;
     }
     dw2 = block_sum(dw2, red);
     w2 = block_sum(w2, red);
     if (sqrt(dw2) / sqrt(w2) < g.ratio) break;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] = l1[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double d = y[i] - ((i & 1) ? r.f1[i >> 1] : r.f0[i >> 1]);
+      w[i] = 1.0 / (1.0 + exp(2.0 * (d - thr) / sd));
+    }
     __syncthreads();
   }
   __syncthreads();
   double* z = g.z + (size_t)sys * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    z[i] = zs[i];
-    if (g.zf) g.zf[(size_t)sys * n + i] = (float)zs[i];
+    const double zi = (i & 1) ? r.f1[i >> 1] : r.f0[i >> 1];
+    z[i] = zi;
+    if (g.zf) g.zf[(size_t)sys * n + i] = (float)zi;
   }
-  if (threadIdx.x == 0 && g.iters) g.iters[sys] = bad ? -1 : solves;
+  if (threadIdx.x == 0 && g.iters) g.iters[sys] = solves;
 }
 
 // y[(I * N + a) * n_chan + j]: mean of beam a, channel j over interval I,
@@ -255,31 +338,33 @@ __global__ void ccm_bandpass_kernel(const int64_t* __restrict__ sums, int interl
 }  // namespace
 
 size_t arpls_smem_bytes(int n) {
-  const size_t b = (size_t)kArArrays * n * sizeof(double);
-  return b <= 200 * 1024 ? b : 0;  // 0: the arrays live in global memory
+  const size_t b = (size_t)kCrArrays * cr_rows(n) * sizeof(double);
+  return b <= 214 * 1024 ? b : 0;  // 0: the arrays live in global memory
 }
 
 size_t arpls_work_doubles(int n, int n_sys) {
-  return arpls_smem_bytes(n) ? 0 : (size_t)kArArrays * n * n_sys;
+  // the weights always; the reduction arrays when they are not in shared memory
+  return (size_t)n * n_sys + (arpls_smem_bytes(n) ? 0 : (size_t)kCrArrays * cr_rows(n) * n_sys);
 }
 
 cudaError_t launch_arpls(const mraid_plan_s* pl, const double* d_y, int n_sys, int n, double lam,
                          double ratio, int itermax, double* d_z, float* d_zf, int32_t* d_iters,
                          double* d_work) {
   if (n_sys <= 0) return cudaSuccess;
+  if (!d_work) return cudaErrorInvalidValue;
   ArplsArgs g;
   g.y = d_y;
   g.z = d_z;
   g.zf = d_zf;
   g.iters = d_iters;
+  g.work = d_work;
   g.n = n;
   g.n_sys = n_sys;
   g.itermax = itermax;
   g.lam = lam;
   g.ratio = ratio;
   const size_t smem = arpls_smem_bytes(n);
-  g.work = smem ? nullptr : d_work;
-  if (!smem && !d_work) return cudaErrorInvalidValue;
+  g.in_smem = smem ? 1 : 0;
   cudaError_t e = cudaFuncSetAttribute(arpls_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

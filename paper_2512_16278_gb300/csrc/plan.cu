@@ -568,8 +568,8 @@ mraid_status mraid_arpls(mraid_plan_t pl, const double* d_y, int32_t n_sys, int3
   if (st != MRAID_OK) return st;
   st = check_bandpass_params(bp);
   if (st != MRAID_OK) return st;
-  if (!d_y || !d_z || n < 3 || n_sys < 0) {
-    set_error("mraid_arpls: d_y and d_z are required, n >= 3, n_sys >= 0");
+  if (!d_y || !d_z || n < 3 || n > (1 << 20) || n_sys < 0) {
+    set_error("mraid_arpls: d_y and d_z are required, 3 <= n <= 2^20, n_sys >= 0");
     return MRAID_ERR_INVALID_ARG;
   }
   st = ensure_arpls_work(pl, n, n_sys);
@@ -592,8 +592,8 @@ mraid_status mraid_run_bandpass(mraid_plan_t pl, const void* d_data,
     set_error("mraid_run_bandpass: d_data, d_stat and d_flags are required");
     return MRAID_ERR_INVALID_ARG;
   }
-  if (pl->p.bit_depth != 8 || pl->p.n_chan < 3) {
-    set_error("mraid_run_bandpass: 8-bit samples and at least 3 channels");
+  if (pl->p.bit_depth != 8 || pl->p.n_chan < 3 || pl->p.n_chan > (1 << 20)) {
+    set_error("mraid_run_bandpass: 8-bit samples and 3 to 2^20 channels");
     return MRAID_ERR_UNSUPPORTED;
   }
   const int interval = bp->interval;
