@@ -191,7 +191,8 @@ struct ArplsArgs {
   double* z;         // [sys][n]
   float* zf;         // [sys][n] float copy, or null
   int32_t* iters;    // [sys], or null
-  double* work;      // [sys][n] weights, then [sys][13 m] when not in shared memory
+  double* work;      // [sys][2][n] weights and new weights, then [sys][13 m] when the
+                     // reduction arrays are not in shared memory
   int n, n_sys, itermax, in_smem;
   double lam, ratio;
 };
@@ -202,9 +203,10 @@ __global__ void __launch_bounds__(kArThreads, 1) arpls_kernel(ArplsArgs g) {
   extern __shared__ double ar_sm[];
   __shared__ double red[kArWarps];
   const int sys = blockIdx.x, n = g.n, m = cr_rows(n);
-  double* w = g.work + (size_t)sys * n;
+  double* w = g.work + (size_t)sys * 2 * n;
+  double* wt = w + n;
   double* cr = g.in_smem ? ar_sm
-                         : g.work + (size_t)g.n_sys * n + (size_t)sys * kCrArrays * m;
+                         : g.work + (size_t)g.n_sys * 2 * n + (size_t)sys * kCrArrays * m;
   const CrArrays r(cr, m);
   const double* y = g.y + (size_t)sys * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] = 1.0;
@@ -237,17 +239,15 @@ __global__ void __launch_bounds__(kArThreads, 1) arpls_kernel(ArplsArgs g) {
     double dw2 = 0.0, w2 = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const double d = y[i] - ((i & 1) ? r.f1[i >> 1] : r.f0[i >> 1]);
-      const double wt = 1.0 / (1.0 + exp(2.0 * (d - thr) / sd));
-      dw2 += (w[i] - wt) * (w[i] - wt);
+      const double wn = 1.0 / (1.0 + exp(2.0 * (d - thr) / sd));
+      dw2 += (w[i] - wn) * (w[i] - wn);
       w2 += w[i] * w[i];
+      wt[i] = wn;
     }
     dw2 = block_sum(dw2, red);
     w2 = block_sum(w2, red);
     if (sqrt(dw2) / sqrt(w2) < g.ratio) break;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const double d = y[i] - ((i & 1) ? r.f1[i >> 1] : r.f0[i >> 1]);
-      w[i] = 1.0 / (1.0 + exp(2.0 * (d - thr) / sd));
-    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] = wt[i];
     __syncthreads();
   }
   __syncthreads();
@@ -313,12 +313,16 @@ __global__ void ccm_bandpass_kernel(const int64_t* __restrict__ sums, int interl
   const int64_t n = S[psum - 1];
   const int k = (int)(cell / n_chan), j = (int)(cell % n_chan);
   const int I = k / interval;
+  // FP32 throughout (this GPU's FP64 rate is low): S_a < 2^24 is exact
+  // in float, and the offsets d_a are O(1), so rounding the mean and the
+  // baseline to float costs ~1e-5 absolute in d_a, ~1e-7 of C
+  const float inv_n = 1.f / (float)n;
   for (int a = lane; a < n_beam; a += 32) {
     const int64_t sa = S[a * N1 - a * (a - 1) / 2 + (n_beam - a)];
-    dv[a] = (float)((double)sa / (double)n - z[((int64_t)I * n_beam + a) * n_chan + j]);
+    dv[a] = fmaf((float)sa, inv_n, -(float)z[((int64_t)I * n_beam + a) * n_chan + j]);
   }
   __syncwarp();
-  const float inv_n2 = (float)(1.0 / ((double)n * (double)n));
+  const float inv_n2 = inv_n * inv_n;
   float* dst = ccm + cell * np;
   int a = 0, rowlen = n_beam, row_start = 0;
   for (int e = lane; e < np; e += 32) {
@@ -344,7 +348,8 @@ size_t arpls_smem_bytes(int n) {
 
 size_t arpls_work_doubles(int n, int n_sys) {
   // the weights always; the reduction arrays when they are not in shared memory
-  return (size_t)n * n_sys + (arpls_smem_bytes(n) ? 0 : (size_t)kCrArrays * cr_rows(n) * n_sys);
+  return (size_t)2 * n * n_sys +
+         (arpls_smem_bytes(n) ? 0 : (size_t)kCrArrays * cr_rows(n) * n_sys);
 }
 
 cudaError_t launch_arpls(const mraid_plan_s* pl, const double* d_y, int n_sys, int n, double lam,
