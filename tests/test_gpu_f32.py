@@ -68,6 +68,7 @@ def test_f32_block_matches_oracle(offset, gram):
     (16, 16, 96, 4),     # first count with the extra-slot MMA
     (23, 32, 128, 3),    # largest count on the tensor cores
     (19, 40, 64, 3),     # 40 channels: not a multiple of 16, CUDA cores
+    (13, 32, 48, 4),     # 48 samples: not a multiple of 32, CUDA cores
     (24, 16, 64, 2),     # beyond 23 beams: CUDA cores
 ])
 def test_f32_shapes_match_oracle(n_beam, n_chan, n_s, n_sub):

@@ -76,3 +76,82 @@ def test_fast_block_sampled_parity_and_mask_properties(fast_block):
         assert F[k].mean() > 0.99 and F[k + 1].mean() > 0.99
     spikes = [(k, c) for (_, c, k, _) in ev["spike"]]
     assert np.mean([F[k, c] for (k, c) in spikes]) < 0.05
+
+
+def check_mask(stat, flags, info, k_sigma=3.0):
+    """The reported fit is the fit of the unmasked cells and every unmasked
+    cell is at or below the final threshold."""
+    assert info["converged"] == 1 and info["timed_out"] == 0
+    un = stat[~flags].astype(np.float64)
+    assert un.size == info["n_used"]
+    assert abs(un.mean() - info["mu"]) <= 1e-9 * abs(info["mu"])
+    assert abs(un.std() - info["sigma"]) <= 1e-6 * info["sigma"]
+    assert np.all(un <= info["thresh"])
+    assert abs(info["thresh"] - (info["mu"] + k_sigma * info["sigma"])) <= 1e-12
+    assert flags.sum() == info["n_flagged"]
+
+
+def test_fast_block_seven_timescales(fast_block):
+    """Table 1's seven sub-interval lengths (0.05 s to 10 s) in one
+    mraid_multires call on the full block: sampled cells of every level
+    against the oracle run at that level's sub-integration length, and the
+    masking properties per level."""
+    import torch
+    m = lib()
+    cfg, h = fast_block
+    d = h.to("cuda", non_blocking=False)
+    factors = [1, 4, 10, 20, 40, 100, 200]
+    with m.Plan(cfg.n_beam, cfg.n_chan, cfg.n_samp_sub, cfg.n_sub) as plan:
+        levels = plan.multires(d, factors)
+    del d
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(77)
+    for lv in levels:
+        f = lv["factor"]
+        n_f = cfg.n_sub // f
+        stat = lv["stat"].cpu().numpy()
+        flags = lv["flags"].cpu().numpy().astype(bool)
+        assert stat.shape == (n_f * cfg.n_chan,)
+        check_mask(stat, flags, lv["info"])
+        idx = np.unique(rng.integers(0, n_f * cfg.n_chan, size=24 if f <= 20 else 8))
+        subs, chans = (idx // cfg.n_chan).astype(np.int32), (idx % cfg.n_chan).astype(np.int32)
+        o = oracle.cells(None, f * cfg.n_samp_sub, subs, chans, n_threads=synth.default_threads(),
+                         data_ptr=h.data_ptr(), shape=(cfg.n_beam, cfg.n_time, cfg.n_chan))
+        s_err = np.abs(stat[idx] - o["stat"]) / o["stat"]
+        assert s_err.max() <= STAT_TOL, (f, s_err.max())
+
+
+def test_fast_block_bandpass_path(fast_block):
+    """The bandpass-centred path on the full block with 1 s fit intervals:
+    the baselines of two intervals (all 19 beams) against the oracle's ArPLS
+    of the oracle's time-aggregated spectra, the statistic of sampled cells
+    in those intervals from the oracle's CCM about the oracle's baselines,
+    and the masking properties."""
+    import torch
+    m = lib()
+    cfg, h = fast_block
+    d = h.to("cuda", non_blocking=False)
+    with m.Plan(cfg.n_beam, cfg.n_chan, cfg.n_samp_sub, cfg.n_sub) as plan:
+        out = plan.run_bandpass(d, evals=False)
+    del d
+    torch.cuda.empty_cache()
+    bp = m.mraid_default_bandpass_params()
+    band = out["bandpass"].cpu().numpy()
+    stat = out["stat"].cpu().numpy()
+    flags = out["flags"].cpu().numpy().astype(bool)
+    check_mask(stat, flags, out["info"])
+    data = h.numpy().reshape(cfg.n_beam, cfg.n_time, cfg.n_chan)
+    rng = np.random.default_rng(78)
+    for I in (0, 7):
+        s0 = I * bp.interval
+        z = np.empty((cfg.n_beam, cfg.n_chan))
+        for a in range(cfg.n_beam):
+            y = oracle.bandpass_input(data, cfg.n_samp_sub, s0, bp.interval, a)
+            z[a], _ = oracle.arpls(y, bp.lam, bp.ratio, bp.itermax)
+        np.testing.assert_allclose(band[I], z, rtol=2e-7)
+        for _ in range(6):
+            k = s0 + int(rng.integers(0, bp.interval))
+            c = int(rng.integers(0, cfg.n_chan))
+            C = oracle.cell_ccm_bandpass(data, cfg.n_samp_sub, k, c, z[:, c])
+            so = oracle.stat(oracle.jacobi(C)[0])
+            assert abs(stat[k * cfg.n_chan + c] - so) <= STAT_TOL * so, (I, k, c)

@@ -15,7 +15,7 @@ from gpu_util import STAT_TOL, compare_flags, lib
 
 pytestmark = pytest.mark.gpu
 
-N, C, S, K = 19, 64, 128, 48
+N, C, S, K = 19, 64, 128, 48   # tensor-core Gram: sums interleaved by 8 channels
 # unsorted; 5 leaves 3 sub-integrations out; 16 and 24 are formed from 8,
 # 48 from 24, 6 from 3 (or 2): every source rule is exercised
 FACTORS = [8, 1, 3, 5, 2, 48, 16, 24, 6]
@@ -108,3 +108,28 @@ def test_multires_rejects_bad_arguments(block):
         with pytest.raises(m.MraidError) as ei:
             m.mraid_multires(plan.handle, x, [2], [st], [fl])
         assert ei.value.status == code["MRAID_ERR_UNSUPPORTED"]
+
+
+def test_levels_on_the_cuda_core_gram():
+    """40 channels (not a multiple of 16) and 36 beams: the CUDA-core Gram
+    writes the sums cell by cell; every level still equals mraid_run at
+    its longer sub-integration, bit for bit."""
+    import torch
+    m = lib()
+    for (nb, nc, ns, nk) in ((13, 40, 64, 12), (36, 16, 64, 8)):
+        cfg = synth.SMALL.replace(n_beam=nb, n_chan=nc, n_samp_sub=ns, n_sub=nk, n_burst=1)
+        data = synth.generate(cfg)
+        d = torch.from_numpy(data).cuda()
+        factors = [1, 2, 3, nk] if nk % 3 == 0 else [1, 2, 4, nk]
+        with m.Plan(nb, nc, ns, nk) as plan:
+            m.mraid_profile_enable(plan.handle)
+            levels = plan.multires(d, factors)
+            ran = m.mraid_profile_read(plan.handle)
+        assert "gram_tc" not in ran and "gram_u8" in ran, ran
+        for lv in levels:
+            f = lv["factor"]
+            n_f = nk // f
+            with m.Plan(nb, nc, f * ns, n_f, beam_stride=nk * ns * nc) as p2:
+                out = p2.run(d, evals=False, q1=False)
+            np.testing.assert_array_equal(lv["stat"].cpu().numpy(), out["stat"].cpu().numpy())
+            np.testing.assert_array_equal(lv["flags"].cpu().numpy(), out["flags"].cpu().numpy())
