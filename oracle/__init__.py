@@ -66,6 +66,9 @@ def _load():
         lib.orc_cells_u8.argtypes = [_P, i32, i64, i32, i32, i64, _P, _P, i32, _P, _P, _P, _P]
         lib.orc_flag.argtypes = [_P, i64, i32, _P, dbl, i32, _P, ctypes.POINTER(FlagInfo)]
         lib.orc_beam_flags.argtypes = [_P, _P, i64, i32, _P, i32, dbl, _P, _P]
+        lib.orc_cell_gram_pol2_u8.argtypes = [_P, i32, i64, i32, i32, i32, i32, _P]
+        lib.orc_cells_pol2_u8.argtypes = [_P, i32, i64, i32, i32, i64, _P, _P, i32, _P, _P, _P,
+                                          _P]
         lib.orc_whittaker.argtypes = [_P, _P, i32, dbl, _P]
         lib.orc_arpls.argtypes = [_P, i32, dbl, dbl, i32, _P]
         lib.orc_bandpass_input_u8.argtypes = [_P, i32, i64, i32, i32, i32, i32, i32, _P]
@@ -76,7 +79,7 @@ def _load():
                   "orc_corr_from_cov", "orc_jacobi", "orc_cell_u8", "orc_block_u8",
                   "orc_cells_u8", "orc_flag", "orc_beam_flags", "orc_whittaker", "orc_arpls",
                   "orc_bandpass_input_u8", "orc_cell_ccm_bandpass_u8",
-                  "orc_block_bandpass_u8"):
+                  "orc_block_bandpass_u8", "orc_cell_gram_pol2_u8", "orc_cells_pol2_u8"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -288,3 +291,36 @@ def block_bandpass(data: np.ndarray, n_samp_sub: int, interval: int, lam: float,
                                          interval, lam, ratio, itermax, n_threads, _ptr(z),
                                          _ptr(it), _ptr(ev), _ptr(st)), "block_bandpass")
     return {"z": z, "iters": it, "evals": ev, "stat": st}
+
+
+# ---------------------------------------------------------- two polarisations
+# Section 2 (two polarisations recorded): the total power of beam a is the
+# sum of its two polarisations, blocks a and N + a of a 2N-block array.
+
+def cell_gram_pol2(data: np.ndarray, n_samp_sub: int, sub: int, chan: int) -> np.ndarray:
+    """Exact augmented Gram (N+1)x(N+1) of the total power; data has 2N blocks."""
+    n_blocks, bstride, n_chan = _block_view(data)
+    if n_blocks % 2:
+        raise ValueError("two-polarisation data has an even number of blocks")
+    N = n_blocks // 2
+    G = np.zeros((N + 1, N + 1), dtype=np.int64)
+    _check(_load().orc_cell_gram_pol2_u8(_ptr(data), N, bstride, n_chan, n_samp_sub, sub, chan,
+                                         _ptr(G)), "gram_pol2")
+    return G
+
+
+def cells_pol2(data: np.ndarray, n_samp_sub: int, subs, chans, n_threads: int = 1) -> dict:
+    """Selected cells of a two-polarisation block (G, evals, q1, stat)."""
+    n_blocks, bstride, n_chan = _block_view(data)
+    N = n_blocks // 2
+    subs = np.ascontiguousarray(subs, dtype=np.int32)
+    chans = np.ascontiguousarray(chans, dtype=np.int32)
+    n = subs.shape[0]
+    G = np.zeros((n, N + 1, N + 1), dtype=np.int64)
+    ev = np.zeros((n, N))
+    q1 = np.zeros((n, N))
+    st = np.zeros(n)
+    _check(_load().orc_cells_pol2_u8(_ptr(data), N, bstride, n_chan, n_samp_sub, n, _ptr(subs),
+                                     _ptr(chans), n_threads, _ptr(G), _ptr(ev), _ptr(q1),
+                                     _ptr(st)), "cells_pol2")
+    return {"G": G, "evals": ev, "q1": q1, "stat": st}

@@ -33,6 +33,29 @@ int orc_cell_gram_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
   return 0;
 }
 
+int orc_cell_gram_pol2_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
+                          int32_t n_chan, int32_t n_samp_sub, int32_t sub, int32_t chan,
+                          int64_t* G) {
+  if (!data || !G || n_beam < 1 || n_chan < 1 || n_samp_sub < 1 || sub < 0 ||
+      chan < 0 || chan >= n_chan)
+    return -1;
+  const int32_t N = n_beam, M = n_beam + 1;
+  const int64_t t0 = (int64_t)sub * n_samp_sub;
+  for (int32_t a = 0; a < M; ++a)
+    for (int32_t b = 0; b < M; ++b) {
+      int64_t s = 0;
+      for (int32_t t = 0; t < n_samp_sub; ++t) {
+        const int64_t o = (t0 + t) * n_chan + chan;
+        /* total power: polarisation 0 (block a) plus polarisation 1 (block N + a) */
+        int64_t xa = (a < N) ? (int64_t)data[a * beam_stride + o] + data[(N + a) * beam_stride + o] : 1;
+        int64_t xb = (b < N) ? (int64_t)data[b * beam_stride + o] + data[(N + b) * beam_stride + o] : 1;
+        s += xa * xb;
+      }
+      G[a * M + b] = s;
+    }
+  return 0;
+}
+
 int orc_cell_cov_f32(const float* data, int32_t n_beam, int64_t beam_stride,
                      int32_t n_chan, int32_t n_samp_sub, int32_t sub,
                      int32_t chan, double* cov) {
@@ -245,6 +268,31 @@ int orc_cell_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
   return rc;
 }
 
+/* the path of orc_cell_u8 on the total power of two polarisations */
+static int cell_pol2_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
+                        int32_t n_chan, int32_t n_samp_sub, int32_t sub, int32_t chan,
+                        int64_t* G, double* evals, double* q1, double* stat) {
+  const int32_t N = n_beam, M = n_beam + 1;
+  int64_t* g = (int64_t*)malloc(sizeof(int64_t) * (size_t)M * (size_t)M);
+  double* rr = (double*)malloc(sizeof(double) * (size_t)N * (size_t)N);
+  double* ev = (double*)malloc(sizeof(double) * (size_t)N);
+  int rc = -1;
+  if (g && rr && ev &&
+      orc_cell_gram_pol2_u8(data, n_beam, beam_stride, n_chan, n_samp_sub, sub, chan, g) == 0) {
+    int deg = orc_corr_from_gram(g, N, rr);
+    if (deg >= 0 && orc_jacobi(rr, N, ev, q1, NULL) == 0) {
+      if (G) memcpy(G, g, sizeof(int64_t) * (size_t)M * (size_t)M);
+      if (evals) memcpy(evals, ev, sizeof(double) * (size_t)N);
+      if (stat) *stat = orc_stat(ev, N);
+      rc = deg;
+    }
+  }
+  free(g);
+  free(rr);
+  free(ev);
+  return rc;
+}
+
 typedef struct {
   const uint8_t* data;
   int32_t n_beam, n_chan, n_samp_sub;
@@ -255,6 +303,7 @@ typedef struct {
   int64_t* G;
   double *evals, *q1, *stat;
   int rc;
+  int pol2;  /* 1: total power of two polarisations */
 } cells_job;
 
 static void* cells_worker(void* arg) {
@@ -264,11 +313,14 @@ static void* cells_worker(void* arg) {
   for (int64_t i = j->i0; i < j->i1; ++i) {
     int32_t sub = j->subs ? j->subs[i] : (int32_t)(i / j->n_chan);
     int32_t chan = j->chans ? j->chans[i] : (int32_t)(i % j->n_chan);
-    if (orc_cell_u8(j->data, N, j->beam_stride, j->n_chan, j->n_samp_sub, sub,
-                    chan, j->G ? j->G + i * M * M : NULL, NULL,
-                    j->evals ? j->evals + i * N : NULL, j->q1 ? j->q1 + i * N : NULL,
-                    &j->stat[i]) < 0)
-      j->rc = -1;
+    int64_t* Gi = j->G ? j->G + i * M * M : NULL;
+    double* evi = j->evals ? j->evals + i * N : NULL;
+    double* q1i = j->q1 ? j->q1 + i * N : NULL;
+    const int rc = j->pol2 ? cell_pol2_u8(j->data, N, j->beam_stride, j->n_chan, j->n_samp_sub,
+                                          sub, chan, Gi, evi, q1i, &j->stat[i])
+                           : orc_cell_u8(j->data, N, j->beam_stride, j->n_chan, j->n_samp_sub,
+                                         sub, chan, Gi, NULL, evi, q1i, &j->stat[i]);
+    if (rc < 0) j->rc = -1;
   }
   return NULL;
 }
@@ -276,7 +328,7 @@ static void* cells_worker(void* arg) {
 static int run_cells(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
                      int32_t n_chan, int32_t n_samp_sub, int64_t n_list,
                      const int32_t* subs, const int32_t* chans, int32_t n_threads,
-                     int64_t* G, double* evals, double* q1, double* stat) {
+                     int64_t* G, double* evals, double* q1, double* stat, int pol2) {
   if (!data || !stat || n_list < 0) return -1;
   if (n_threads < 1) n_threads = 1;
   if (n_threads > 512) n_threads = 512;
@@ -287,7 +339,7 @@ static int run_cells(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
   for (int32_t i = 0; i < n_threads; ++i) {
     cells_job j = {data, n_beam, n_chan, n_samp_sub, beam_stride, subs, chans,
                    n_list * i / n_threads, n_list * (i + 1) / n_threads, G,
-                   evals, q1, stat, -1};
+                   evals, q1, stat, -1, pol2};
     jobs[i] = j;
     created[i] = i > 0 && pthread_create(&th[i], NULL, cells_worker, &jobs[i]) == 0;
   }
@@ -306,7 +358,7 @@ int orc_block_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
                  int32_t n_threads, double* evals, double* q1, double* stat) {
   return run_cells(data, n_beam, beam_stride, n_chan, n_samp_sub,
                    (int64_t)n_sub * n_chan, NULL, NULL, n_threads, NULL, evals,
-                   q1, stat);
+                   q1, stat, 0);
 }
 
 int orc_cells_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
@@ -315,7 +367,16 @@ int orc_cells_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
                  int64_t* G, double* evals, double* q1, double* stat) {
   if (!subs || !chans) return -1;
   return run_cells(data, n_beam, beam_stride, n_chan, n_samp_sub, n_list, subs,
-                   chans, n_threads, G, evals, q1, stat);
+                   chans, n_threads, G, evals, q1, stat, 0);
+}
+
+int orc_cells_pol2_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
+                      int32_t n_chan, int32_t n_samp_sub, int64_t n_list,
+                      const int32_t* subs, const int32_t* chans, int32_t n_threads,
+                      int64_t* G, double* evals, double* q1, double* stat) {
+  if (!subs || !chans) return -1;
+  return run_cells(data, n_beam, beam_stride, n_chan, n_samp_sub, n_list, subs,
+                   chans, n_threads, G, evals, q1, stat, 1);
 }
 
 /* ------------------------------------------------- iterative RFI masking */

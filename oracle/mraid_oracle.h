@@ -42,6 +42,14 @@ int orc_cell_gram_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
                      int32_t n_chan, int32_t n_samp_sub, int32_t sub,
                      int32_t chan, int64_t* G);
 
+/* Two polarisations (Section 2: the FAST data record two; the total power
+ * B of Eq. 1 is their sum): polarisation p of beam a is block p*N + a of
+ * data (blocks beam_stride apart), x_a(t) = p0_a(t) + p1_a(t) in 0..510.
+ * Exact augmented Gram of x, as orc_cell_gram_u8. */
+int orc_cell_gram_pol2_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
+                          int32_t n_chan, int32_t n_samp_sub, int32_t sub, int32_t chan,
+                          int64_t* G);
+
 /* Same for float32 samples: G is not exact here, so the oracle forms the
  * mean-subtracted covariance directly in FP64 (cov[a][b], N x N). */
 int orc_cell_cov_f32(const float* data, int32_t n_beam, int64_t beam_stride,
@@ -87,6 +95,12 @@ int orc_cells_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
                  int32_t n_chan, int32_t n_samp_sub, int64_t n_list,
                  const int32_t* subs, const int32_t* chans, int32_t n_threads,
                  int64_t* G, double* evals, double* q1, double* stat);
+
+/* orc_cells_u8 on the total power of a two-polarisation block. */
+int orc_cells_pol2_u8(const uint8_t* data, int32_t n_beam, int64_t beam_stride,
+                      int32_t n_chan, int32_t n_samp_sub, int64_t n_list,
+                      const int32_t* subs, const int32_t* chans, int32_t n_threads,
+                      int64_t* G, double* evals, double* q1, double* stat);
 
 /* Iterative clipping of the statistic (cells [sub][chan], n_cells a multiple
  * of n_chan). keep: n_chan bytes, nonzero = preserved channel (never flagged,
