@@ -212,6 +212,19 @@ mraid_status mraid_multires(mraid_plan_t plan, const void* d_data, int32_t n_lev
                             const int32_t* factors, float* const* d_stats,
                             uint8_t* const* d_flags, mraid_flag_info* infos);
 
+/* Two recorded polarisations (Section 2): d_data holds 2N blocks of 8-bit
+ * samples, polarisation-major: block p*N + a is polarisation p of beam a,
+ * [time][chan], blocks the plan's beam_stride apart. Eq. 1 is taken of the
+ * total power x_a = p0_a + p1_a (0..510). d_sums, d_corr and the rest as
+ * in mraid_ccm and mraid_run; the sums are those of x, exact. The plan
+ * describes the N beams (n_beam <= 64, bit_depth 8). A work buffer of
+ * (2N+1)(2N+2)/2 int64 per cell is allocated on first use. */
+mraid_status mraid_ccm_pol2(mraid_plan_t plan, const void* d_data, int64_t* d_sums,
+                            float* d_corr);
+mraid_status mraid_run_pol2(mraid_plan_t plan, const void* d_data, float* d_evals,
+                            float* d_q1, float* d_stat, uint8_t* d_flags,
+                            mraid_flag_info* info);
+
 /* Bandpass normalisation (Section 3.1) with ArPLS, the asymmetrically
  * reweighted penalized least squares of Baek, Park, Ahn and Ahn (2015) that
  * the paper uses; Section 4.5 names its three parameters without values. */

@@ -28,7 +28,7 @@ __all__ = [
     "mraid_serve_poll", "mraid_serve_drain", "mraid_serve_close", "StreamDesc", "BlockResult",
     "Server", "mraid_autotune", "mraid_set_variant", "mraid_set_eig_variant", "tune",
     "mraid_refine", "mraid_multires", "BandpassParams", "mraid_default_bandpass_params",
-    "mraid_arpls", "mraid_run_bandpass", "STATUS",
+    "mraid_arpls", "mraid_run_bandpass", "mraid_ccm_pol2", "mraid_run_pol2", "STATUS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -170,6 +170,8 @@ def load():
         "mraid_multires": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(vp),
                                           ctypes.POINTER(vp), ctypes.POINTER(FlagInfo)]),
         "mraid_default_bandpass_params": (None, [ctypes.POINTER(BandpassParams)]),
+        "mraid_ccm_pol2": (ctypes.c_int, [vp, vp, vp, vp]),
+        "mraid_run_pol2": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, ctypes.POINTER(FlagInfo)]),
         "mraid_arpls": (ctypes.c_int, [vp, vp, i32, i32, ctypes.POINTER(BandpassParams), vp, vp]),
         "mraid_run_bandpass": (ctypes.c_int, [vp, vp, ctypes.POINTER(BandpassParams), vp, vp, vp,
                                               vp, vp, ctypes.POINTER(FlagInfo)]),
@@ -287,6 +289,18 @@ def mraid_run_bandpass(plan: int, d_data, bp: BandpassParams, d_bandpass, d_eval
                                      _ptr(d_evals), _ptr(d_q1), _ptr(d_stat), _ptr(d_flags),
                                      ctypes.byref(info) if info is not None else None),
            "mraid_run_bandpass")
+
+
+def mraid_ccm_pol2(plan: int, d_data, d_sums=None, d_corr=None):
+    _check(load().mraid_ccm_pol2(plan, _ptr(d_data), _ptr(d_sums), _ptr(d_corr)),
+           "mraid_ccm_pol2")
+
+
+def mraid_run_pol2(plan: int, d_data, d_evals, d_q1, d_stat, d_flags,
+                   info: Optional[FlagInfo] = None):
+    _check(load().mraid_run_pol2(plan, _ptr(d_data), _ptr(d_evals), _ptr(d_q1), _ptr(d_stat),
+                                 _ptr(d_flags), ctypes.byref(info) if info is not None else None),
+           "mraid_run_pol2")
 
 
 def mraid_sync(plan: int):
@@ -570,6 +584,31 @@ class Plan:
         mraid_sync(self.handle)
         return [{"factor": f, "stat": stats[i], "flags": flags[i], "info": infos[i].as_dict()}
                 for i, f in enumerate(factors)]
+
+    def ccm_pol2(self, data, sums: bool = True, corr: bool = True):
+        """Gram sums / correlation of the total power of a two-polarisation
+        block (2N blocks, polarisation-major)."""
+        N = self.n_beam
+        s = self._empty(self.n_cells, (N + 1) * (N + 2) // 2, dtype=self.torch.int64) if sums else None
+        c = self._empty(self.n_cells, N * (N + 1) // 2, dtype=self.torch.float32) if corr else None
+        mraid_ccm_pol2(self.handle, data, s, c)
+        return s, c
+
+    def run_pol2(self, data, evals: bool = True, q1: bool = True):
+        """Whole path on the total power of a two-polarisation block."""
+        N = self.n_beam
+        t = self.torch
+        out = {
+            "evals": self._empty(self.n_cells, N, dtype=t.float32) if evals else None,
+            "q1": self._empty(self.n_cells, N, dtype=t.float32) if q1 else None,
+            "stat": self._empty(self.n_cells, dtype=t.float32),
+            "flags": self._empty(self.n_cells, dtype=t.uint8),
+        }
+        info = FlagInfo()
+        mraid_run_pol2(self.handle, data, out["evals"], out["q1"], out["stat"], out["flags"], info)
+        mraid_sync(self.handle)
+        out["info"] = info.as_dict()
+        return out
 
     def arpls(self, y, **kw):
         """(z, solves) of the ArPLS baselines of the rows of y (float64

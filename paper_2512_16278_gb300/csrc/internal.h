@@ -25,7 +25,7 @@ struct FlagDev {  // device image of mraid_flag_info
 
 enum KernelId {
   K_GRAM = 0, K_CORR, K_EIG, K_FLAG, K_GRAM_TC, K_GRAM_F32, K_GRAM_TC_F32, K_AGG,
-  K_BP_INPUT, K_ARPLS, K_CCM_BP, K_COUNT
+  K_BP_INPUT, K_ARPLS, K_CCM_BP, K_POL2_FOLD, K_COUNT
 };
 const char* kernel_name(int id);
 
@@ -108,6 +108,9 @@ struct mraid_plan_s {
   size_t bp_sys = 0;
   double* ar_work = nullptr;
   size_t ar_work_elems = 0;
+  // two polarisations: Gram sums of the 2N stacked blocks [cell][P2]
+  int64_t* pol_sums = nullptr;
+  size_t pol_cells = 0;
 };
 
 namespace mraid {
@@ -187,6 +190,9 @@ cudaError_t launch_bandpass_input(const mraid_plan_s* pl, const int64_t* d_sums,
 // per cell C_ab = cov_ab / n^2 + (mu_a - z_a)(mu_b - z_b), packed, all cells
 cudaError_t launch_ccm_bandpass(const mraid_plan_s* pl, const int64_t* d_sums, bool interleaved,
                                 int interval, const double* d_z, float* d_ccm);
+// pol2.cu: total-power sums [cell][P] from the stacked 2N-block sums
+cudaError_t launch_pol2_fold(const mraid_plan_s* pl, const int64_t* d_stacked, int64_t n_cells,
+                             int64_t* d_sums);
 // multires.cu: d_dst[k] = sum_{j < m} d_src[k m + j] over the int64 Gram
 // sums of n_out_sub sub-intervals (n_chan cells each)
 cudaError_t launch_gram_aggregate(const mraid_plan_s* pl, const int64_t* d_src, int64_t* d_dst,

@@ -40,6 +40,7 @@ const char* kernel_name(int id) {
     case K_BP_INPUT: return "bandpass_input";
     case K_ARPLS: return "arpls";
     case K_CCM_BP: return "ccm_bandpass";
+    case K_POL2_FOLD: return "pol2_fold";
   }
   return "unknown";
 }
@@ -553,6 +554,125 @@ mraid_status ensure_arpls_work(mraid_plan_s* pl, int n, int n_sys) {
 }
 }  // namespace
 }  // namespace mraid
+
+namespace mraid {
+namespace {
+// Exact Gram sums [cell][P] of the total power of a two-polarisation block
+// into d_sums: the 8-bit Gram of the 2N stacked blocks (a plan view with 2N
+// beams on the plan's stream and counters), then the fold.
+mraid_status pol2_sums(mraid_plan_s* pl, const void* d_data, int64_t* d_sums) {
+  const int N = pl->p.n_beam;
+  if (pl->p.bit_depth != 8 || 2 * N > kMaxBeam) {
+    set_error("two polarisations: 8-bit samples and at most %d beams", kMaxBeam / 2);
+    return MRAID_ERR_UNSUPPORTED;
+  }
+  const int P2 = (2 * N + 1) * (2 * N + 2) / 2;
+  if ((size_t)pl->n_cells > pl->pol_cells) {
+    cudaFree(pl->pol_sums);
+    pl->pol_sums = nullptr;
+    pl->pol_cells = 0;
+    cudaError_t e = cudaMalloc(&pl->pol_sums, (size_t)pl->n_cells * P2 * sizeof(int64_t));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_fail(e, "two-polarisation workspace allocation");
+    }
+    pl->pol_cells = (size_t)pl->n_cells;
+  }
+  mraid_plan_s v;
+  v.p = pl->p;
+  v.p.n_beam = 2 * N;
+  v.p.keep = nullptr;
+  v.device = pl->device;
+  v.sm_count = pl->sm_count;
+  v.stream = pl->stream;
+  v.n_cells = pl->n_cells;
+  v.beam_stride = pl->beam_stride;
+  v.np = 2 * N * (2 * N + 1) / 2;
+  v.psum = P2;
+  v.d_degenerate = pl->d_degenerate;
+  v.d_error = pl->d_error;
+  v.force_dp4a = pl->force_dp4a;
+  v.tc_variant = tc_default_variant(2 * N);
+  cudaError_t e = cudaSuccess;
+  if (!v.force_dp4a && gram_tc_supported(&v, d_data)) {
+    e = MRAID_PROF(pl, K_GRAM_TC,
+                   launch_gram_tc(&v, static_cast<const uint8_t*>(d_data), 0, v.p.n_sub,
+                                  pl->pol_sums, nullptr));
+  } else {
+    for (int s = 0; s < v.p.n_sub && e == cudaSuccess; s += kMaxSubPerLaunch) {
+      const int ns = (v.p.n_sub - s) < kMaxSubPerLaunch ? (v.p.n_sub - s) : kMaxSubPerLaunch;
+      e = MRAID_PROF(pl, K_GRAM,
+                     launch_gram_u8(&v, static_cast<const uint8_t*>(d_data), s, ns,
+                                    pl->pol_sums + (int64_t)s * v.p.n_chan * P2));
+    }
+  }
+  if (e == cudaSuccess)
+    e = MRAID_PROF(pl, K_POL2_FOLD, launch_pol2_fold(pl, pl->pol_sums, pl->n_cells, d_sums));
+  return e == cudaSuccess ? MRAID_OK : cuda_fail(e, "two-polarisation Gram");
+}
+}  // namespace
+}  // namespace mraid
+
+mraid_status mraid_ccm_pol2(mraid_plan_t pl, const void* d_data, int64_t* d_sums,
+                            float* d_corr) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  if (!d_data || (!d_sums && !d_corr)) {
+    set_error("mraid_ccm_pol2: d_data and one of d_sums, d_corr are required");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  int64_t* sums = d_sums;
+  if (!sums) {
+    st = ensure_workspace(pl, (size_t)pl->n_cells);
+    if (st != MRAID_OK) return st;
+    sums = pl->ws.sums;
+  }
+  st = pol2_sums(pl, d_data, sums);
+  if (st != MRAID_OK) return st;
+  if (d_corr) {
+    cudaError_t e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
+    if (e == cudaSuccess)
+      e = MRAID_PROF(pl, K_CORR, launch_corr_from_sums(pl, sums, pl->n_cells, d_corr));
+    if (e != cudaSuccess) return cuda_fail(e, "corr launch");
+  }
+  return MRAID_OK;
+}
+
+mraid_status mraid_run_pol2(mraid_plan_t pl, const void* d_data, float* d_evals, float* d_q1,
+                            float* d_stat, uint8_t* d_flags, mraid_flag_info* info) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  if (!d_data || !d_stat || !d_flags) {
+    set_error("mraid_run_pol2: d_data, d_stat and d_flags are required");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  st = ensure_workspace(pl, (size_t)pl->n_cells);
+  if (st != MRAID_OK) return st;
+  if (d_q1) {
+    st = evals_for_q1(pl, (size_t)pl->n_cells, &d_evals);
+    if (st != MRAID_OK) return st;
+  }
+  cudaError_t e = cudaMemsetAsync(pl->d_sweeps, 0, 2 * sizeof(unsigned long long), pl->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "memset");
+  st = pol2_sums(pl, d_data, pl->ws.sums);
+  if (st != MRAID_OK) return st;
+  // zero-variance beams of the total power are counted by the correlation
+  e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
+  if (e == cudaSuccess)
+    e = MRAID_PROF(pl, K_CORR, launch_corr_from_sums(pl, pl->ws.sums, pl->n_cells, pl->ws.corr));
+  if (e != cudaSuccess) return cuda_fail(e, "corr launch");
+  e = MRAID_PROF(pl, K_EIG, launch_eig(pl, pl->ws.corr, pl->n_cells, d_evals, d_q1, d_stat));
+  if (e != cudaSuccess) return cuda_fail(e, "eig launch");
+  e = MRAID_PROF(pl, K_FLAG, launch_flag(pl, d_stat, d_flags));
+  if (e != cudaSuccess) return cuda_fail(e, "flag launch");
+  e = cudaMemcpyAsync(&pl->d_info->n_degenerate, pl->d_degenerate, sizeof(int64_t),
+                      cudaMemcpyDeviceToDevice, pl->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&pl->d_info->jacobi_sweeps, pl->d_sweeps, 2 * sizeof(int64_t),
+                        cudaMemcpyDeviceToDevice, pl->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "counter copy");
+  return enqueue_info_copy(pl, info);
+}
 
 void mraid_default_bandpass_params(mraid_bandpass_params* bp) {
   if (!bp) return;
@@ -1087,6 +1207,7 @@ void mraid_destroy(mraid_plan_t pl) {
   cudaFree(pl->ws.corr);
   cudaFree(pl->ws.evals);
   cudaFree(pl->ws.tri);
+  cudaFree(pl->pol_sums);
   cudaFree(pl->bp_y);
   cudaFree(pl->bp_z);
   cudaFree(pl->bp_iters);
