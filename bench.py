@@ -49,6 +49,8 @@ def parse_args():
                     help="shrink the block to this many sub-integrations (profiling runs)")
     ap.add_argument("--f32-subs", type=int, default=20,
                     help="sub-integrations of the float32-input variant (0: skip)")
+    ap.add_argument("--pol2-steps", type=int, default=3,
+                    help="timed runs of the two-polarisation path (0: skip)")
     ap.add_argument("--bandpass-steps", type=int, default=3,
                     help="timed runs of the bandpass-centred path (0: skip)")
     ap.add_argument("--multires-steps", type=int, default=3,
@@ -489,6 +491,64 @@ def bench_bandpass(m, torch, d, h, cfg, stream, steps):
                                        "the oracle's CCM about the GPU bandpass"}}
 
 
+def bench_pol2(m, torch, h, cfg, stream, steps):
+    """Two recorded polarisations: the block as polarisation 0 and a second
+    synthetic block (next seed, its own RFI) as polarisation 1, stacked in
+    device memory; mraid_run_pol2 per step, kernel breakdown, and sampled
+    cells against the oracle's total-power path."""
+    import numpy as np
+    import oracle
+    import synth
+    N, C, S, K = cfg.n_beam, cfg.n_chan, cfg.n_samp_sub, cfg.n_sub
+    nb = cfg.nbytes
+    h2 = torch.empty(2 * nb, dtype=torch.uint8, pin_memory=True)
+    h2[:nb].copy_(h)
+    synth.generate(cfg.replace(seed=cfg.seed + 1), out_ptr=h2.data_ptr() + nb)
+    d2 = h2.to("cuda")
+    cells = K * C
+    with torch.cuda.stream(stream):
+        plan = m.Plan(N, C, S, K, stream=stream)
+        ev = torch.empty(cells, N, dtype=torch.float32, device="cuda")
+        st = torch.empty(cells, dtype=torch.float32, device="cuda")
+        fl = torch.empty(cells, dtype=torch.uint8, device="cuda")
+    info = m.FlagInfo()
+    m.mraid_run_pol2(plan.handle, d2, ev, None, st, fl, info)
+    m.mraid_sync(plan.handle)
+    m.mraid_profile_reset(plan.handle)
+    m.mraid_profile_enable(plan.handle, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        m.mraid_run_pol2(plan.handle, d2, ev, None, st, fl, info)
+    e1.record(stream)
+    m.mraid_sync(plan.handle)
+    m.mraid_profile_enable(plan.handle, False)
+    prof = m.mraid_profile_read(plan.handle)
+    ms = e0.elapsed_time(e1) / steps
+    kt = {k: tot / steps for k, (n, tot) in prof.items() if n > 0}
+    rng = np.random.default_rng(9)
+    idx = np.unique(rng.integers(0, cells, size=48))
+    data = h2.numpy().reshape(2 * N, cfg.n_time, C)
+    o = oracle.cells_pol2(data, S, (idx // C).astype(np.int32), (idx % C).astype(np.int32),
+                          n_threads=synth.default_threads())
+    evh = ev.cpu().numpy()[idx]
+    e_err = float((np.abs(evh - o["evals"]).max(axis=1) / np.abs(o["evals"]).max(axis=1)).max())
+    s_err = float((np.abs(st.cpu().numpy()[idx] - o["stat"]) / o["stat"]).max())
+    plan.close()
+    del d2, h2
+    torch.cuda.empty_cache()
+    return {"workload": f"{N} beams x 2 polarisations x {C} channels x {K} x {S} samples "
+                        f"(uint8, {2 * nb / 1e9:.1f} GB)",
+            "ms_per_step": ms, "cells_per_s": cells / (ms / 1e3),
+            "input_gbs": 2 * nb / (ms / 1e3) / 1e9,
+            "kernels_ms_per_step": kt, "masked_fraction": info.n_flagged / cells,
+            "sampled_parity": {"cells": int(idx.size), "eig_err_rel_max": e_err,
+                               "stat_err_rel_max": s_err},
+            "path": "exact Gram of the 2N stacked polarisation blocks, folded into the total "
+                    "power's Gram (int64), then the correlation, eigensolver and mask"}
+
+
 def bench_batched(m, torch, stream, steps):
     """Four receivers of 5 s each (13/19/36/72 beams) in one graph-captured
     pass, against the plain form (one mraid_run per block, one after the
@@ -822,6 +882,9 @@ def run_mraid(args):
         refine = {"ms": r0.elapsed_time(r1) / 5,
                   "beam_bits_set": int(sum(bin(int(x) & 0xffffffff).count("1")
                                            for x in bits.view(-1).cpu().tolist()))}
+    pol2 = None
+    if world == 1 and args.pol2_steps > 0:
+        pol2 = bench_pol2(m, torch, h, cfg, stream, args.pol2_steps)
     bandpass = None
     if world == 1 and args.bandpass_steps > 0 and rank == 0:
         bandpass = bench_bandpass(m, torch, d, h, cfg, stream, args.bandpass_steps)
@@ -871,6 +934,7 @@ def run_mraid(args):
             "precision_f32": precision,
             "multires": multires,
             "bandpass": bandpass,
+            "pol2": pol2,
             "batched": batched,
             "served": served,
         }

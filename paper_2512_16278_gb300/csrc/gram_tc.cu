@@ -69,6 +69,8 @@ constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 struct TcArgs {
   int n_beam, n_chan, n_samp_sub, sub0, n_sub;
+  int n_pol;   // 2: blocks b and N + b are two polarisations of beam b, summed
+  int center;  // subtracted before f16: 128 (one polarisation), 255 (sum of two)
   int n_u8;  // u8 ring depth (stages), fixed at launch with the shared-memory size
   int R;    // slots per group: N + 1
   int R2;   // slots 16..N per group (0 if N + 1 <= 16)
@@ -238,22 +240,23 @@ template <class C>
 __host__ __device__ constexpr size_t f16_stage_bytes(int n_beam) {
   return (size_t)stage_slots(n_beam) * C::kSlotBytes;
 }
-// u8 ring depth for n_beam beams: as deep as the shared memory allows, so
-// TMA keeps streaming while the MMAs pause for an epilogue
+// u8 ring depth for n_beam beams (n_pol blocks each): as deep as the
+// shared memory allows, so TMA keeps streaming while the MMAs pause for an
+// epilogue
 template <class C>
-__host__ __device__ constexpr int u8_ring_depth(int n_beam) {
+__host__ __device__ constexpr int u8_ring_depth(int n_beam, int n_pol = 1) {
   return (int)((kSmemBudget - 1024 - (size_t)C::kNF * f16_stage_bytes<C>(n_beam) - sizeof(Smem)) /
-               ((size_t)n_beam * C::kT * kBoxCh)) < kMaxNU
+               ((size_t)n_pol * n_beam * C::kT * kBoxCh)) < kMaxNU
              ? (int)((kSmemBudget - 1024 - (size_t)C::kNF * f16_stage_bytes<C>(n_beam) -
                       sizeof(Smem)) /
-                     ((size_t)n_beam * C::kT * kBoxCh))
+                     ((size_t)n_pol * n_beam * C::kT * kBoxCh))
              : kMaxNU;
 }
 // dynamic shared memory for n_beam beams and a ring of n_u8 stages
 template <class C>
-__host__ __device__ constexpr size_t smem_bytes(int n_beam, int n_u8) {
+__host__ __device__ constexpr size_t smem_bytes(int n_beam, int n_u8, int n_pol = 1) {
   return 1024 /* alignment slack */ + (size_t)C::kNF * f16_stage_bytes<C>(n_beam) +
-         (size_t)n_u8 * n_beam * C::kT * kBoxCh + sizeof(Smem);
+         (size_t)n_u8 * n_pol * n_beam * C::kT * kBoxCh + sizeof(Smem);
 }
 
 template <int T_, int NF_, int U_>
@@ -268,7 +271,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
   const int kNU = g.n_u8;
   unsigned char* f16 = base;                                   // kNF stages
   unsigned char* u8 = f16 + (size_t)kNF * kF16StageBytes;      // kNU stages
-  const int u8_stage_bytes = g.n_beam * kT * kBoxCh;
+  const int u8_stage_bytes = g.n_pol * g.n_beam * kT * kBoxCh;
   Smem* s = reinterpret_cast<Smem*>(u8 + (size_t)kNU * u8_stage_bytes);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -382,6 +385,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
     const int ct = threadIdx.x - 4 * 32;
     const uint32_t magic = 0x64646464u;   // f16 bit pattern 0x64xx = 1024 + x
     const uint32_t bias = 0x64806480u;    // f16x2 (1152, 1152)
+    const uint32_t bias2 = 0x64ff64ffu;   // f16x2 (1279, 1279): two polarisations
     uint32_t cnt = 0;
     bool ok = true;
     for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
@@ -392,6 +396,30 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
         if (!ok) break;
         const uint4* src = reinterpret_cast<const uint4*>(u8 + (size_t)us * u8_stage_bytes);
         unsigned char* dst = f16 + (size_t)fs * kF16StageBytes;
+        if (g.n_pol == 2) {
+          // total power of two polarisations: x = p0 + p1 (0..510) in
+          // 16-bit lanes; f16 0x6400 | x = 1024 + x, minus 1279 gives
+          // x - 255 exactly (|x - 255| <= 255)
+          for (int r = ct; r < N * kT; r += kConvThreads) {
+            const uint4 wa = src[r], wb = src[r + N * kT];
+            const int b = r / kT, t = r % kT;
+            const uint32_t off = (t / 8) * 128 + (t % 8) * 16;
+            const uint32_t off0 = (uint32_t)b * kSlotBytes + off;
+            const uint32_t off1 = (uint32_t)slot_pos(1, b, g.R, g.R2) * kSlotBytes + off;
+            auto two = [&](uint32_t x, uint32_t y, uint32_t sel) {
+              const uint32_t v = (__byte_perm(x, 0u, sel) + __byte_perm(y, 0u, sel)) | 0x64006400u;
+              uint32_t o;
+              asm("sub.f16x2 %0, %1, %2;" : "=r"(o) : "r"(v), "r"(bias2));
+              return o;
+            };
+            const uint4 o0 = make_uint4(two(wa.x, wb.x, 0x4140), two(wa.x, wb.x, 0x4342),
+                                        two(wa.y, wb.y, 0x4140), two(wa.y, wb.y, 0x4342));
+            const uint4 o1 = make_uint4(two(wa.z, wb.z, 0x4140), two(wa.z, wb.z, 0x4342),
+                                        two(wa.w, wb.w, 0x4140), two(wa.w, wb.w, 0x4342));
+            *reinterpret_cast<uint4*>(dst + off0) = o0;
+            *reinterpret_cast<uint4*>(dst + off1) = o1;
+          }
+        } else {
 #pragma unroll C::kUnroll
         for (int r = ct; r < N * kT; r += kConvThreads) {
           const uint4 w = src[r];  // 16 channels of beam b at sample t
@@ -410,6 +438,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
           asm("sub.f16x2 %0, %1, %2;" : "=r"(o1.w) : "r"(__byte_perm(w.w, magic, 0x4342)), "r"(bias));
           *reinterpret_cast<uint4*>(dst + off0) = o0;
           *reinterpret_cast<uint4*>(dst + off1) = o1;
+        }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&s->u8_empty[us]);
@@ -549,9 +578,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
             if (b < a || b > N) continue;
             const int64_t gab = (int64_t)rv[jb];
             int64_t v;
+            const int64_t cc = g.center;
             if (a == N) v = n;                                  // (N, N): sample count
-            else if (b == N) v = gab + 128 * n;                 // S_a
-            else v = gab + 128 * (sa + (int64_t)s->s_sum[grp][c][b]) + 16384 * n;
+            else if (b == N) v = gab + cc * n;                  // S_a
+            else v = gab + cc * (sa + (int64_t)s->s_sum[grp][c][b]) + cc * cc * n;
             dst[(b - a) * step] = v;
           }
         }
@@ -976,10 +1006,31 @@ int tc_default_variant(int n_beam) {
 }
 
 
-bool gram_tc_supported(const mraid_plan_s* pl, const void* d_data) {
+// u8 ring depth of variant v for n_beam beams of n_pol blocks
+static int tc_u8_depth(int v, int n_beam, int n_pol) {
+  switch (v) {
+    case 1: return u8_ring_depth<TcCfg<32, 4, 1>>(n_beam, n_pol);
+    case 2: return u8_ring_depth<TcCfg<32, 2, 1>>(n_beam, n_pol);
+    case 3: return u8_ring_depth<TcCfg<64, 3, 1>>(n_beam, n_pol);
+    case 4: return u8_ring_depth<TcCfg<64, 2, 2>>(n_beam, n_pol);
+    case 5: return u8_ring_depth<TcCfg<64, 3, 2>>(n_beam, n_pol);
+    case 6: return u8_ring_depth<TcCfg<64, 4, 1>>(n_beam, n_pol);
+    case 7: return u8_ring_depth<TcCfg<64, 4, 2>>(n_beam, n_pol);
+    default: return u8_ring_depth<TcCfg<64, 2, 1>>(n_beam, n_pol);
+  }
+}
+
+// Two polarisations double the u8 stage; a variant whose ring would then be
+// shallower than two stages gives way to variant 0 (two f16 stages).
+static int tc_variant_for(const mraid_plan_s* pl, int n_pol) {
+  return n_pol == 2 && tc_u8_depth(pl->tc_variant, pl->p.n_beam, 2) < 2 ? 0 : pl->tc_variant;
+}
+
+bool gram_tc_supported(const mraid_plan_s* pl, const void* d_data, int n_pol) {
   const mraid_params& p = pl->p;
-  const int t = tc_variant_samples(pl->tc_variant);
+  const int t = tc_variant_samples(tc_variant_for(pl, n_pol));
   return p.bit_depth == 8 && p.n_beam >= 2 && p.n_beam + 1 <= kGroupSlots &&
+         (n_pol == 1 || (n_pol == 2 && tc_u8_depth(tc_variant_for(pl, 2), p.n_beam, 2) >= 2)) &&
          p.n_samp_sub % t == 0 && p.n_samp_sub <= 1024 && p.n_chan % kBoxCh == 0 &&
          pl->beam_stride % 16 == 0 && (reinterpret_cast<uintptr_t>(d_data) & 15) == 0 &&
          (int64_t)p.n_sub * p.n_samp_sub <= 2147483647ll /* TMA time coordinate */ &&
@@ -987,15 +1038,17 @@ bool gram_tc_supported(const mraid_plan_s* pl, const void* d_data) {
 }
 
 cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int sub0, int n_sub,
-                           int64_t* d_sums, float* d_corr, int64_t* d_sums8) {
+                           int64_t* d_sums, float* d_corr, int64_t* d_sums8, int n_pol) {
   const mraid_params& p = pl->p;
-  if (!gram_tc_supported(pl, d_data)) return cudaErrorNotSupported;
+  if (!gram_tc_supported(pl, d_data, n_pol)) return cudaErrorNotSupported;
+  const int variant = tc_variant_for(pl, n_pol);
   CUtensorMap map;
   const cuuint64_t n_time = (cuuint64_t)(sub0 + n_sub) * p.n_samp_sub;
-  cuuint64_t dims[3] = {(cuuint64_t)p.n_chan, n_time, (cuuint64_t)p.n_beam};
+  // one box holds every block of the stage: n_pol * N blocks, beam_stride apart
+  cuuint64_t dims[3] = {(cuuint64_t)p.n_chan, n_time, (cuuint64_t)n_pol * p.n_beam};
   cuuint64_t strides[2] = {(cuuint64_t)p.n_chan, (cuuint64_t)pl->beam_stride};
-  const int t = tc_variant_samples(pl->tc_variant);
-  cuuint32_t box[3] = {(cuuint32_t)kBoxCh, (cuuint32_t)t, (cuuint32_t)p.n_beam};
+  const int t = tc_variant_samples(variant);
+  cuuint32_t box[3] = {(cuuint32_t)kBoxCh, (cuuint32_t)t, (cuuint32_t)(n_pol * p.n_beam)};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t*>(d_data),
                            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -1008,6 +1061,8 @@ cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int su
   a.n_samp_sub = p.n_samp_sub;
   a.sub0 = sub0;
   a.n_sub = n_sub;
+  a.n_pol = n_pol;
+  a.center = n_pol == 2 ? 255 : 128;
   const int R = p.n_beam + 1;              // beams + the row of ones
   a.R = R;
   a.R2 = R > 16 ? R - 16 : 0;
@@ -1023,15 +1078,15 @@ cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int su
 #define MRAID_TC_LAUNCH(T, NF, U)                                                                 \
   do {                                                                                           \
     using C_ = TcCfg<T, NF, U>;                                                                     \
-    const int n_u8 = u8_ring_depth<C_>(p.n_beam);                                                \
+    const int n_u8 = u8_ring_depth<C_>(p.n_beam, n_pol);                                         \
     a.n_u8 = n_u8;                                                                               \
-    const size_t smem = smem_bytes<C_>(p.n_beam, n_u8);                                          \
+    const size_t smem = smem_bytes<C_>(p.n_beam, n_u8, n_pol);                                   \
     e = cudaFuncSetAttribute(gram_tc_kernel<T, NF, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              (int)smem);                                                         \
     if (e == cudaSuccess && grid > 0)                                                            \
       gram_tc_kernel<T, NF, U><<<grid, kThreads, smem, pl->stream>>>(map, a);                       \
   } while (0)
-  switch (pl->tc_variant) {
+  switch (variant) {
     case 1: MRAID_TC_LAUNCH(32, 4, 1); break;
     case 2: MRAID_TC_LAUNCH(32, 2, 1); break;
     case 3: MRAID_TC_LAUNCH(64, 3, 1); break;
@@ -1079,6 +1134,8 @@ cudaError_t launch_gram_tc_f32(const mraid_plan_s* pl, const float* d_data, int 
   a.R = R;
   a.R2 = R > 16 ? R - 16 : 0;
   a.rb = (R + 1) / 2 * 2;
+  a.n_pol = 1;
+  a.center = 0;
   a.sums = nullptr;
   a.sums8 = nullptr;
   a.corr = d_corr;

@@ -41,6 +41,7 @@ const char* kernel_name(int id) {
     case K_ARPLS: return "arpls";
     case K_CCM_BP: return "ccm_bandpass";
     case K_POL2_FOLD: return "pol2_fold";
+    case K_POL2_PIECES: return "pol2_pieces";
   }
   return "unknown";
 }
@@ -557,28 +558,64 @@ mraid_status ensure_arpls_work(mraid_plan_s* pl, int n, int n_sys) {
 
 namespace mraid {
 namespace {
-// Exact Gram sums [cell][P] of the total power of a two-polarisation block
-// into d_sums: the 8-bit Gram of the 2N stacked blocks (a plan view with 2N
-// beams on the plan's stream and counters), then the fold.
-mraid_status pol2_sums(mraid_plan_s* pl, const void* d_data, int64_t* d_sums) {
+// Exact Gram sums of the total power of a two-polarisation block into
+// d_sums. Tensor cores where they take the shape: the kernel adds the two
+// polarisations of every sample and writes the sums of 256-sample pieces
+// (a plan view with 256-sample sub-integrations), which are then added per
+// sub-integration; d_sums comes out interleaved by 8 channels unless
+// want_public. Otherwise: the 8-bit Gram of the 2N stacked blocks (a plan
+// view with 2N beams), folded into [cell][P]. *interleaved tells which.
+constexpr int kPol2Piece = 256;
+mraid_status pol2_sums(mraid_plan_s* pl, const void* d_data, int64_t* d_sums, bool want_public,
+                       bool* interleaved) {
   const int N = pl->p.n_beam;
   if (pl->p.bit_depth != 8 || 2 * N > kMaxBeam) {
     set_error("two polarisations: 8-bit samples and at most %d beams", kMaxBeam / 2);
     return MRAID_ERR_UNSUPPORTED;
   }
   const int P2 = (2 * N + 1) * (2 * N + 2) / 2;
-  if ((size_t)pl->n_cells > pl->pol_cells) {
+  const int m = pl->p.n_samp_sub / kPol2Piece;
+  mraid_plan_s w;  // pieces of 256 samples, N beams, two polarisations
+  w.p = pl->p;
+  w.p.keep = nullptr;
+  w.p.n_samp_sub = kPol2Piece;
+  w.p.n_sub = pl->p.n_sub * m;
+  w.device = pl->device;
+  w.sm_count = pl->sm_count;
+  w.stream = pl->stream;
+  w.n_cells = pl->n_cells * m;
+  w.beam_stride = pl->beam_stride;
+  w.np = pl->np;
+  w.psum = pl->psum;
+  w.d_degenerate = pl->d_degenerate;
+  w.d_error = pl->d_error;
+  w.tc_variant = pl->tc_variant;
+  const bool tc = !pl->force_dp4a && pl->p.n_samp_sub % kPol2Piece == 0 && m >= 1 &&
+                  gram_tc_supported(&w, d_data, 2);
+  const size_t need = tc ? (size_t)w.n_cells * pl->psum : (size_t)pl->n_cells * P2;
+  if (need > pl->pol_cells) {  // pol_cells counts int64 elements
     cudaFree(pl->pol_sums);
     pl->pol_sums = nullptr;
     pl->pol_cells = 0;
-    cudaError_t e = cudaMalloc(&pl->pol_sums, (size_t)pl->n_cells * P2 * sizeof(int64_t));
+    cudaError_t e = cudaMalloc(&pl->pol_sums, need * sizeof(int64_t));
     if (e != cudaSuccess) {
       cudaGetLastError();
       return cuda_fail(e, "two-polarisation workspace allocation");
     }
-    pl->pol_cells = (size_t)pl->n_cells;
+    pl->pol_cells = need;
   }
-  mraid_plan_s v;
+  cudaError_t e = cudaSuccess;
+  if (tc) {
+    *interleaved = !want_public;
+    e = MRAID_PROF(pl, K_GRAM_TC,
+                   launch_gram_tc(&w, static_cast<const uint8_t*>(d_data), 0, w.p.n_sub, nullptr,
+                                  nullptr, pl->pol_sums, 2));
+    if (e == cudaSuccess)
+      e = MRAID_PROF(pl, K_POL2_PIECES, launch_pol2_pieces(pl, pl->pol_sums, m, d_sums, want_public));
+    return e == cudaSuccess ? MRAID_OK : cuda_fail(e, "two-polarisation Gram");
+  }
+  *interleaved = false;
+  mraid_plan_s v;  // 2N stacked blocks
   v.p = pl->p;
   v.p.n_beam = 2 * N;
   v.p.keep = nullptr;
@@ -593,7 +630,6 @@ mraid_status pol2_sums(mraid_plan_s* pl, const void* d_data, int64_t* d_sums) {
   v.d_error = pl->d_error;
   v.force_dp4a = pl->force_dp4a;
   v.tc_variant = tc_default_variant(2 * N);
-  cudaError_t e = cudaSuccess;
   if (!v.force_dp4a && gram_tc_supported(&v, d_data)) {
     e = MRAID_PROF(pl, K_GRAM_TC,
                    launch_gram_tc(&v, static_cast<const uint8_t*>(d_data), 0, v.p.n_sub,
@@ -627,12 +663,13 @@ mraid_status mraid_ccm_pol2(mraid_plan_t pl, const void* d_data, int64_t* d_sums
     if (st != MRAID_OK) return st;
     sums = pl->ws.sums;
   }
-  st = pol2_sums(pl, d_data, sums);
+  bool inter = false;
+  st = pol2_sums(pl, d_data, sums, d_sums != nullptr, &inter);
   if (st != MRAID_OK) return st;
   if (d_corr) {
     cudaError_t e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
     if (e == cudaSuccess)
-      e = MRAID_PROF(pl, K_CORR, launch_corr_from_sums(pl, sums, pl->n_cells, d_corr));
+      e = MRAID_PROF(pl, K_CORR, launch_corr_from_sums(pl, sums, pl->n_cells, d_corr, inter));
     if (e != cudaSuccess) return cuda_fail(e, "corr launch");
   }
   return MRAID_OK;
@@ -654,12 +691,14 @@ mraid_status mraid_run_pol2(mraid_plan_t pl, const void* d_data, float* d_evals,
   }
   cudaError_t e = cudaMemsetAsync(pl->d_sweeps, 0, 2 * sizeof(unsigned long long), pl->stream);
   if (e != cudaSuccess) return cuda_fail(e, "memset");
-  st = pol2_sums(pl, d_data, pl->ws.sums);
+  bool inter = false;
+  st = pol2_sums(pl, d_data, pl->ws.sums, false, &inter);
   if (st != MRAID_OK) return st;
   // zero-variance beams of the total power are counted by the correlation
   e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
   if (e == cudaSuccess)
-    e = MRAID_PROF(pl, K_CORR, launch_corr_from_sums(pl, pl->ws.sums, pl->n_cells, pl->ws.corr));
+    e = MRAID_PROF(pl, K_CORR,
+                   launch_corr_from_sums(pl, pl->ws.sums, pl->n_cells, pl->ws.corr, inter));
   if (e != cudaSuccess) return cuda_fail(e, "corr launch");
   e = MRAID_PROF(pl, K_EIG, launch_eig(pl, pl->ws.corr, pl->n_cells, d_evals, d_q1, d_stat));
   if (e != cudaSuccess) return cuda_fail(e, "eig launch");

@@ -22,21 +22,28 @@ def two_pol_block(n_beam, n_chan, n_s, n_sub, seed, n_burst=1):
     return cfg, np.ascontiguousarray(np.concatenate([p0, p1], axis=0))
 
 
-@pytest.mark.parametrize("n_beam,n_chan,n_s,n_sub", [
-    (7, 48, 128, 6),     # 2N + 1 = 15 stacked slots: tensor-core Gram of the stacked blocks
-    (19, 40, 96, 5),     # 38 stacked blocks: CUDA-core Gram
+@pytest.mark.parametrize("n_beam,n_chan,n_s,n_sub,route", [
+    (19, 48, 512, 3, "pieces"),   # tensor cores add the polarisations, 2 pieces of 256
+    (23, 16, 256, 4, "pieces"),   # the most beams the tensor-core Gram takes
+    (7, 48, 128, 6, "stacked"),   # 128 samples: 2N + 1 = 15 stacked slots on tensor cores
+    (19, 40, 96, 5, "stacked"),   # 38 stacked blocks: CUDA-core Gram
 ])
-def test_pol2_sums_exact(n_beam, n_chan, n_s, n_sub):
+def test_pol2_sums_exact(n_beam, n_chan, n_s, n_sub, route):
     import torch
     m = lib()
     cfg, data = two_pol_block(n_beam, n_chan, n_s, n_sub, 31 + n_beam)
+    # extreme samples too: both polarisations 255 and 0 in places
+    data[:, :n_s // 4, 0] = 255
+    data[:, n_s // 4:n_s // 2, 1] = 0
     d = torch.from_numpy(data).cuda()
     with m.Plan(n_beam, n_chan, n_s, n_sub) as plan:
         m.mraid_profile_enable(plan.handle)
         sums, _ = plan.ccm_pol2(d, corr=False)
         plan.sync()
         ran = m.mraid_profile_read(plan.handle)
-    assert ("gram_tc" in ran) == (2 * n_beam + 1 <= 24), ran
+    assert ("pol2_pieces" in ran) == (route == "pieces"), ran
+    if route == "stacked":
+        assert ("gram_tc" in ran) == (2 * n_beam + 1 <= 24), ran
     G = unpack_sums(sums.cpu().numpy(), n_beam)
     for k in range(n_sub):
         for c in range(n_chan):
@@ -44,13 +51,14 @@ def test_pol2_sums_exact(n_beam, n_chan, n_s, n_sub):
                                           oracle.cell_gram_pol2(data, n_s, k, c))
 
 
-def test_pol2_run_matches_oracle():
+@pytest.mark.parametrize("S", [256, 128])   # tensor-core pieces; stacked CUDA-core Gram
+def test_pol2_run_matches_oracle(S):
     import torch
     m = lib()
     # no broadband bursts: in a block of 32 sub-integrations each burst
     # covers 2, and with the narrowband channels a fifth of the cells would
     # sit near s ~ 0.85, lifting mu + 3 sigma above 1 (nothing flagged)
-    N, C, S, K = 19, 64, 128, 32
+    N, C, K = 19, 64, 32
     cfg, data = two_pol_block(N, C, S, K, 101, n_burst=0)
     d = torch.from_numpy(data).cuda()
     with m.Plan(N, C, S, K) as plan:
@@ -70,12 +78,13 @@ def test_pol2_run_matches_oracle():
         assert F[:, c].mean() > 0.9, c
 
 
-def test_pol2_with_silent_second_polarisation_equals_single():
+@pytest.mark.parametrize("S", [256, 128])
+def test_pol2_with_silent_second_polarisation_equals_single(S):
     """Polarisation 1 all zero: the total power is polarisation 0, and the
     statistic and flags equal mraid_run's on polarisation 0 alone."""
     import torch
     m = lib()
-    N, C, S, K = 19, 64, 128, 16
+    N, C, K = 19, 64, 16
     cfg, data = two_pol_block(N, C, S, K, 7)
     data[N:] = 0
     d = torch.from_numpy(data).cuda()
