@@ -71,6 +71,7 @@ struct TcArgs {
   int n_beam, n_chan, n_samp_sub, sub0, n_sub;
   int n_pol;   // 2: blocks b and N + b are two polarisations of beam b, summed
   int center;  // subtracted before f16: 128 (one polarisation), 255 (sum of two)
+  int piece_stages;  // stages per TMEM accumulation; the epilogue adds the pieces
   int n_u8;  // u8 ring depth (stages), fixed at launch with the shared-memory size
   int R;    // slots per group: N + 1
   int R2;   // slots 16..N per group (0 if N + 1 <= 16)
@@ -259,7 +260,9 @@ __host__ __device__ constexpr size_t smem_bytes(int n_beam, int n_u8, int n_pol 
          (size_t)n_u8 * n_pol * n_beam * C::kT * kBoxCh + sizeof(Smem);
 }
 
-template <int T_, int NF_, int U_>
+// kPol 2: the two-polarisation mode (converter adds blocks b and N + b;
+// the epilogue adds the TMEM pieces of a sub-integration as integers)
+template <int T_, int NF_, int U_, int kPol>
 __global__ void __launch_bounds__(kThreads, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
   using C = TcCfg<T_, NF_, U_>;
@@ -348,15 +351,20 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
       // no-swizzle canonical layout: K-adjacent core matrices 128 B apart,
       // MN-adjacent (next slot) kSlotBytes apart
       const uint32_t lbo = 128, sbo = kSlotBytes;
-      uint32_t fcnt = 0, item_iter = 0;
+      uint32_t fcnt = 0, pcnt = 0;  // stages and accumulation pieces issued
       bool ok = true;
-      for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x, ++item_iter) {
+      for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
         for (int st = 0; st < stages && ok; ++st, ++fcnt) {
           const int fs = fcnt % kNF;
+          // stage within the TMEM accumulation piece (the whole item for one
+          // polarisation)
+          int ps = st;
+          if constexpr (kPol == 2) ps = st % g.piece_stages;
+          const int last = kPol == 2 ? g.piece_stages - 1 : stages - 1;
           ok = mbar_wait(&s->f16_full[fs], (fcnt / kNF) & 1, g.error);
           if (!ok) break;
-          if (st == 0 && item_iter > 0) {
-            ok = mbar_wait(&s->acc_empty, (item_iter - 1) & 1, g.error);
+          if (ps == 0 && pcnt > 0) {
+            ok = mbar_wait(&s->acc_empty, (pcnt - 1) & 1, g.error);
             if (!ok) break;
           }
           fence_after();
@@ -365,7 +373,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
 #pragma unroll
           for (int ks = 0; ks < kT / 16; ++ks) {
             const uint32_t a = stage_addr + ks * 256;  // 16 samples = two 128-byte core matrices
-            const uint32_t acc = (st > 0 || ks > 0) ? 1u : 0u;
+            const uint32_t acc = (ps > 0 || ks > 0) ? 1u : 0u;
             mma_f16(tmem, smem_desc(a, lbo, sbo), smem_desc(a, lbo, sbo), id1, acc);
             mma_f16(tmem + 192, smem_desc(a + pa1, lbo, sbo), smem_desc(a + pb1, lbo, sbo), id1,
                     acc);
@@ -374,7 +382,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
                       smem_desc(a + 16 * kSlotBytes, lbo, sbo), id2, acc);
           }
           mma_commit(&s->f16_empty[fs]);  // stage buffer free once these MMAs finish
-          if (st == stages - 1) mma_commit(&s->acc_full);
+          if (ps == last) {
+            mma_commit(&s->acc_full);
+            ++pcnt;
+          }
         }
       }
       mma_commit(&s->drain);
@@ -396,7 +407,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
         if (!ok) break;
         const uint4* src = reinterpret_cast<const uint4*>(u8 + (size_t)us * u8_stage_bytes);
         unsigned char* dst = f16 + (size_t)fs * kF16StageBytes;
-        if (g.n_pol == 2) {
+        if constexpr (kPol == 2) {
           // total power of two polarisations: x = p0 + p1 (0..510) in
           // 16-bit lanes; f16 0x6400 | x = 1024 + x, minus 1279 gives
           // x - 255 exactly (|x - 255| <= 255)
@@ -457,144 +468,202 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
     const int slot2 = 16 + (g2 == 1 ? p2 - g.R2 : p2);
     const int64_t n = g.n_samp_sub;
     const int R = g.R, R2 = g.R2;
-    uint32_t item_iter = 0;
+    uint32_t pcnt = 0;
     bool ok = true;
-    for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x, ++item_iter) {
-      ok = mbar_wait(&s->acc_full, item_iter & 1, g.error);
-      if (!ok) break;
-      fence_after();
-      float row[2][kGroupSlots];   // D1 row `slot` of each group, by column block
-      float row2[16];              // D2 row `slot2`, by column block
-#pragma unroll
-      for (int grp = 0; grp < 2; ++grp) {
-        // chunks of 32 columns (4 blocks x 8 channels), one load in flight
-#pragma unroll
-        for (int ch = 0; ch < kGroupSlots / 4; ++ch) {
-          if (ch * 4 < g.rb) {
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + grp * 192 + ch * 32, v);
-            tmem_wait_ld();
-            pick4(v, c, &row[grp][4 * ch]);
-          } else {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) row[grp][4 * ch + u] = 0.f;
+    for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
+      // the rest of the item from the rows D1 `slot` of each group and D2
+      // `slot2` (by column block): floats of exact integers (one
+      // polarisation) or int32 sums of the pieces (two)
+      auto finish = [&](auto& row, auto& row2) {
+        // G[a][N] (row sum) and G[a][a] from each row, picked with
+        // compile-time register indices and runtime block -> slot maps
+        using V = std::remove_reference_t<decltype(row[0][0])>;
+        V sumN[2], diag[2], sumN2 = 0, diag2 = 0;
+  #pragma unroll
+        for (int grp = 0; grp < 2; ++grp) {
+          sumN[grp] = diag[grp] = 0;
+  #pragma unroll
+          for (int jb = 0; jb < kGroupSlots; ++jb) {
+            const int b = d1_slot(grp, jb, R2);
+            if (jb < R && b == N) sumN[grp] = row[grp][jb];
+            if (jb < R && b == slot) diag[grp] = row[grp][jb];
           }
         }
-      }
-#pragma unroll
-      for (int ch = 0; ch < 4; ++ch) {
-        if (2 * R2 > 4 * ch) {
-          uint32_t v[32];
-          tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + 384 + ch * 32, v);
-          tmem_wait_ld();
-          pick4(v, c, &row2[4 * ch]);
-        } else {
-#pragma unroll
-          for (int u = 0; u < 4; ++u) row2[4 * ch + u] = 0.f;
+        // D2 columns: blocks 0..R2-1 are group 0 slots 16.., then group 1's
+        const int jb2 = g2 == 1 ? R2 : 0;
+  #pragma unroll
+        for (int jb = 0; jb < 16; ++jb) {
+          if (jb - jb2 == N - 16) sumN2 = row2[jb];
+          if (jb - jb2 == slot2 - 16) diag2 = row2[jb];
         }
-      }
-      fence_before();
-      mbar_arrive(&s->acc_empty);  // accumulators may be overwritten now
-      // G[a][N] (row sum) and G[a][a] from each row, picked with
-      // compile-time register indices and runtime block -> slot maps
-      float sumN[2], diag[2], sumN2 = 0.f, diag2 = 0.f;
-#pragma unroll
-      for (int grp = 0; grp < 2; ++grp) {
-        sumN[grp] = diag[grp] = 0.f;
-#pragma unroll
-        for (int jb = 0; jb < kGroupSlots; ++jb) {
-          const int b = d1_slot(grp, jb, R2);
-          if (jb < R && b == N) sumN[grp] = row[grp][jb];
-          if (jb < R && b == slot) diag[grp] = row[grp][jb];
-        }
-      }
-      // D2 columns: blocks 0..R2-1 are group 0 slots 16.., then group 1's
-      const int jb2 = g2 == 1 ? R2 : 0;
-#pragma unroll
-      for (int jb = 0; jb < 16; ++jb) {
-        if (jb - jb2 == N - 16) sumN2 = row2[jb];
-        if (jb - jb2 == slot2 - 16) diag2 = row2[jb];
-      }
 
-      const int k = (int)(it / chunks), ch0 = (int)(it % chunks) * kBoxCh;
-      // row sums and inverse standard deviations, shared through smem
-      auto table = [&](int grp, int a, float sum_a, float diag_a) {
-        const int64_t sa = (int64_t)sum_a;
-        const int64_t var = n * (int64_t)diag_a - sa * sa;
-        s->s_sum[grp][c][a] = (int32_t)sa;
-        float inv = 0.f;
-        if (a < N) {
-          if (var > 0) {
-            const float vf = (float)var;
-            inv = rsqrtf(vf);
-            inv = inv * (1.5f - 0.5f * vf * inv * inv);
-          } else {
-            atomicAdd(g.degenerate, 1ull);
-          }
-        }
-        s->s_inv[grp][c][a] = inv;
-      };
-#pragma unroll
-      for (int grp = 0; grp < 2; ++grp)
-        if (slot < N + 1) table(grp, slot, sumN[grp], diag[grp]);
-      if (g2 >= 0 && slot2 < N + 1) table(g2, slot2, sumN2, diag2);
-      named_sync(1, kEpiThreads);
-      // one packed output row: a, its group, its values by column block and
-      // the slot of each block (b < 0: not this group's)
-      auto emit = [&](int grp, int a, const float* rv, auto nb_c, auto slot_of) {
-        constexpr int NB = decltype(nb_c)::value;
-        const int64_t cell = (int64_t)k * g.n_chan + ch0 + grp * 8 + c;
-        const int64_t sa = s->s_sum[grp][c][a];
-        const float inva = s->s_inv[grp][c][a];
-        if (g.corr && a < N) {
-          float* dst = g.corr + cell * (int64_t)(N * (N + 1) / 2) + (a * N - a * (a - 1) / 2);
-#pragma unroll
-          for (int jb = 0; jb < NB; ++jb) {
-            const int b = slot_of(jb);
-            if (b < a || b >= N) continue;
-            float r;
-            if (b == a) {
-              r = 1.f;
+        const int k = (int)(it / chunks), ch0 = (int)(it % chunks) * kBoxCh;
+        // row sums and inverse standard deviations, shared through smem
+        auto table = [&](int grp, int a, V sum_a, V diag_a) {
+          const int64_t sa = (int64_t)sum_a;
+          const int64_t var = n * (int64_t)diag_a - sa * sa;
+          s->s_sum[grp][c][a] = (int32_t)sa;
+          float inv = 0.f;
+          if (a < N) {
+            if (var > 0) {
+              const float vf = (float)var;
+              inv = rsqrtf(vf);
+              inv = inv * (1.5f - 0.5f * vf * inv * inv);
             } else {
-              const int64_t cov = n * (int64_t)rv[jb] - sa * (int64_t)s->s_sum[grp][c][b];
-              r = (float)cov * inva * s->s_inv[grp][c][b];
+              atomicAdd(g.degenerate, 1ull);
             }
-            dst[b - a] = r;
           }
-        }
-        if (g.sums || g.sums8) {
-          const int N1 = N + 1;
-          const int64_t P = N1 * (N1 + 1) / 2;
-          const int row = a * N1 - a * (a - 1) / 2;
-          // public layout: one cell's entries contiguous; interleaved: the
-          // 8 channels of a group side by side, so a warp's 8-byte stores
-          // fill 64-byte runs
-          int64_t* dst = g.sums8 ? g.sums8 + ((cell >> 3) * P + row) * 8 + (cell & 7)
-                                 : g.sums + cell * P + row;
-          const int step = g.sums8 ? 8 : 1;
-#pragma unroll
-          for (int jb = 0; jb < NB; ++jb) {
-            const int b = slot_of(jb);
-            if (b < a || b > N) continue;
-            const int64_t gab = (int64_t)rv[jb];
-            int64_t v;
-            const int64_t cc = g.center;
-            if (a == N) v = n;                                  // (N, N): sample count
-            else if (b == N) v = gab + cc * n;                  // S_a
-            else v = gab + cc * (sa + (int64_t)s->s_sum[grp][c][b]) + cc * cc * n;
-            dst[(b - a) * step] = v;
+          s->s_inv[grp][c][a] = inv;
+        };
+  #pragma unroll
+        for (int grp = 0; grp < 2; ++grp)
+          if (slot < N + 1) table(grp, slot, sumN[grp], diag[grp]);
+        if (g2 >= 0 && slot2 < N + 1) table(g2, slot2, sumN2, diag2);
+        named_sync(1, kEpiThreads);
+        // one packed output row: a, its group, its values by column block and
+        // the slot of each block (b < 0: not this group's)
+        auto emit = [&](int grp, int a, const V* rv, auto nb_c, auto slot_of) {
+          constexpr int NB = decltype(nb_c)::value;
+          const int64_t cell = (int64_t)k * g.n_chan + ch0 + grp * 8 + c;
+          const int64_t sa = s->s_sum[grp][c][a];
+          const float inva = s->s_inv[grp][c][a];
+          if (g.corr && a < N) {
+            float* dst = g.corr + cell * (int64_t)(N * (N + 1) / 2) + (a * N - a * (a - 1) / 2);
+  #pragma unroll
+            for (int jb = 0; jb < NB; ++jb) {
+              const int b = slot_of(jb);
+              if (b < a || b >= N) continue;
+              float r;
+              if (b == a) {
+                r = 1.f;
+              } else {
+                const int64_t cov = n * (int64_t)rv[jb] - sa * (int64_t)s->s_sum[grp][c][b];
+                r = (float)cov * inva * s->s_inv[grp][c][b];
+              }
+              dst[b - a] = r;
+            }
           }
-        }
+          if (g.sums || g.sums8) {
+            const int N1 = N + 1;
+            const int64_t P = N1 * (N1 + 1) / 2;
+            const int row = a * N1 - a * (a - 1) / 2;
+            // public layout: one cell's entries contiguous; interleaved: the
+            // 8 channels of a group side by side, so a warp's 8-byte stores
+            // fill 64-byte runs
+            int64_t* dst = g.sums8 ? g.sums8 + ((cell >> 3) * P + row) * 8 + (cell & 7)
+                                   : g.sums + cell * P + row;
+            const int step = g.sums8 ? 8 : 1;
+  #pragma unroll
+            for (int jb = 0; jb < NB; ++jb) {
+              const int b = slot_of(jb);
+              if (b < a || b > N) continue;
+              const int64_t gab = (int64_t)rv[jb];
+              int64_t v;
+              const int64_t cc = g.center;
+              if (a == N) v = n;                                  // (N, N): sample count
+              else if (b == N) v = gab + cc * n;                  // S_a
+              else v = gab + cc * (sa + (int64_t)s->s_sum[grp][c][b]) + cc * cc * n;
+              dst[(b - a) * step] = v;
+            }
+          }
+        };
+  #pragma unroll
+        for (int grp = 0; grp < 2; ++grp)
+          if (slot <= N)
+            emit(grp, slot, row[grp], std::integral_constant<int, kGroupSlots>{},
+                 [&](int jb) { return jb < R ? d1_slot(grp, jb, R2) : -1; });
+        if (g2 >= 0 && slot2 <= N)
+          emit(g2, slot2, row2, std::integral_constant<int, 16>{},
+               [&](int jb) { return (jb >= jb2 && jb < jb2 + R2) ? 16 + jb - jb2 : -1; });
+        named_sync(1, kEpiThreads);  // smem tables reused by the next item
       };
+      if constexpr (kPol == 1) {
+        ok = mbar_wait(&s->acc_full, pcnt & 1, g.error);
+        if (!ok) break;
+        ++pcnt;
+        fence_after();
+        float row[2][kGroupSlots];   // D1 row `slot` of each group, by column block
+        float row2[16];              // D2 row `slot2`, by column block
 #pragma unroll
-      for (int grp = 0; grp < 2; ++grp)
-        if (slot <= N)
-          emit(grp, slot, row[grp], std::integral_constant<int, kGroupSlots>{},
-               [&](int jb) { return jb < R ? d1_slot(grp, jb, R2) : -1; });
-      if (g2 >= 0 && slot2 <= N)
-        emit(g2, slot2, row2, std::integral_constant<int, 16>{},
-             [&](int jb) { return (jb >= jb2 && jb < jb2 + R2) ? 16 + jb - jb2 : -1; });
-      named_sync(1, kEpiThreads);  // smem tables reused by the next item
+        for (int grp = 0; grp < 2; ++grp) {
+          // chunks of 32 columns (4 blocks x 8 channels), one load in flight
+#pragma unroll
+          for (int ch = 0; ch < kGroupSlots / 4; ++ch) {
+            if (ch * 4 < g.rb) {
+              uint32_t v[32];
+              tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + grp * 192 + ch * 32, v);
+              tmem_wait_ld();
+              pick4(v, c, &row[grp][4 * ch]);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) row[grp][4 * ch + u] = 0.f;
+            }
+          }
+        }
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+          if (2 * R2 > 4 * ch) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + 384 + ch * 32, v);
+            tmem_wait_ld();
+            pick4(v, c, &row2[4 * ch]);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) row2[4 * ch + u] = 0.f;
+          }
+        }
+        fence_before();
+        mbar_arrive(&s->acc_empty);  // accumulators may be overwritten now
+        finish(row, row2);
+      } else {
+        // exact integer sums over the accumulation pieces (each piece's
+        // sums are integers below 2^24, so exact in FP32; the total fits int32)
+        const int pieces = stages / g.piece_stages;
+        int32_t row[2][kGroupSlots];
+        int32_t row2[16];
+#pragma unroll
+        for (int grp = 0; grp < 2; ++grp)
+#pragma unroll
+          for (int jb = 0; jb < kGroupSlots; ++jb) row[grp][jb] = 0;
+#pragma unroll
+        for (int jb = 0; jb < 16; ++jb) row2[jb] = 0;
+        for (int pc = 0; pc < pieces && ok; ++pc, ++pcnt) {
+          ok = mbar_wait(&s->acc_full, pcnt & 1, g.error);
+          if (!ok) break;
+          fence_after();
+#pragma unroll
+          for (int grp = 0; grp < 2; ++grp) {
+#pragma unroll
+            for (int ch = 0; ch < kGroupSlots / 4; ++ch) {
+              if (ch * 4 < g.rb) {
+                uint32_t v[32];
+                float f4[4];
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + grp * 192 + ch * 32, v);
+                tmem_wait_ld();
+                pick4(v, c, f4);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) row[grp][4 * ch + u] += __float2int_rn(f4[u]);
+              }
+            }
+          }
+#pragma unroll
+          for (int ch = 0; ch < 4; ++ch) {
+            if (2 * R2 > 4 * ch) {
+              uint32_t v[32];
+              float f4[4];
+              tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + 384 + ch * 32, v);
+              tmem_wait_ld();
+              pick4(v, c, f4);
+#pragma unroll
+              for (int u = 0; u < 4; ++u) row2[4 * ch + u] += __float2int_rn(f4[u]);
+            }
+          }
+          fence_before();
+          mbar_arrive(&s->acc_empty);
+        }
+        if (!ok) break;
+        finish(row, row2);
+      }
     }
   }
   __syncthreads();
@@ -1020,10 +1089,10 @@ static int tc_u8_depth(int v, int n_beam, int n_pol) {
   }
 }
 
-// Two polarisations double the u8 stage; a variant whose ring would then be
-// shallower than two stages gives way to variant 0 (two f16 stages).
+// Two polarisations double the u8 stage: they run variant 0 (two f16
+// stages), which leaves the u8 ring at least two stages deep.
 static int tc_variant_for(const mraid_plan_s* pl, int n_pol) {
-  return n_pol == 2 && tc_u8_depth(pl->tc_variant, pl->p.n_beam, 2) < 2 ? 0 : pl->tc_variant;
+  return n_pol == 2 ? 0 : pl->tc_variant;
 }
 
 bool gram_tc_supported(const mraid_plan_s* pl, const void* d_data, int n_pol) {
@@ -1063,6 +1132,18 @@ cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int su
   a.n_sub = n_sub;
   a.n_pol = n_pol;
   a.center = n_pol == 2 ? 255 : 128;
+  // FP32 sums in TMEM stay exact while they are below 2^24: 1024 samples of
+  // products up to 128^2 for one polarisation, 256 samples of products up to
+  // 255^2 for the sum of two; a sub-integration of two polarisations is
+  // accumulated in pieces (the largest number of stages dividing it within
+  // 256 samples) that the epilogue adds as integers
+  {
+    const int stages = p.n_samp_sub / t;
+    int d = stages;
+    if (n_pol == 2)
+      while (d > 1 && (stages % d != 0 || d * t > 256)) --d;
+    a.piece_stages = d;
+  }
   const int R = p.n_beam + 1;              // beams + the row of ones
   a.R = R;
   a.R2 = R > 16 ? R - 16 : 0;
@@ -1075,18 +1156,21 @@ cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int su
   const int64_t items = (int64_t)n_sub * (p.n_chan / kBoxCh);
   const int grid = (int)(items < pl->sm_count ? items : pl->sm_count);
   cudaError_t e = cudaSuccess;
-#define MRAID_TC_LAUNCH(T, NF, U)                                                                 \
+#define MRAID_TC_LAUNCH_P(T, NF, U, P)                                                             \
   do {                                                                                           \
     using C_ = TcCfg<T, NF, U>;                                                                     \
-    const int n_u8 = u8_ring_depth<C_>(p.n_beam, n_pol);                                         \
+    const int n_u8 = u8_ring_depth<C_>(p.n_beam, P);                                             \
     a.n_u8 = n_u8;                                                                               \
-    const size_t smem = smem_bytes<C_>(p.n_beam, n_u8, n_pol);                                   \
-    e = cudaFuncSetAttribute(gram_tc_kernel<T, NF, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             (int)smem);                                                         \
+    const size_t smem = smem_bytes<C_>(p.n_beam, n_u8, P);                                       \
+    e = cudaFuncSetAttribute(gram_tc_kernel<T, NF, U, P>,                                        \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
     if (e == cudaSuccess && grid > 0)                                                            \
-      gram_tc_kernel<T, NF, U><<<grid, kThreads, smem, pl->stream>>>(map, a);                       \
+      gram_tc_kernel<T, NF, U, P><<<grid, kThreads, smem, pl->stream>>>(map, a);                  \
   } while (0)
-  switch (variant) {
+#define MRAID_TC_LAUNCH(T, NF, U) MRAID_TC_LAUNCH_P(T, NF, U, 1)
+  if (n_pol == 2) {
+    MRAID_TC_LAUNCH_P(64, 2, 1, 2);  // variant 0: two f16 stages leave room for the doubled u8 ring
+  } else switch (variant) {
     case 1: MRAID_TC_LAUNCH(32, 4, 1); break;
     case 2: MRAID_TC_LAUNCH(32, 2, 1); break;
     case 3: MRAID_TC_LAUNCH(64, 3, 1); break;
@@ -1097,6 +1181,7 @@ cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int su
     default: MRAID_TC_LAUNCH(64, 2, 1); break;
   }
 #undef MRAID_TC_LAUNCH
+#undef MRAID_TC_LAUNCH_P
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -1136,6 +1221,7 @@ cudaError_t launch_gram_tc_f32(const mraid_plan_s* pl, const float* d_data, int 
   a.rb = (R + 1) / 2 * 2;
   a.n_pol = 1;
   a.center = 0;
+  a.piece_stages = 1;
   a.sums = nullptr;
   a.sums8 = nullptr;
   a.corr = d_corr;

@@ -25,7 +25,7 @@ struct FlagDev {  // device image of mraid_flag_info
 
 enum KernelId {
   K_GRAM = 0, K_CORR, K_EIG, K_FLAG, K_GRAM_TC, K_GRAM_F32, K_GRAM_TC_F32, K_AGG,
-  K_BP_INPUT, K_ARPLS, K_CCM_BP, K_POL2_FOLD, K_POL2_PIECES, K_COUNT
+  K_BP_INPUT, K_ARPLS, K_CCM_BP, K_POL2_FOLD, K_COUNT
 };
 const char* kernel_name(int id);
 
@@ -108,8 +108,8 @@ struct mraid_plan_s {
   size_t bp_sys = 0;
   double* ar_work = nullptr;
   size_t ar_work_elems = 0;
-  // two polarisations: sums of 256-sample pieces (tensor cores) or of the
-  // 2N stacked blocks; pol_cells counts its int64 elements
+  // two polarisations: Gram sums of the 2N stacked blocks where the tensor
+  // cores do not take the block; pol_cells counts its int64 elements
   int64_t* pol_sums = nullptr;
   size_t pol_cells = 0;
 };
@@ -138,8 +138,8 @@ cudaError_t launch_gram_f32(const mraid_plan_s* pl, const float* d_data, int sub
 // tensor-core Gram fused with the correlation (gram_tc.cu); either output
 // may be null. cudaErrorNotSupported when the shape or layout does not fit.
 // n_pol 2: blocks b and N + b are two polarisations of beam b, summed in
-// the converter (the sums are of the total power, exact for sub-integrations
-// of up to 256 samples)
+// the converter; the sums and the correlation are of the total power (exact:
+// TMEM accumulates pieces of at most 256 samples, the epilogue adds them)
 bool gram_tc_supported(const mraid_plan_s* pl, const void* d_data, int n_pol = 1);
 int tc_variant_samples(int v);
 int tc_default_variant(int n_beam);
@@ -198,10 +198,6 @@ cudaError_t launch_ccm_bandpass(const mraid_plan_s* pl, const int64_t* d_sums, b
 // pol2.cu: total-power sums [cell][P] from the stacked 2N-block sums
 cudaError_t launch_pol2_fold(const mraid_plan_s* pl, const int64_t* d_stacked, int64_t n_cells,
                              int64_t* d_sums);
-// pol2.cu: sums of sub-integrations of m pieces from the pieces' sums
-// (interleaved); d_sums interleaved, or [cell][P] when out_public
-cudaError_t launch_pol2_pieces(const mraid_plan_s* pl, const int64_t* d_pieces, int m,
-                               int64_t* d_sums, bool out_public);
 // multires.cu: d_dst[k] = sum_{j < m} d_src[k m + j] over the int64 Gram
 // sums of n_out_sub sub-intervals (n_chan cells each)
 cudaError_t launch_gram_aggregate(const mraid_plan_s* pl, const int64_t* d_src, int64_t* d_dst,

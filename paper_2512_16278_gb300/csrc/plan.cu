@@ -41,7 +41,6 @@ const char* kernel_name(int id) {
     case K_ARPLS: return "arpls";
     case K_CCM_BP: return "ccm_bandpass";
     case K_POL2_FOLD: return "pol2_fold";
-    case K_POL2_PIECES: return "pol2_pieces";
   }
   return "unknown";
 }
@@ -558,41 +557,20 @@ mraid_status ensure_arpls_work(mraid_plan_s* pl, int n, int n_sys) {
 
 namespace mraid {
 namespace {
-// Exact Gram sums of the total power of a two-polarisation block into
-// d_sums. Tensor cores where they take the shape: the kernel adds the two
-// polarisations of every sample and writes the sums of 256-sample pieces
-// (a plan view with 256-sample sub-integrations), which are then added per
-// sub-integration; d_sums comes out interleaved by 8 channels unless
-// want_public. Otherwise: the 8-bit Gram of the 2N stacked blocks (a plan
-// view with 2N beams), folded into [cell][P]. *interleaved tells which.
-constexpr int kPol2Piece = 256;
-mraid_status pol2_sums(mraid_plan_s* pl, const void* d_data, int64_t* d_sums, bool want_public,
-                       bool* interleaved) {
+// True when the tensor-core Gram takes a two-polarisation block whole: it
+// adds the polarisations in its converter and the pieces of each
+// sub-integration in its epilogue, so it writes the total power's sums
+// and correlation directly.
+bool pol2_on_tensor_cores(const mraid_plan_s* pl, const void* d_data) {
+  return !pl->force_dp4a && pl->p.bit_depth == 8 && gram_tc_supported(pl, d_data, 2);
+}
+
+// Otherwise: the exact 8-bit Gram of the 2N stacked blocks (a plan view
+// with 2N beams), folded into the total power's sums [cell][P] in d_sums.
+mraid_status pol2_stacked_sums(mraid_plan_s* pl, const void* d_data, int64_t* d_sums) {
   const int N = pl->p.n_beam;
-  if (pl->p.bit_depth != 8 || 2 * N > kMaxBeam) {
-    set_error("two polarisations: 8-bit samples and at most %d beams", kMaxBeam / 2);
-    return MRAID_ERR_UNSUPPORTED;
-  }
   const int P2 = (2 * N + 1) * (2 * N + 2) / 2;
-  const int m = pl->p.n_samp_sub / kPol2Piece;
-  mraid_plan_s w;  // pieces of 256 samples, N beams, two polarisations
-  w.p = pl->p;
-  w.p.keep = nullptr;
-  w.p.n_samp_sub = kPol2Piece;
-  w.p.n_sub = pl->p.n_sub * m;
-  w.device = pl->device;
-  w.sm_count = pl->sm_count;
-  w.stream = pl->stream;
-  w.n_cells = pl->n_cells * m;
-  w.beam_stride = pl->beam_stride;
-  w.np = pl->np;
-  w.psum = pl->psum;
-  w.d_degenerate = pl->d_degenerate;
-  w.d_error = pl->d_error;
-  w.tc_variant = pl->tc_variant;
-  const bool tc = !pl->force_dp4a && pl->p.n_samp_sub % kPol2Piece == 0 && m >= 1 &&
-                  gram_tc_supported(&w, d_data, 2);
-  const size_t need = tc ? (size_t)w.n_cells * pl->psum : (size_t)pl->n_cells * P2;
+  const size_t need = (size_t)pl->n_cells * P2;
   if (need > pl->pol_cells) {  // pol_cells counts int64 elements
     cudaFree(pl->pol_sums);
     pl->pol_sums = nullptr;
@@ -604,18 +582,7 @@ mraid_status pol2_sums(mraid_plan_s* pl, const void* d_data, int64_t* d_sums, bo
     }
     pl->pol_cells = need;
   }
-  cudaError_t e = cudaSuccess;
-  if (tc) {
-    *interleaved = !want_public;
-    e = MRAID_PROF(pl, K_GRAM_TC,
-                   launch_gram_tc(&w, static_cast<const uint8_t*>(d_data), 0, w.p.n_sub, nullptr,
-                                  nullptr, pl->pol_sums, 2));
-    if (e == cudaSuccess)
-      e = MRAID_PROF(pl, K_POL2_PIECES, launch_pol2_pieces(pl, pl->pol_sums, m, d_sums, want_public));
-    return e == cudaSuccess ? MRAID_OK : cuda_fail(e, "two-polarisation Gram");
-  }
-  *interleaved = false;
-  mraid_plan_s v;  // 2N stacked blocks
+  mraid_plan_s v;
   v.p = pl->p;
   v.p.n_beam = 2 * N;
   v.p.keep = nullptr;
@@ -630,6 +597,7 @@ mraid_status pol2_sums(mraid_plan_s* pl, const void* d_data, int64_t* d_sums, bo
   v.d_error = pl->d_error;
   v.force_dp4a = pl->force_dp4a;
   v.tc_variant = tc_default_variant(2 * N);
+  cudaError_t e = cudaSuccess;
   if (!v.force_dp4a && gram_tc_supported(&v, d_data)) {
     e = MRAID_PROF(pl, K_GRAM_TC,
                    launch_gram_tc(&v, static_cast<const uint8_t*>(d_data), 0, v.p.n_sub,
@@ -646,6 +614,43 @@ mraid_status pol2_sums(mraid_plan_s* pl, const void* d_data, int64_t* d_sums, bo
     e = MRAID_PROF(pl, K_POL2_FOLD, launch_pol2_fold(pl, pl->pol_sums, pl->n_cells, d_sums));
   return e == cudaSuccess ? MRAID_OK : cuda_fail(e, "two-polarisation Gram");
 }
+
+mraid_status check_pol2(const mraid_plan_s* pl) {
+  if (pl->p.bit_depth != 8 || 2 * pl->p.n_beam > kMaxBeam) {
+    set_error("two polarisations: 8-bit samples and at most %d beams", kMaxBeam / 2);
+    return MRAID_ERR_UNSUPPORTED;
+  }
+  return MRAID_OK;
+}
+
+// Sums ([cell][P], may be null) and correlation (may be null) of the
+// total power of a two-polarisation block; counts zero-variance beams.
+mraid_status pol2_ccm(mraid_plan_s* pl, const void* d_data, int64_t* d_sums, float* d_corr) {
+  cudaError_t e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "memset");
+  if (pol2_on_tensor_cores(pl, d_data)) {
+    e = MRAID_PROF(pl, K_GRAM_TC,
+                   launch_gram_tc(pl, static_cast<const uint8_t*>(d_data), 0, pl->p.n_sub, d_sums,
+                                  d_corr, nullptr, 2));
+    return e == cudaSuccess ? MRAID_OK : cuda_fail(e, "gram_tc launch");
+  }
+  int64_t* sums = d_sums;
+  if (!sums) {
+    mraid_status st = ensure_workspace(pl, (size_t)pl->n_cells);
+    if (st != MRAID_OK) return st;
+    sums = pl->ws.sums;
+  }
+  mraid_status st = pol2_stacked_sums(pl, d_data, sums);
+  if (st != MRAID_OK) return st;
+  if (d_corr) {
+    // the stacked Gram's own counts are of the 2N blocks: count again
+    e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
+    if (e == cudaSuccess)
+      e = MRAID_PROF(pl, K_CORR, launch_corr_from_sums(pl, sums, pl->n_cells, d_corr));
+    if (e != cudaSuccess) return cuda_fail(e, "corr launch");
+  }
+  return MRAID_OK;
+}
 }  // namespace
 }  // namespace mraid
 
@@ -657,22 +662,9 @@ mraid_status mraid_ccm_pol2(mraid_plan_t pl, const void* d_data, int64_t* d_sums
     set_error("mraid_ccm_pol2: d_data and one of d_sums, d_corr are required");
     return MRAID_ERR_INVALID_ARG;
   }
-  int64_t* sums = d_sums;
-  if (!sums) {
-    st = ensure_workspace(pl, (size_t)pl->n_cells);
-    if (st != MRAID_OK) return st;
-    sums = pl->ws.sums;
-  }
-  bool inter = false;
-  st = pol2_sums(pl, d_data, sums, d_sums != nullptr, &inter);
+  st = check_pol2(pl);
   if (st != MRAID_OK) return st;
-  if (d_corr) {
-    cudaError_t e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
-    if (e == cudaSuccess)
-      e = MRAID_PROF(pl, K_CORR, launch_corr_from_sums(pl, sums, pl->n_cells, d_corr, inter));
-    if (e != cudaSuccess) return cuda_fail(e, "corr launch");
-  }
-  return MRAID_OK;
+  return pol2_ccm(pl, d_data, d_sums, d_corr);
 }
 
 mraid_status mraid_run_pol2(mraid_plan_t pl, const void* d_data, float* d_evals, float* d_q1,
@@ -683,6 +675,8 @@ mraid_status mraid_run_pol2(mraid_plan_t pl, const void* d_data, float* d_evals,
     set_error("mraid_run_pol2: d_data, d_stat and d_flags are required");
     return MRAID_ERR_INVALID_ARG;
   }
+  st = check_pol2(pl);
+  if (st != MRAID_OK) return st;
   st = ensure_workspace(pl, (size_t)pl->n_cells);
   if (st != MRAID_OK) return st;
   if (d_q1) {
@@ -691,15 +685,8 @@ mraid_status mraid_run_pol2(mraid_plan_t pl, const void* d_data, float* d_evals,
   }
   cudaError_t e = cudaMemsetAsync(pl->d_sweeps, 0, 2 * sizeof(unsigned long long), pl->stream);
   if (e != cudaSuccess) return cuda_fail(e, "memset");
-  bool inter = false;
-  st = pol2_sums(pl, d_data, pl->ws.sums, false, &inter);
+  st = pol2_ccm(pl, d_data, nullptr, pl->ws.corr);
   if (st != MRAID_OK) return st;
-  // zero-variance beams of the total power are counted by the correlation
-  e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
-  if (e == cudaSuccess)
-    e = MRAID_PROF(pl, K_CORR,
-                   launch_corr_from_sums(pl, pl->ws.sums, pl->n_cells, pl->ws.corr, inter));
-  if (e != cudaSuccess) return cuda_fail(e, "corr launch");
   e = MRAID_PROF(pl, K_EIG, launch_eig(pl, pl->ws.corr, pl->n_cells, d_evals, d_q1, d_stat));
   if (e != cudaSuccess) return cuda_fail(e, "eig launch");
   e = MRAID_PROF(pl, K_FLAG, launch_flag(pl, d_stat, d_flags));

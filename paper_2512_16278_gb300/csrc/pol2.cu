@@ -6,10 +6,8 @@
 // and sum_t x_a = sum p0_a + sum p1_a. So the exact Gram of the total power
 // is a fold of the exact Gram of the 2N stacked polarisation blocks (block
 // p*N + a = polarisation p of beam a), which the 8-bit Gram kernels form
-// as they stand; int64 addition keeps it exact. Where the tensor-core Gram
-// takes the shape it adds the polarisations itself, in pieces of 256
-// samples (so its FP32 sums of products up to 255^2 stay below 2^24), and
-// the pieces of a sub-integration are added here.
+// as they stand; int64 addition keeps it exact. (Where the tensor-core Gram
+// takes the shape it adds the polarisations itself and needs none of this.)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -51,42 +49,7 @@ __global__ void pol2_fold_kernel(const int64_t* __restrict__ in, int64_t* __rest
   }
 }
 
-// The tensor-core route: the kernel sums the polarisations itself and
-// writes the exact sums of pieces of 256 samples (interleaved by 8
-// channels, [piece cell / 8][P][piece cell % 8]); a sub-integration of m
-// pieces adds them up. Output interleaved the same way, or [cell][P].
-__global__ void pol2_pieces_kernel(const int64_t* __restrict__ in, int64_t* __restrict__ out,
-                                   int64_t n_cells, int n_chan, int P, int m, int out_public) {
-  const int64_t total = n_cells * P;
-  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total;
-       o += (int64_t)gridDim.x * blockDim.x) {
-    // o runs over the interleaved order: group, entry, channel in group
-    const int c8 = (int)(o & 7);
-    const int64_t ge = o >> 3;
-    const int e = (int)(ge % P);
-    const int64_t cell = (ge / P) * 8 + c8;
-    const int64_t k = cell / n_chan, chan = cell - k * n_chan;
-    int64_t acc = 0;
-    for (int j = 0; j < m; ++j) {
-      const int64_t pc = (k * m + j) * n_chan + chan;  // piece cell; pc % 8 == c8
-      acc += in[((pc >> 3) * P + e) * 8 + c8];
-    }
-    out[out_public ? cell * P + e : o] = acc;
-  }
-}
-
 }  // namespace
-
-cudaError_t launch_pol2_pieces(const mraid_plan_s* pl, const int64_t* d_pieces, int m,
-                               int64_t* d_sums, bool out_public) {
-  const int64_t total = pl->n_cells * pl->psum;
-  int64_t blocks = (total + 255) / 256;
-  if (blocks > (int64_t)pl->sm_count * 16) blocks = (int64_t)pl->sm_count * 16;
-  if (blocks < 1) return cudaSuccess;
-  pol2_pieces_kernel<<<(unsigned)blocks, 256, 0, pl->stream>>>(
-      d_pieces, d_sums, pl->n_cells, pl->p.n_chan, pl->psum, m, out_public ? 1 : 0);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_pol2_fold(const mraid_plan_s* pl, const int64_t* d_stacked, int64_t n_cells,
                              int64_t* d_sums) {

@@ -23,10 +23,12 @@ def two_pol_block(n_beam, n_chan, n_s, n_sub, seed, n_burst=1):
 
 
 @pytest.mark.parametrize("n_beam,n_chan,n_s,n_sub,route", [
-    (19, 48, 512, 3, "pieces"),   # tensor cores add the polarisations, 2 pieces of 256
-    (23, 16, 256, 4, "pieces"),   # the most beams the tensor-core Gram takes
-    (7, 48, 128, 6, "stacked"),   # 128 samples: 2N + 1 = 15 stacked slots on tensor cores
-    (19, 40, 96, 5, "stacked"),   # 38 stacked blocks: CUDA-core Gram
+    (19, 48, 512, 3, "tc"),       # tensor cores add the polarisations; 2 pieces of 256
+    (19, 48, 384, 2, "tc"),       # 2 pieces of 192 (the largest divisor within 256)
+    (23, 16, 256, 4, "tc"),       # the most beams the tensor-core Gram takes
+    (19, 32, 128, 6, "tc"),       # one piece
+    (7, 40, 128, 6, "stacked"),   # 40 channels: the stacked 2N-block Gram on CUDA cores
+    (30, 16, 64, 4, "stacked"),   # 30 beams: beyond the tensor-core kernel
 ])
 def test_pol2_sums_exact(n_beam, n_chan, n_s, n_sub, route):
     import torch
@@ -41,9 +43,8 @@ def test_pol2_sums_exact(n_beam, n_chan, n_s, n_sub, route):
         sums, _ = plan.ccm_pol2(d, corr=False)
         plan.sync()
         ran = m.mraid_profile_read(plan.handle)
-    assert ("pol2_pieces" in ran) == (route == "pieces"), ran
-    if route == "stacked":
-        assert ("gram_tc" in ran) == (2 * n_beam + 1 <= 24), ran
+    assert ("pol2_fold" in ran) == (route == "stacked"), ran
+    assert ("gram_tc" in ran) == (route == "tc"), ran
     G = unpack_sums(sums.cpu().numpy(), n_beam)
     for k in range(n_sub):
         for c in range(n_chan):
@@ -51,14 +52,14 @@ def test_pol2_sums_exact(n_beam, n_chan, n_s, n_sub, route):
                                           oracle.cell_gram_pol2(data, n_s, k, c))
 
 
-@pytest.mark.parametrize("S", [256, 128])   # tensor-core pieces; stacked CUDA-core Gram
-def test_pol2_run_matches_oracle(S):
+@pytest.mark.parametrize("S,C", [(256, 64), (128, 40)])   # tensor cores; stacked CUDA-core Gram
+def test_pol2_run_matches_oracle(S, C):
     import torch
     m = lib()
     # no broadband bursts: in a block of 32 sub-integrations each burst
     # covers 2, and with the narrowband channels a fifth of the cells would
     # sit near s ~ 0.85, lifting mu + 3 sigma above 1 (nothing flagged)
-    N, C, K = 19, 64, 32
+    N, K = 19, 32
     cfg, data = two_pol_block(N, C, S, K, 101, n_burst=0)
     d = torch.from_numpy(data).cuda()
     with m.Plan(N, C, S, K) as plan:
@@ -78,13 +79,13 @@ def test_pol2_run_matches_oracle(S):
         assert F[:, c].mean() > 0.9, c
 
 
-@pytest.mark.parametrize("S", [256, 128])
-def test_pol2_with_silent_second_polarisation_equals_single(S):
+@pytest.mark.parametrize("S,C", [(256, 64), (128, 40)])
+def test_pol2_with_silent_second_polarisation_equals_single(S, C):
     """Polarisation 1 all zero: the total power is polarisation 0, and the
     statistic and flags equal mraid_run's on polarisation 0 alone."""
     import torch
     m = lib()
-    N, C, K = 19, 64, 16
+    N, K = 19, 16
     cfg, data = two_pol_block(N, C, S, K, 7)
     data[N:] = 0
     d = torch.from_numpy(data).cuda()
