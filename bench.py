@@ -491,7 +491,7 @@ def bench_bandpass(m, torch, d, h, cfg, stream, steps):
                                        "the oracle's CCM about the GPU bandpass"}}
 
 
-def bench_pol2(m, torch, h, cfg, stream, steps):
+def bench_pol2(m, torch, h, cfg, stream, steps, peaks):
     """Two recorded polarisations: the block as polarisation 0 and a second
     synthetic block (next seed, its own RFI) as polarisation 1, stacked in
     device memory; mraid_run_pol2 per step, kernel breakdown, and sampled
@@ -527,6 +527,14 @@ def bench_pol2(m, torch, h, cfg, stream, steps):
     prof = m.mraid_profile_read(plan.handle)
     ms = e0.elapsed_time(e1) / steps
     kt = {k: tot / steps for k, (n, tot) in prof.items() if n > 0}
+    gram = None
+    if "gram_tc" in kt:
+        b = 2 * nb + cells * 4 * (N * (N + 1) // 2)     # both polarisations in, r out
+        a = b / (kt["gram_tc"] / 1e3) / 1e9
+        gram = {"bound": "hbm", "kernel": "gram_tc (two polarisations)", "achieved": a,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": a / peaks["hbm_gbs"],
+                "traffic": kernel_traffic("gram_tc_pol2"), "work_per_launch": b,
+                "ms_per_launch": kt["gram_tc"]}
     rng = np.random.default_rng(9)
     idx = np.unique(rng.integers(0, cells, size=48))
     data = h2.numpy().reshape(2 * N, cfg.n_time, C)
@@ -542,11 +550,13 @@ def bench_pol2(m, torch, h, cfg, stream, steps):
                         f"(uint8, {2 * nb / 1e9:.1f} GB)",
             "ms_per_step": ms, "cells_per_s": cells / (ms / 1e3),
             "input_gbs": 2 * nb / (ms / 1e3) / 1e9,
-            "kernels_ms_per_step": kt, "masked_fraction": info.n_flagged / cells,
+            "kernels_ms_per_step": kt, "gram_roofline": gram,
+            "masked_fraction": info.n_flagged / cells,
             "sampled_parity": {"cells": int(idx.size), "eig_err_rel_max": e_err,
                                "stat_err_rel_max": s_err},
-            "path": "exact Gram of the 2N stacked polarisation blocks, folded into the total "
-                    "power's Gram (int64), then the correlation, eigensolver and mask"}
+            "path": "tensor cores: polarisations added in the converter, TMEM pieces of 256 "
+                    "samples added as integers in the epilogue, correlation fused; then the "
+                    "eigensolver and mask"}
 
 
 def bench_batched(m, torch, stream, steps):
@@ -884,7 +894,7 @@ def run_mraid(args):
                                            for x in bits.view(-1).cpu().tolist()))}
     pol2 = None
     if world == 1 and args.pol2_steps > 0:
-        pol2 = bench_pol2(m, torch, h, cfg, stream, args.pol2_steps)
+        pol2 = bench_pol2(m, torch, h, cfg, stream, args.pol2_steps, peaks)
     bandpass = None
     if world == 1 and args.bandpass_steps > 0 and rank == 0:
         bandpass = bench_bandpass(m, torch, d, h, cfg, stream, args.bandpass_steps)
