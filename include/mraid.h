@@ -217,8 +217,12 @@ mraid_status mraid_multires(mraid_plan_t plan, const void* d_data, int32_t n_lev
  * [time][chan], blocks the plan's beam_stride apart. Eq. 1 is taken of the
  * total power x_a = p0_a + p1_a (0..510). d_sums, d_corr and the rest as
  * in mraid_ccm and mraid_run; the sums are those of x, exact. The plan
- * describes the N beams (n_beam <= 64, bit_depth 8). A work buffer of
- * (2N+1)(2N+2)/2 int64 per cell is allocated on first use. */
+ * describes the N beams (n_beam <= 64, bit_depth 8). Where the tensor-core
+ * Gram takes the shape (N <= 23, channels a multiple of 16, samples per
+ * sub-integration a multiple of 64 up to 1024, 16-byte aligned) it adds the
+ * polarisations as it reads them and needs no work buffer; otherwise the
+ * Gram of the 2N stacked blocks is formed and folded, in a work buffer of
+ * (2N+1)(2N+2)/2 int64 per cell allocated on first use. */
 mraid_status mraid_ccm_pol2(mraid_plan_t plan, const void* d_data, int64_t* d_sums,
                             float* d_corr);
 mraid_status mraid_run_pol2(mraid_plan_t plan, const void* d_data, float* d_evals,
