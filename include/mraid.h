@@ -39,7 +39,10 @@
 extern "C" {
 #endif
 
-#define MRAID_ABI_VERSION 1
+/* 1: the plain, batched and served paths; 2: adds mraid_multires, the
+ * bandpass entry points (mraid_bandpass_params) and the two-polarisation
+ * entry points. Existing structures and calls are unchanged. */
+#define MRAID_ABI_VERSION 2
 
 typedef enum {
   MRAID_OK = 0,

@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_abi_version_and_status_strings(lib):
     import paper_2512_16278_gb300 as m
-    assert m.mraid_abi_version() == 1
+    assert m.mraid_abi_version() == 2
     for s, name in m.STATUS.items():
         assert m.mraid_status_string(s)
     assert m.mraid_status_string(999) == "unknown status"
