@@ -408,3 +408,140 @@ cudaError_t launch_ccm_bandpass(const mraid_plan_s* pl, const int64_t* d_sums, b
 }
 
 }  // namespace mraid
+
+namespace mraid {
+namespace {
+mraid_status check_bandpass_params(const mraid_bandpass_params* bp) {
+  if (!bp || !(bp->lam > 0.0) || !(bp->lam < 1e300) || !(bp->ratio > 0.0) || bp->itermax < 1 ||
+      bp->itermax > 1000 || bp->interval < 1) {
+    set_error("bandpass parameters: lam > 0, ratio > 0, itermax in 1..1000, interval >= 1");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  return MRAID_OK;
+}
+
+// ArPLS arrays in global memory for spectra too long for shared memory
+mraid_status ensure_arpls_work(mraid_plan_s* pl, int n, int n_sys) {
+  const size_t need = arpls_work_doubles(n, n_sys);
+  if (need <= pl->ar_work_elems) return MRAID_OK;
+  cudaFree(pl->ar_work);
+  pl->ar_work = nullptr;
+  pl->ar_work_elems = 0;
+  cudaError_t e = cudaMalloc(&pl->ar_work, need * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e, "arpls work allocation");
+  }
+  pl->ar_work_elems = need;
+  return MRAID_OK;
+}
+}  // namespace
+}  // namespace mraid
+
+// ---------------------------------------------------------------------------
+// Entry points (include/mraid.h)
+
+using namespace mraid;
+
+void mraid_default_bandpass_params(mraid_bandpass_params* bp) {
+  if (!bp) return;
+  bp->lam = 1e5;
+  bp->ratio = 1e-3;
+  bp->itermax = 50;
+  bp->interval = 20;
+}
+
+mraid_status mraid_arpls(mraid_plan_t pl, const double* d_y, int32_t n_sys, int32_t n,
+                         const mraid_bandpass_params* bp, double* d_z, int32_t* d_iters) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  st = check_bandpass_params(bp);
+  if (st != MRAID_OK) return st;
+  if (!d_y || !d_z || n < 3 || n > (1 << 20) || n_sys < 0) {
+    set_error("mraid_arpls: d_y and d_z are required, 3 <= n <= 2^20, n_sys >= 0");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  st = ensure_arpls_work(pl, n, n_sys);
+  if (st != MRAID_OK) return st;
+  cudaError_t e = MRAID_PROF(pl, K_ARPLS,
+                             launch_arpls(pl, d_y, n_sys, n, bp->lam, bp->ratio, bp->itermax, d_z,
+                                          nullptr, d_iters, pl->ar_work));
+  return e == cudaSuccess ? MRAID_OK : cuda_fail(e, "arpls launch");
+}
+
+mraid_status mraid_run_bandpass(mraid_plan_t pl, const void* d_data,
+                                const mraid_bandpass_params* bp, float* d_bandpass,
+                                float* d_evals, float* d_q1, float* d_stat, uint8_t* d_flags,
+                                mraid_flag_info* info) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  st = check_bandpass_params(bp);
+  if (st != MRAID_OK) return st;
+  if (!d_data || !d_stat || !d_flags) {
+    set_error("mraid_run_bandpass: d_data, d_stat and d_flags are required");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  if (pl->p.bit_depth != 8 || pl->p.n_chan < 3 || pl->p.n_chan > (1 << 20)) {
+    set_error("mraid_run_bandpass: 8-bit samples and 3 to 2^20 channels");
+    return MRAID_ERR_UNSUPPORTED;
+  }
+  const int interval = bp->interval;
+  const int n_int = (pl->p.n_sub + interval - 1) / interval;
+  const int n_sys = n_int * pl->p.n_beam;
+  const size_t elems = (size_t)n_sys * pl->p.n_chan;
+  st = ensure_workspace(pl, (size_t)pl->n_cells);
+  if (st != MRAID_OK) return st;
+  cudaError_t e = cudaSuccess;
+  if (elems > pl->bp_elems || (size_t)n_sys > pl->bp_sys) {
+    cudaFree(pl->bp_y);
+    cudaFree(pl->bp_z);
+    cudaFree(pl->bp_iters);
+    pl->bp_y = pl->bp_z = nullptr;
+    pl->bp_iters = nullptr;
+    pl->bp_elems = pl->bp_sys = 0;
+    e = cudaMalloc(&pl->bp_y, elems * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&pl->bp_z, elems * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&pl->bp_iters, (size_t)n_sys * sizeof(int32_t));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_fail(e, "bandpass workspace allocation");
+    }
+    pl->bp_elems = elems;
+    pl->bp_sys = (size_t)n_sys;
+  }
+  st = ensure_arpls_work(pl, pl->p.n_chan, n_sys);
+  if (st != MRAID_OK) return st;
+  if (d_q1) {
+    st = evals_for_q1(pl, (size_t)pl->n_cells, &d_evals);
+    if (st != MRAID_OK) return st;
+  }
+  e = cudaMemsetAsync(pl->d_sweeps, 0, 2 * sizeof(unsigned long long), pl->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "memset");
+  bool inter = false;
+  st = gram_sums_pass(pl, d_data, nullptr, &inter);
+  if (st != MRAID_OK) return st;
+  // the sums pass may count zero-variance beams; nothing is normalised here
+  e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
+  if (e == cudaSuccess)
+    e = MRAID_PROF(pl, K_BP_INPUT,
+                   launch_bandpass_input(pl, pl->ws.sums, inter, interval, pl->bp_y));
+  if (e == cudaSuccess)
+    e = MRAID_PROF(pl, K_ARPLS,
+                   launch_arpls(pl, pl->bp_y, n_sys, pl->p.n_chan, bp->lam, bp->ratio,
+                                bp->itermax, pl->bp_z, d_bandpass, pl->bp_iters, pl->ar_work));
+  if (e == cudaSuccess)
+    e = MRAID_PROF(pl, K_CCM_BP,
+                   launch_ccm_bandpass(pl, pl->ws.sums, inter, interval, pl->bp_z, pl->ws.corr));
+  if (e != cudaSuccess) return cuda_fail(e, "bandpass kernels");
+  e = MRAID_PROF(pl, K_EIG, launch_eig(pl, pl->ws.corr, pl->n_cells, d_evals, d_q1, d_stat));
+  if (e != cudaSuccess) return cuda_fail(e, "eig launch");
+  e = MRAID_PROF(pl, K_FLAG, launch_flag(pl, d_stat, d_flags));
+  if (e != cudaSuccess) return cuda_fail(e, "flag launch");
+  e = cudaMemcpyAsync(&pl->d_info->n_degenerate, pl->d_degenerate, sizeof(int64_t),
+                      cudaMemcpyDeviceToDevice, pl->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&pl->d_info->jacobi_sweeps, pl->d_sweeps, 2 * sizeof(int64_t),
+                        cudaMemcpyDeviceToDevice, pl->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "counter copy");
+  return enqueue_info_copy(pl, info);
+}

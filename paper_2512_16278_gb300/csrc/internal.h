@@ -117,6 +117,25 @@ struct mraid_plan_s {
 namespace mraid {
 
 void set_error(const char* fmt, ...);
+// plan.cu helpers shared by the entry points of the other files
+constexpr int kMaxSubPerLaunch = 32768;  // sub-integrations per Gram launch (grid.y bound)
+mraid_status check_plan(mraid_plan_t pl);
+mraid_status ensure_tri_workspace(mraid_plan_s* pl, size_t cells);
+// the plan's sums and correlation buffers (and the eigensolver's) for `cells`
+mraid_status ensure_workspace(mraid_plan_s* pl, size_t cells);
+// eigenvalue buffer for the q1 pass when the caller wants q1 but not evals
+mraid_status evals_for_q1(mraid_plan_s* pl, size_t cells, float** evals);
+// Gram sums + correlation of sub-integrations [sub0, sub0 + n_sub) of d_data
+// (either output may be null; cells relative to sub0)
+mraid_status ccm_range(mraid_plan_s* pl, const void* d_data, int sub0, int n_sub,
+                       int64_t* d_sums, float* d_corr);
+// copy the device masking report to the caller's struct at the next sync
+mraid_status enqueue_info_copy(mraid_plan_s* pl, mraid_flag_info* info);
+// one pass over 8-bit samples: the Gram sums of every sub-integration into
+// ws.sums (interleaved by 8 channels when the tensor cores form them), and
+// the correlation into d_corr when it is not null
+mraid_status gram_sums_pass(mraid_plan_s* pl, const void* d_data, float* d_corr,
+                            bool* interleaved);
 // Allocate every work buffer mraid_run can need (so later calls allocate
 // nothing, e.g. inside a stream capture).
 mraid_status plan_prepare(mraid_plan_s* pl);
@@ -125,6 +144,16 @@ void plan_deliver_info(mraid_plan_s* pl);
 // Bracket a kernel launch with profiling events (no-ops unless enabled).
 void prof_begin(mraid_plan_s* pl, int id, cudaEvent_t* start, cudaStream_t stream);
 void prof_end(mraid_plan_s* pl, int id, cudaEvent_t start, cudaStream_t stream);
+// run expr (a launch returning cudaError_t) between profiling events
+#define MRAID_PROF_ON(pl, id, stream, expr)   \
+  ([&]() {                                    \
+    cudaEvent_t s_;                           \
+    mraid::prof_begin((pl), (id), &s_, (stream)); \
+    cudaError_t e_ = (expr);                  \
+    mraid::prof_end((pl), (id), s_, (stream));    \
+    return e_;                                \
+  }())
+#define MRAID_PROF(pl, id, expr) MRAID_PROF_ON(pl, id, (pl)->stream, expr)
 mraid_status cuda_fail(cudaError_t e, const char* what);
 
 // gram.cu

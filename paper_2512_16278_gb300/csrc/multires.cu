@@ -68,3 +68,136 @@ cudaError_t launch_gram_aggregate(const mraid_plan_s* pl, const int64_t* d_src, 
 }
 
 }  // namespace mraid
+
+// ---------------------------------------------------------------------------
+// Entry points (include/mraid.h)
+
+using namespace mraid;
+
+mraid_status mraid_multires(mraid_plan_t pl, const void* d_data, int32_t n_levels,
+                            const int32_t* factors, float* const* d_stats,
+                            uint8_t* const* d_flags, mraid_flag_info* infos) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  if (!d_data || !factors || !d_stats || !d_flags || n_levels < 1 || n_levels > kMaxLevels) {
+    set_error("mraid_multires: d_data, factors, d_stats and d_flags are required; n_levels in 1..%d",
+              kMaxLevels);
+    return MRAID_ERR_INVALID_ARG;
+  }
+  if (pl->p.bit_depth != 8) {
+    set_error("mraid_multires: exact Gram sums exist for 8-bit samples only");
+    return MRAID_ERR_UNSUPPORTED;
+  }
+  const int n_sub = pl->p.n_sub, n_chan = pl->p.n_chan;
+  int order[kMaxLevels];
+  for (int i = 0; i < n_levels; ++i) {
+    const int f = factors[i];
+    if (f < 1 || f > n_sub || !d_stats[i] || !d_flags[i]) {
+      set_error("mraid_multires: level %d: factor %d outside 1..%d or a NULL output", i, f, n_sub);
+      return MRAID_ERR_INVALID_ARG;
+    }
+    for (int j = 0; j < i; ++j)
+      if (factors[j] == f) {
+        set_error("mraid_multires: factor %d given twice", f);
+        return MRAID_ERR_INVALID_ARG;
+      }
+    // insertion into ascending factor order
+    int k = i;
+    while (k > 0 && factors[order[k - 1]] > f) {
+      order[k] = order[k - 1];
+      --k;
+    }
+    order[k] = i;
+  }
+  // sums of the longer levels, one after another in ml_sums
+  const int64_t per_sub = (int64_t)n_chan * pl->psum;
+  size_t off[kMaxLevels] = {};
+  size_t need = 0;
+  for (int i = 0; i < n_levels; ++i)
+    if (factors[i] > 1) {
+      off[i] = need;
+      need += (size_t)(n_sub / factors[i]) * (size_t)per_sub;
+      need = (need + 1) & ~size_t(1);  // keep every level 16-byte aligned
+    }
+  st = ensure_workspace(pl, (size_t)pl->n_cells);
+  if (st != MRAID_OK) return st;
+  cudaError_t e = cudaSuccess;
+  if (need > pl->ml_sums_elems) {
+    cudaFree(pl->ml_sums);
+    pl->ml_sums = nullptr;
+    pl->ml_sums_elems = 0;
+    e = cudaMalloc(&pl->ml_sums, need * sizeof(int64_t));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_fail(e, "multires sums allocation");
+    }
+    pl->ml_sums_elems = need;
+  }
+  if (!pl->d_ml_info) {
+    e = cudaMalloc(&pl->d_ml_info, kMaxLevels * sizeof(mraid_flag_info));
+    if (e == cudaSuccess) e = cudaMallocHost(&pl->h_ml_info, kMaxLevels * sizeof(mraid_flag_info));
+    if (e != cudaSuccess) {
+      cudaFree(pl->d_ml_info);
+      pl->d_ml_info = nullptr;
+      cudaGetLastError();
+      return cuda_fail(e, "multires report allocation");
+    }
+  }
+  auto reset_counters = [&]() {
+    cudaError_t r = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
+    if (r == cudaSuccess)
+      r = cudaMemsetAsync(pl->d_sweeps, 0, 2 * sizeof(unsigned long long), pl->stream);
+    return r;
+  };
+  e = cudaMemsetAsync(pl->d_ml_info, 0, (size_t)n_levels * sizeof(mraid_flag_info), pl->stream);
+  if (e == cudaSuccess) e = reset_counters();
+  if (e != cudaSuccess) return cuda_fail(e, "memset");
+  // the one pass over the samples: Gram sums of every sub-integration, and
+  // the correlation too when the plan's own length is a level; the
+  // aggregation adds whole sub-integrations, so it does not depend on the
+  // sums' layout, and the correlation kernel reads either
+  const bool has1 = factors[order[0]] == 1;
+  bool inter = false;
+  st = gram_sums_pass(pl, d_data, has1 ? pl->ws.corr : nullptr, &inter);
+  if (st != MRAID_OK) return st;
+  for (int li = 0; li < n_levels; ++li) {
+    const int i = order[li], f = factors[i];
+    const int n_f = n_sub / f;
+    const int64_t cells = (int64_t)n_f * n_chan;
+    if (f > 1) {
+      // source: the longest level already formed whose length divides f
+      int g = 1;
+      const int64_t* src = pl->ws.sums;
+      for (int lj = 0; lj < li; ++lj) {
+        const int j = order[lj];
+        if (factors[j] > g && f % factors[j] == 0) {
+          g = factors[j];
+          src = pl->ml_sums + off[j];
+        }
+      }
+      int64_t* dst = pl->ml_sums + off[i];
+      e = reset_counters();
+      if (e == cudaSuccess)
+        e = MRAID_PROF(pl, K_AGG, launch_gram_aggregate(pl, src, dst, n_f, f / g));
+      if (e == cudaSuccess)
+        e = MRAID_PROF(pl, K_CORR, launch_corr_from_sums(pl, dst, cells, pl->ws.corr, inter));
+      if (e != cudaSuccess) return cuda_fail(e, "multires sums");
+    }
+    e = MRAID_PROF(pl, K_EIG, launch_eig(pl, pl->ws.corr, cells, nullptr, nullptr, d_stats[i]));
+    if (e != cudaSuccess) return cuda_fail(e, "eig launch");
+    e = MRAID_PROF(pl, K_FLAG, launch_flag(pl, d_stats[i], d_flags[i], cells, pl->d_ml_info + i));
+    if (e != cudaSuccess) return cuda_fail(e, "flag launch");
+    e = cudaMemcpyAsync(&pl->d_ml_info[i].n_degenerate, pl->d_degenerate, sizeof(int64_t),
+                        cudaMemcpyDeviceToDevice, pl->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&pl->d_ml_info[i].jacobi_sweeps, pl->d_sweeps, 2 * sizeof(int64_t),
+                          cudaMemcpyDeviceToDevice, pl->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "counter copy");
+  }
+  e = cudaMemcpyAsync(pl->h_ml_info, pl->d_ml_info, (size_t)n_levels * sizeof(mraid_flag_info),
+                      cudaMemcpyDeviceToHost, pl->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "info copy");
+  pl->pending_ml = infos;
+  pl->pending_ml_n = infos ? n_levels : 0;
+  return MRAID_OK;
+}

@@ -86,20 +86,8 @@ static void prof_fold(mraid_plan_s* pl) {
   pl->prof.pending.clear();
 }
 
-#define MRAID_PROF_ON(pl, id, stream, expr)   \
-  ([&]() {                                    \
-    cudaEvent_t s_;                           \
-    prof_begin((pl), (id), &s_, (stream));    \
-    cudaError_t e_ = (expr);                  \
-    prof_end((pl), (id), s_, (stream));       \
-    return e_;                                \
-  }())
-#define MRAID_PROF(pl, id, expr) MRAID_PROF_ON(pl, id, (pl)->stream, expr)
 
-namespace {
-
-// Sub-integrations per gram launch (grid.y bound) and per host-path chunk.
-constexpr int kMaxSubPerLaunch = 32768;
+// Plan helpers shared with the entry points of the other files (internal.h).
 
 // Workspace of the tridiagonal eigensolver, for beam counts it serves.
 mraid_status ensure_tri_workspace(mraid_plan_s* pl, size_t cells) {
@@ -235,7 +223,22 @@ mraid_status enqueue_info_copy(mraid_plan_s* pl, mraid_flag_info* info) {
   return MRAID_OK;
 }
 
-}  // namespace
+// One pass over 8-bit samples for the paths that need the Gram sums: the
+// int64 sums of every sub-integration into ws.sums (and the correlation
+// into d_corr when it is not null). The tensor-core kernel writes the sums
+// interleaved by 8 channels ([cell / 8][P][cell % 8], 64-byte store runs;
+// *interleaved = true); otherwise they are [cell][P].
+mraid_status gram_sums_pass(mraid_plan_s* pl, const void* d_data, float* d_corr,
+                            bool* interleaved) {
+  *interleaved = !pl->force_dp4a && gram_tc_supported(pl, d_data);
+  if (*interleaved) {
+    cudaError_t e = MRAID_PROF(pl, K_GRAM_TC,
+                               launch_gram_tc(pl, static_cast<const uint8_t*>(d_data), 0,
+                                              pl->p.n_sub, nullptr, d_corr, pl->ws.sums));
+    return e == cudaSuccess ? MRAID_OK : cuda_fail(e, "gram_tc launch");
+  }
+  return ccm_range(pl, d_data, 0, pl->p.n_sub, pl->ws.sums, d_corr);
+}
 
 mraid_status plan_prepare(mraid_plan_s* pl) {
   mraid_status st = ensure_workspace(pl, (size_t)pl->n_cells);
@@ -509,427 +512,6 @@ mraid_status mraid_run(mraid_plan_t pl, const void* d_data, float* d_evals, floa
   return enqueue_info_copy(pl, info);
 }
 
-namespace mraid {
-namespace {
-// One pass over 8-bit samples for the paths that need the Gram sums: the
-// int64 sums of every sub-integration into ws.sums (and the correlation
-// into d_corr when it is not null). The tensor-core kernel writes the sums
-// interleaved by 8 channels ([cell / 8][P][cell % 8], 64-byte store runs;
-// *interleaved = true); otherwise they are [cell][P].
-mraid_status gram_sums_pass(mraid_plan_s* pl, const void* d_data, float* d_corr,
-                            bool* interleaved) {
-  *interleaved = !pl->force_dp4a && gram_tc_supported(pl, d_data);
-  if (*interleaved) {
-    cudaError_t e = MRAID_PROF(pl, K_GRAM_TC,
-                               launch_gram_tc(pl, static_cast<const uint8_t*>(d_data), 0,
-                                              pl->p.n_sub, nullptr, d_corr, pl->ws.sums));
-    return e == cudaSuccess ? MRAID_OK : cuda_fail(e, "gram_tc launch");
-  }
-  return ccm_range(pl, d_data, 0, pl->p.n_sub, pl->ws.sums, d_corr);
-}
-
-mraid_status check_bandpass_params(const mraid_bandpass_params* bp) {
-  if (!bp || !(bp->lam > 0.0) || !(bp->lam < 1e300) || !(bp->ratio > 0.0) || bp->itermax < 1 ||
-      bp->itermax > 1000 || bp->interval < 1) {
-    set_error("bandpass parameters: lam > 0, ratio > 0, itermax in 1..1000, interval >= 1");
-    return MRAID_ERR_INVALID_ARG;
-  }
-  return MRAID_OK;
-}
-
-// ArPLS arrays in global memory for spectra too long for shared memory
-mraid_status ensure_arpls_work(mraid_plan_s* pl, int n, int n_sys) {
-  const size_t need = arpls_work_doubles(n, n_sys);
-  if (need <= pl->ar_work_elems) return MRAID_OK;
-  cudaFree(pl->ar_work);
-  pl->ar_work = nullptr;
-  pl->ar_work_elems = 0;
-  cudaError_t e = cudaMalloc(&pl->ar_work, need * sizeof(double));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return cuda_fail(e, "arpls work allocation");
-  }
-  pl->ar_work_elems = need;
-  return MRAID_OK;
-}
-}  // namespace
-}  // namespace mraid
-
-namespace mraid {
-namespace {
-// True when the tensor-core Gram takes a two-polarisation block whole: it
-// adds the polarisations in its converter and the pieces of each
-// sub-integration in its epilogue, so it writes the total power's sums
-// and correlation directly.
-bool pol2_on_tensor_cores(const mraid_plan_s* pl, const void* d_data) {
-  return !pl->force_dp4a && pl->p.bit_depth == 8 && gram_tc_supported(pl, d_data, 2);
-}
-
-// Otherwise: the exact 8-bit Gram of the 2N stacked blocks (a plan view
-// with 2N beams), folded into the total power's sums [cell][P] in d_sums.
-mraid_status pol2_stacked_sums(mraid_plan_s* pl, const void* d_data, int64_t* d_sums) {
-  const int N = pl->p.n_beam;
-  const int P2 = (2 * N + 1) * (2 * N + 2) / 2;
-  const size_t need = (size_t)pl->n_cells * P2;
-  if (need > pl->pol_cells) {  // pol_cells counts int64 elements
-    cudaFree(pl->pol_sums);
-    pl->pol_sums = nullptr;
-    pl->pol_cells = 0;
-    cudaError_t e = cudaMalloc(&pl->pol_sums, need * sizeof(int64_t));
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return cuda_fail(e, "two-polarisation workspace allocation");
-    }
-    pl->pol_cells = need;
-  }
-  mraid_plan_s v;
-  v.p = pl->p;
-  v.p.n_beam = 2 * N;
-  v.p.keep = nullptr;
-  v.device = pl->device;
-  v.sm_count = pl->sm_count;
-  v.stream = pl->stream;
-  v.n_cells = pl->n_cells;
-  v.beam_stride = pl->beam_stride;
-  v.np = 2 * N * (2 * N + 1) / 2;
-  v.psum = P2;
-  v.d_degenerate = pl->d_degenerate;
-  v.d_error = pl->d_error;
-  v.force_dp4a = pl->force_dp4a;
-  v.tc_variant = tc_default_variant(2 * N);
-  cudaError_t e = cudaSuccess;
-  if (!v.force_dp4a && gram_tc_supported(&v, d_data)) {
-    e = MRAID_PROF(pl, K_GRAM_TC,
-                   launch_gram_tc(&v, static_cast<const uint8_t*>(d_data), 0, v.p.n_sub,
-                                  pl->pol_sums, nullptr));
-  } else {
-    for (int s = 0; s < v.p.n_sub && e == cudaSuccess; s += kMaxSubPerLaunch) {
-      const int ns = (v.p.n_sub - s) < kMaxSubPerLaunch ? (v.p.n_sub - s) : kMaxSubPerLaunch;
-      e = MRAID_PROF(pl, K_GRAM,
-                     launch_gram_u8(&v, static_cast<const uint8_t*>(d_data), s, ns,
-                                    pl->pol_sums + (int64_t)s * v.p.n_chan * P2));
-    }
-  }
-  if (e == cudaSuccess)
-    e = MRAID_PROF(pl, K_POL2_FOLD, launch_pol2_fold(pl, pl->pol_sums, pl->n_cells, d_sums));
-  return e == cudaSuccess ? MRAID_OK : cuda_fail(e, "two-polarisation Gram");
-}
-
-mraid_status check_pol2(const mraid_plan_s* pl) {
-  if (pl->p.bit_depth != 8 || 2 * pl->p.n_beam > kMaxBeam) {
-    set_error("two polarisations: 8-bit samples and at most %d beams", kMaxBeam / 2);
-    return MRAID_ERR_UNSUPPORTED;
-  }
-  return MRAID_OK;
-}
-
-// Sums ([cell][P], may be null) and correlation (may be null) of the
-// total power of a two-polarisation block; counts zero-variance beams.
-mraid_status pol2_ccm(mraid_plan_s* pl, const void* d_data, int64_t* d_sums, float* d_corr) {
-  cudaError_t e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "memset");
-  if (pol2_on_tensor_cores(pl, d_data)) {
-    e = MRAID_PROF(pl, K_GRAM_TC,
-                   launch_gram_tc(pl, static_cast<const uint8_t*>(d_data), 0, pl->p.n_sub, d_sums,
-                                  d_corr, nullptr, 2));
-    return e == cudaSuccess ? MRAID_OK : cuda_fail(e, "gram_tc launch");
-  }
-  int64_t* sums = d_sums;
-  if (!sums) {
-    mraid_status st = ensure_workspace(pl, (size_t)pl->n_cells);
-    if (st != MRAID_OK) return st;
-    sums = pl->ws.sums;
-  }
-  mraid_status st = pol2_stacked_sums(pl, d_data, sums);
-  if (st != MRAID_OK) return st;
-  if (d_corr) {
-    // the stacked Gram's own counts are of the 2N blocks: count again
-    e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
-    if (e == cudaSuccess)
-      e = MRAID_PROF(pl, K_CORR, launch_corr_from_sums(pl, sums, pl->n_cells, d_corr));
-    if (e != cudaSuccess) return cuda_fail(e, "corr launch");
-  }
-  return MRAID_OK;
-}
-}  // namespace
-}  // namespace mraid
-
-mraid_status mraid_ccm_pol2(mraid_plan_t pl, const void* d_data, int64_t* d_sums,
-                            float* d_corr) {
-  mraid_status st = check_plan(pl);
-  if (st != MRAID_OK) return st;
-  if (!d_data || (!d_sums && !d_corr)) {
-    set_error("mraid_ccm_pol2: d_data and one of d_sums, d_corr are required");
-    return MRAID_ERR_INVALID_ARG;
-  }
-  st = check_pol2(pl);
-  if (st != MRAID_OK) return st;
-  return pol2_ccm(pl, d_data, d_sums, d_corr);
-}
-
-mraid_status mraid_run_pol2(mraid_plan_t pl, const void* d_data, float* d_evals, float* d_q1,
-                            float* d_stat, uint8_t* d_flags, mraid_flag_info* info) {
-  mraid_status st = check_plan(pl);
-  if (st != MRAID_OK) return st;
-  if (!d_data || !d_stat || !d_flags) {
-    set_error("mraid_run_pol2: d_data, d_stat and d_flags are required");
-    return MRAID_ERR_INVALID_ARG;
-  }
-  st = check_pol2(pl);
-  if (st != MRAID_OK) return st;
-  st = ensure_workspace(pl, (size_t)pl->n_cells);
-  if (st != MRAID_OK) return st;
-  if (d_q1) {
-    st = evals_for_q1(pl, (size_t)pl->n_cells, &d_evals);
-    if (st != MRAID_OK) return st;
-  }
-  cudaError_t e = cudaMemsetAsync(pl->d_sweeps, 0, 2 * sizeof(unsigned long long), pl->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "memset");
-  st = pol2_ccm(pl, d_data, nullptr, pl->ws.corr);
-  if (st != MRAID_OK) return st;
-  e = MRAID_PROF(pl, K_EIG, launch_eig(pl, pl->ws.corr, pl->n_cells, d_evals, d_q1, d_stat));
-  if (e != cudaSuccess) return cuda_fail(e, "eig launch");
-  e = MRAID_PROF(pl, K_FLAG, launch_flag(pl, d_stat, d_flags));
-  if (e != cudaSuccess) return cuda_fail(e, "flag launch");
-  e = cudaMemcpyAsync(&pl->d_info->n_degenerate, pl->d_degenerate, sizeof(int64_t),
-                      cudaMemcpyDeviceToDevice, pl->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&pl->d_info->jacobi_sweeps, pl->d_sweeps, 2 * sizeof(int64_t),
-                        cudaMemcpyDeviceToDevice, pl->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "counter copy");
-  return enqueue_info_copy(pl, info);
-}
-
-void mraid_default_bandpass_params(mraid_bandpass_params* bp) {
-  if (!bp) return;
-  bp->lam = 1e5;
-  bp->ratio = 1e-3;
-  bp->itermax = 50;
-  bp->interval = 20;
-}
-
-mraid_status mraid_arpls(mraid_plan_t pl, const double* d_y, int32_t n_sys, int32_t n,
-                         const mraid_bandpass_params* bp, double* d_z, int32_t* d_iters) {
-  mraid_status st = check_plan(pl);
-  if (st != MRAID_OK) return st;
-  st = check_bandpass_params(bp);
-  if (st != MRAID_OK) return st;
-  if (!d_y || !d_z || n < 3 || n > (1 << 20) || n_sys < 0) {
-    set_error("mraid_arpls: d_y and d_z are required, 3 <= n <= 2^20, n_sys >= 0");
-    return MRAID_ERR_INVALID_ARG;
-  }
-  st = ensure_arpls_work(pl, n, n_sys);
-  if (st != MRAID_OK) return st;
-  cudaError_t e = MRAID_PROF(pl, K_ARPLS,
-                             launch_arpls(pl, d_y, n_sys, n, bp->lam, bp->ratio, bp->itermax, d_z,
-                                          nullptr, d_iters, pl->ar_work));
-  return e == cudaSuccess ? MRAID_OK : cuda_fail(e, "arpls launch");
-}
-
-mraid_status mraid_run_bandpass(mraid_plan_t pl, const void* d_data,
-                                const mraid_bandpass_params* bp, float* d_bandpass,
-                                float* d_evals, float* d_q1, float* d_stat, uint8_t* d_flags,
-                                mraid_flag_info* info) {
-  mraid_status st = check_plan(pl);
-  if (st != MRAID_OK) return st;
-  st = check_bandpass_params(bp);
-  if (st != MRAID_OK) return st;
-  if (!d_data || !d_stat || !d_flags) {
-    set_error("mraid_run_bandpass: d_data, d_stat and d_flags are required");
-    return MRAID_ERR_INVALID_ARG;
-  }
-  if (pl->p.bit_depth != 8 || pl->p.n_chan < 3 || pl->p.n_chan > (1 << 20)) {
-    set_error("mraid_run_bandpass: 8-bit samples and 3 to 2^20 channels");
-    return MRAID_ERR_UNSUPPORTED;
-  }
-  const int interval = bp->interval;
-  const int n_int = (pl->p.n_sub + interval - 1) / interval;
-  const int n_sys = n_int * pl->p.n_beam;
-  const size_t elems = (size_t)n_sys * pl->p.n_chan;
-  st = ensure_workspace(pl, (size_t)pl->n_cells);
-  if (st != MRAID_OK) return st;
-  cudaError_t e = cudaSuccess;
-  if (elems > pl->bp_elems || (size_t)n_sys > pl->bp_sys) {
-    cudaFree(pl->bp_y);
-    cudaFree(pl->bp_z);
-    cudaFree(pl->bp_iters);
-    pl->bp_y = pl->bp_z = nullptr;
-    pl->bp_iters = nullptr;
-    pl->bp_elems = pl->bp_sys = 0;
-    e = cudaMalloc(&pl->bp_y, elems * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&pl->bp_z, elems * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&pl->bp_iters, (size_t)n_sys * sizeof(int32_t));
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return cuda_fail(e, "bandpass workspace allocation");
-    }
-    pl->bp_elems = elems;
-    pl->bp_sys = (size_t)n_sys;
-  }
-  st = ensure_arpls_work(pl, pl->p.n_chan, n_sys);
-  if (st != MRAID_OK) return st;
-  if (d_q1) {
-    st = evals_for_q1(pl, (size_t)pl->n_cells, &d_evals);
-    if (st != MRAID_OK) return st;
-  }
-  e = cudaMemsetAsync(pl->d_sweeps, 0, 2 * sizeof(unsigned long long), pl->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "memset");
-  bool inter = false;
-  st = gram_sums_pass(pl, d_data, nullptr, &inter);
-  if (st != MRAID_OK) return st;
-  // the sums pass may count zero-variance beams; nothing is normalised here
-  e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
-  if (e == cudaSuccess)
-    e = MRAID_PROF(pl, K_BP_INPUT,
-                   launch_bandpass_input(pl, pl->ws.sums, inter, interval, pl->bp_y));
-  if (e == cudaSuccess)
-    e = MRAID_PROF(pl, K_ARPLS,
-                   launch_arpls(pl, pl->bp_y, n_sys, pl->p.n_chan, bp->lam, bp->ratio,
-                                bp->itermax, pl->bp_z, d_bandpass, pl->bp_iters, pl->ar_work));
-  if (e == cudaSuccess)
-    e = MRAID_PROF(pl, K_CCM_BP,
-                   launch_ccm_bandpass(pl, pl->ws.sums, inter, interval, pl->bp_z, pl->ws.corr));
-  if (e != cudaSuccess) return cuda_fail(e, "bandpass kernels");
-  e = MRAID_PROF(pl, K_EIG, launch_eig(pl, pl->ws.corr, pl->n_cells, d_evals, d_q1, d_stat));
-  if (e != cudaSuccess) return cuda_fail(e, "eig launch");
-  e = MRAID_PROF(pl, K_FLAG, launch_flag(pl, d_stat, d_flags));
-  if (e != cudaSuccess) return cuda_fail(e, "flag launch");
-  e = cudaMemcpyAsync(&pl->d_info->n_degenerate, pl->d_degenerate, sizeof(int64_t),
-                      cudaMemcpyDeviceToDevice, pl->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&pl->d_info->jacobi_sweeps, pl->d_sweeps, 2 * sizeof(int64_t),
-                        cudaMemcpyDeviceToDevice, pl->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "counter copy");
-  return enqueue_info_copy(pl, info);
-}
-
-mraid_status mraid_multires(mraid_plan_t pl, const void* d_data, int32_t n_levels,
-                            const int32_t* factors, float* const* d_stats,
-                            uint8_t* const* d_flags, mraid_flag_info* infos) {
-  mraid_status st = check_plan(pl);
-  if (st != MRAID_OK) return st;
-  if (!d_data || !factors || !d_stats || !d_flags || n_levels < 1 || n_levels > kMaxLevels) {
-    set_error("mraid_multires: d_data, factors, d_stats and d_flags are required; n_levels in 1..%d",
-              kMaxLevels);
-    return MRAID_ERR_INVALID_ARG;
-  }
-  if (pl->p.bit_depth != 8) {
-    set_error("mraid_multires: exact Gram sums exist for 8-bit samples only");
-    return MRAID_ERR_UNSUPPORTED;
-  }
-  const int n_sub = pl->p.n_sub, n_chan = pl->p.n_chan;
-  int order[kMaxLevels];
-  for (int i = 0; i < n_levels; ++i) {
-    const int f = factors[i];
-    if (f < 1 || f > n_sub || !d_stats[i] || !d_flags[i]) {
-      set_error("mraid_multires: level %d: factor %d outside 1..%d or a NULL output", i, f, n_sub);
-      return MRAID_ERR_INVALID_ARG;
-    }
-    for (int j = 0; j < i; ++j)
-      if (factors[j] == f) {
-        set_error("mraid_multires: factor %d given twice", f);
-        return MRAID_ERR_INVALID_ARG;
-      }
-    // insertion into ascending factor order
-    int k = i;
-    while (k > 0 && factors[order[k - 1]] > f) {
-      order[k] = order[k - 1];
-      --k;
-    }
-    order[k] = i;
-  }
-  // sums of the longer levels, one after another in ml_sums
-  const int64_t per_sub = (int64_t)n_chan * pl->psum;
-  size_t off[kMaxLevels] = {};
-  size_t need = 0;
-  for (int i = 0; i < n_levels; ++i)
-    if (factors[i] > 1) {
-      off[i] = need;
-      need += (size_t)(n_sub / factors[i]) * (size_t)per_sub;
-      need = (need + 1) & ~size_t(1);  // keep every level 16-byte aligned
-    }
-  st = ensure_workspace(pl, (size_t)pl->n_cells);
-  if (st != MRAID_OK) return st;
-  cudaError_t e = cudaSuccess;
-  if (need > pl->ml_sums_elems) {
-    cudaFree(pl->ml_sums);
-    pl->ml_sums = nullptr;
-    pl->ml_sums_elems = 0;
-    e = cudaMalloc(&pl->ml_sums, need * sizeof(int64_t));
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return cuda_fail(e, "multires sums allocation");
-    }
-    pl->ml_sums_elems = need;
-  }
-  if (!pl->d_ml_info) {
-    e = cudaMalloc(&pl->d_ml_info, kMaxLevels * sizeof(mraid_flag_info));
-    if (e == cudaSuccess) e = cudaMallocHost(&pl->h_ml_info, kMaxLevels * sizeof(mraid_flag_info));
-    if (e != cudaSuccess) {
-      cudaFree(pl->d_ml_info);
-      pl->d_ml_info = nullptr;
-      cudaGetLastError();
-      return cuda_fail(e, "multires report allocation");
-    }
-  }
-  auto reset_counters = [&]() {
-    cudaError_t r = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
-    if (r == cudaSuccess)
-      r = cudaMemsetAsync(pl->d_sweeps, 0, 2 * sizeof(unsigned long long), pl->stream);
-    return r;
-  };
-  e = cudaMemsetAsync(pl->d_ml_info, 0, (size_t)n_levels * sizeof(mraid_flag_info), pl->stream);
-  if (e == cudaSuccess) e = reset_counters();
-  if (e != cudaSuccess) return cuda_fail(e, "memset");
-  // the one pass over the samples: Gram sums of every sub-integration, and
-  // the correlation too when the plan's own length is a level; the
-  // aggregation adds whole sub-integrations, so it does not depend on the
-  // sums' layout, and the correlation kernel reads either
-  const bool has1 = factors[order[0]] == 1;
-  bool inter = false;
-  st = gram_sums_pass(pl, d_data, has1 ? pl->ws.corr : nullptr, &inter);
-  if (st != MRAID_OK) return st;
-  for (int li = 0; li < n_levels; ++li) {
-    const int i = order[li], f = factors[i];
-    const int n_f = n_sub / f;
-    const int64_t cells = (int64_t)n_f * n_chan;
-    if (f > 1) {
-      // source: the longest level already formed whose length divides f
-      int g = 1;
-      const int64_t* src = pl->ws.sums;
-      for (int lj = 0; lj < li; ++lj) {
-        const int j = order[lj];
-        if (factors[j] > g && f % factors[j] == 0) {
-          g = factors[j];
-          src = pl->ml_sums + off[j];
-        }
-      }
-      int64_t* dst = pl->ml_sums + off[i];
-      e = reset_counters();
-      if (e == cudaSuccess)
-        e = MRAID_PROF(pl, K_AGG, launch_gram_aggregate(pl, src, dst, n_f, f / g));
-      if (e == cudaSuccess)
-        e = MRAID_PROF(pl, K_CORR, launch_corr_from_sums(pl, dst, cells, pl->ws.corr, inter));
-      if (e != cudaSuccess) return cuda_fail(e, "multires sums");
-    }
-    e = MRAID_PROF(pl, K_EIG, launch_eig(pl, pl->ws.corr, cells, nullptr, nullptr, d_stats[i]));
-    if (e != cudaSuccess) return cuda_fail(e, "eig launch");
-    e = MRAID_PROF(pl, K_FLAG, launch_flag(pl, d_stats[i], d_flags[i], cells, pl->d_ml_info + i));
-    if (e != cudaSuccess) return cuda_fail(e, "flag launch");
-    e = cudaMemcpyAsync(&pl->d_ml_info[i].n_degenerate, pl->d_degenerate, sizeof(int64_t),
-                        cudaMemcpyDeviceToDevice, pl->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(&pl->d_ml_info[i].jacobi_sweeps, pl->d_sweeps, 2 * sizeof(int64_t),
-                          cudaMemcpyDeviceToDevice, pl->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "counter copy");
-  }
-  e = cudaMemcpyAsync(pl->h_ml_info, pl->d_ml_info, (size_t)n_levels * sizeof(mraid_flag_info),
-                      cudaMemcpyDeviceToHost, pl->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "info copy");
-  pl->pending_ml = infos;
-  pl->pending_ml_n = infos ? n_levels : 0;
-  return MRAID_OK;
-}
 
 mraid_status mraid_run_host(mraid_plan_t pl, const void* h_data, float* h_stat, uint8_t* h_flags,
                             mraid_flag_info* info) {
