@@ -493,17 +493,19 @@ constexpr int kMaxQrIter = 24;  // QR steps per eigenvalue (the shift converges 
 // One implicit symmetric QR step with the Wilkinson shift on the unreduced
 // block [l, m] of the tridiagonal (d, e); dm1, dm, em are d[m-1], d[m],
 // e[m-1]. The bulge is chased down with plane rotations; steps outside
-// [l, m) are skipped per lane.
-template <int N>
+// [l, m) are skipped per lane. The code covers the rotation positions
+// 0..K-1, so it serves every block with m <= K.
+template <int N, int K = N - 1>
 __device__ __forceinline__ void qr_step(float (&d)[N], float (&e)[N], int l, int m, float dm1,
                                         float dm, float em) {
+  static_assert(K >= 1 && K <= N - 1, "rotation positions");
   // the eigenvalue of the trailing 2x2 nearer d[m]
   const float dl = 0.5f * (dm1 - dm);
   const float r2s = fmaf(dl, dl, em * em);
   const float rr = r2s * rsqrtf(r2s);  // em != 0 here, so r2s > 0
   const float mu = dm - __fdividef(em * em, dl + (dl >= 0.f ? rr : -rr));
   float x = 0.f, z = 0.f;
-  static_for<N - 1>([&](auto kk) {
+  static_for<K>([&](auto kk) {
     constexpr int k = decltype(kk)::value;
     if (k >= l && k < m) {
       if (k == l) {
@@ -668,8 +670,24 @@ eig_tri_kernel(const float* __restrict__ corr, int64_t n_cells, float* __restric
       });
       const bool need = active && m > 0;
       if (!__any_sync(0xffffffffu, need)) break;
+      // The lowest unreduced block moves up as eigenvalues deflate; the
+      // warp's deepest block bounds the positions a step can touch, so
+      // copies of the step over the first third and two thirds of the
+      // positions serve the later steps (same arithmetic, fewer masked
+      // positions issued).
+      const int mw = __reduce_max_sync(0xffffffffu, need ? m : 0);
       if (need) {
-        qr_step<N>(d, e, l, m, dm1, dm, em);
+        if constexpr (N - 1 >= 6) {
+          constexpr int K1 = (N - 1) / 3, K2 = 2 * (N - 1) / 3;
+          if (mw <= K1)
+            qr_step<N, K1>(d, e, l, m, dm1, dm, em);
+          else if (mw <= K2)
+            qr_step<N, K2>(d, e, l, m, dm1, dm, em);
+          else
+            qr_step<N>(d, e, l, m, dm1, dm, em);
+        } else {
+          qr_step<N>(d, e, l, m, dm1, dm, em);
+        }
         ++steps;
       }
     }
