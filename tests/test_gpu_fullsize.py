@@ -155,3 +155,59 @@ def test_fast_block_bandpass_path(fast_block):
             C = oracle.cell_ccm_bandpass(data, cfg.n_samp_sub, k, c, z[:, c])
             so = oracle.stat(oracle.jacobi(C)[0])
             assert abs(stat[k * cfg.n_chan + c] - so) <= STAT_TOL * so, (I, k, c)
+
+
+def test_fast_block_two_polarisations(fast_block):
+    """Two recorded polarisations at full size (31.9 GB on the device): the
+    block as polarisation 0 and the next seed's block as polarisation 1,
+    through mraid_run_pol2 on the tensor cores, the launch the benchmark
+    times. Sampled cells against the oracle's total-power path, the masking
+    properties, the beam-common narrowband RFI of either polarisation
+    flagged and single-beam pulses away from any other event not."""
+    import torch
+    m = lib()
+    cfg, h = fast_block
+    nb = cfg.nbytes
+    cfg1 = cfg.replace(seed=cfg.seed + 1)
+    h2 = torch.empty(2 * nb, dtype=torch.uint8, pin_memory=True)
+    h2[:nb].copy_(h)
+    synth.generate(cfg1, out_ptr=h2.data_ptr() + nb)
+    d = h2.to("cuda", non_blocking=False)
+    with m.Plan(cfg.n_beam, cfg.n_chan, cfg.n_samp_sub, cfg.n_sub) as plan:
+        m.mraid_profile_enable(plan.handle)
+        out = plan.run_pol2(d)
+        ran = m.mraid_profile_read(plan.handle)
+    assert "gram_tc" in ran and "pol2_fold" not in ran, ran
+    stat = out["stat"].cpu().numpy()
+    evals = out["evals"].cpu().numpy()
+    q1 = out["q1"].cpu().numpy()
+    flags = out["flags"].cpu().numpy().astype(bool)
+    del d
+    torch.cuda.empty_cache()
+    check_mask(stat, flags, out["info"])
+
+    ev0, ev1 = synth.events(cfg), synth.events(cfg1)
+    rng = np.random.default_rng(2513)
+    idx = set(rng.integers(0, cfg.n_cells, size=192).tolist())
+    for ev in (ev0, ev1):
+        idx |= {k * cfg.n_chan + c for (_, c, k, _) in ev["spike"][:16]}
+        idx |= {int(rng.integers(0, cfg.n_sub)) * cfg.n_chan + c for (c, _) in ev["narrow"][:16]}
+    idx = np.array(sorted(idx))
+    data = h2.numpy().reshape(2 * cfg.n_beam, cfg.n_time, cfg.n_chan)
+    o = oracle.cells_pol2(data, cfg.n_samp_sub, (idx // cfg.n_chan).astype(np.int32),
+                          (idx % cfg.n_chan).astype(np.int32), n_threads=synth.default_threads())
+    compare_eig(evals[idx], o["evals"], "two polarisations, fast block")
+    compare_q1(q1[idx], o["q1"], o["evals"])
+    s_err = np.abs(stat[idx] - o["stat"]) / o["stat"]
+    assert s_err.max() <= STAT_TOL, s_err.max()
+
+    F = flags.reshape(cfg.n_sub, cfg.n_chan)
+    for (c, _) in ev0["narrow"] + ev1["narrow"]:
+        assert F[:, c].mean() > 0.9, c
+    busy = set()
+    for c_ in (cfg, cfg1):
+        cells = synth.rfi_cells(c_)
+        busy |= cells["narrow"] | cells["burst"]
+    lone = [(k, c) for ev in (ev0, ev1) for (_, c, k, _) in ev["spike"] if (k, c) not in busy]
+    assert len(lone) > 100
+    assert np.mean([F[k, c] for (k, c) in lone]) < 0.05
