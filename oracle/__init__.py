@@ -114,6 +114,9 @@ def cell_gram(data: np.ndarray, n_samp_sub: int, sub: int, chan: int) -> np.ndar
 
 
 def cell_cov_f32(data: np.ndarray, n_samp_sub: int, sub: int, chan: int) -> np.ndarray:
+    """Population covariance N x N (FP64, two passes) of one cell of float32
+    samples: Eq. 1 for float32 input, before the Pearson normalisation.
+    Pinned by tests/test_oracle_f32.py."""
     n_beam, bstride, n_chan = _block_view(data)
     C = np.zeros((n_beam, n_beam), dtype=np.float64)
     _check(_load().orc_cell_cov_f32(_ptr(data), n_beam, bstride, n_chan, n_samp_sub,
@@ -131,6 +134,8 @@ def corr_from_gram(G: np.ndarray):
 
 
 def corr_from_cov(C: np.ndarray):
+    """(r, n_zero_variance_beams) from a covariance: r_ab = C_ab /
+    sqrt(C_aa C_bb), r_aa = 1, r_ab = 0 beside a zero-variance beam."""
     C = np.ascontiguousarray(C, dtype=np.float64)
     n = C.shape[0]
     r = np.zeros((n, n), dtype=np.float64)
