@@ -234,6 +234,35 @@ def test_invariants_on_synthetic_block(small_block):
         assert q1[np.argmax(np.abs(q1))] > 0
 
 
+
+@pytest.mark.parametrize("n_threads,by_pointer", [(1, False), (4, False), (3, True)])
+def test_cells_driver_matches_brute_force(small_block, n_threads, by_pointer):
+    """The threaded selected-cells driver (the one the GPU parity tests call,
+    also through a raw pointer) against numpy on the same bytes: Gram sums by
+    einsum, eigenvalues by LAPACK of numpy's corrcoef, q1 an eigenvector of
+    lambda_1 with the sign rule, s = lambda_1^2 / ||r||_F^2."""
+    d = small_block
+    rng = np.random.default_rng(29 + n_threads)
+    subs = rng.integers(0, 256, size=23).astype(np.int32)
+    chans = rng.integers(0, 64, size=23).astype(np.int32)
+    if by_pointer:
+        o = oracle.cells(None, 128, subs, chans, n_threads=n_threads,
+                         data_ptr=d.ctypes.data, shape=d.shape)
+    else:
+        o = oracle.cells(d, 128, subs, chans, n_threads=n_threads)
+    for i, (k, c) in enumerate(zip(subs, chans)):
+        X = d[:, k * 128:(k + 1) * 128, c].astype(np.int64)
+        Xa = np.vstack([X, np.ones((1, 128), dtype=np.int64)])
+        np.testing.assert_array_equal(o["G"][i], np.einsum("at,bt->ab", Xa, Xa))
+        r = np.corrcoef(X.astype(np.float64))
+        ev = np.linalg.eigvalsh(r)[::-1]
+        np.testing.assert_allclose(o["evals"][i], ev, rtol=0, atol=1e-12)
+        q = o["q1"][i]
+        np.testing.assert_allclose(r @ q, ev[0] * q, rtol=0, atol=1e-10)
+        assert abs(np.linalg.norm(q) - 1.0) < 1e-12 and q[np.argmax(np.abs(q))] > 0
+        assert abs(o["stat"][i] - ev[0] ** 2 / np.sum(r * r)) < 1e-12
+
+
 # ------------------------------------------- noise statistics (Eq. 1-2)
 
 def test_noise_only_second_moment_and_mp_edges():
