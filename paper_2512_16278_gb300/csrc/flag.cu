@@ -5,7 +5,8 @@
 // One cooperative launch runs the whole iteration on the device: every pass
 // masks the cells above the previous threshold, reduces (count, sum s,
 // sum s^2) over the cells still unmasked and unpreserved (per thread in
-// FP32 over its ~10 cells, then in FP64), and
+// FP32 over its ~10 cells, then in FP64; the per-cell tests are FP32 and
+// decide exactly as FP64 would), and
 // derives mu, sigma (population) and mu + k sigma. The fit stops when a
 // pass masks nothing new (the unmasked count is unchanged) or after
 // max_clip_iter fits. Block partial sums are combined in a fixed order by
@@ -90,34 +91,56 @@ __device__ __forceinline__ void grid_total3(const double* part, int nb, double* 
   __syncthreads();
 }
 
+// Unroll of the per-cell loop: a thread issues the loads of kFlagUnroll
+// cells before it uses them (and before any store), in its usual cell order.
+constexpr int kFlagUnroll = 4;
+
 __global__ void __launch_bounds__(kFlagThreads) flag_kernel(FlagArgs f) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double red[3 * (kFlagThreads / 32)];
   __shared__ double bcast[3];
+  const float* __restrict__ stat = f.stat;
+  uint8_t* __restrict__ flags = f.flags;
+  const uint8_t* __restrict__ keep = f.keep;
+  const int64_t n = f.n_cells;
+  const uint32_t n_chan = (uint32_t)f.n_chan;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = tid; i < f.n_cells; i += nthr) f.flags[i] = 0;
+  for (int64_t i = tid; i < n; i += nthr) flags[i] = 0;
 
   double thresh = INFINITY, mu = 0.0, sigma = 0.0;
   double prev_count = -1.0, used = 0.0;
   int fits = 0, converged = 0;
   for (int pass = 0;; ++pass) {
-    // a thread's few cells sum in FP32 (GB300 runs FP64 at a small fraction
-    // of the FP32 rate); blocks and the grid combine in FP64, fixed order
+    // The mask test v > thresh for a float v equals v > tf with tf the
+    // largest float <= thresh: no float lies in (tf, thresh]. So the cells
+    // need no FP64 (GB300 runs it at a small fraction of the FP32 rate).
+    const float tf = __double2float_rd(thresh);
+    // a thread's few cells sum in FP32 in a fixed order; blocks and the
+    // grid combine in FP64, fixed order
     int cnt_t = 0;
     float s1_t = 0.f, s2_t = 0.f;
-    for (int64_t i = tid; i < f.n_cells; i += nthr) {
-      if (f.keep && f.keep[(uint32_t)i % (uint32_t)f.n_chan]) continue;
-      const float v = f.stat[i];
-      uint8_t m = f.flags[i];
-      if (!m && (double)v > thresh) {
-        m = 1;
-        f.flags[i] = 1;
+    for (int64_t i0 = tid; i0 < n; i0 += kFlagUnroll * nthr) {
+      float v[kFlagUnroll];
+      uint8_t m[kFlagUnroll];
+#pragma unroll
+      for (int u = 0; u < kFlagUnroll; ++u) {
+        const int64_t i = i0 + u * nthr;
+        const bool mine = i < n && !(keep && keep[(uint32_t)i % n_chan]);
+        v[u] = mine ? stat[i] : 0.f;
+        m[u] = mine ? flags[i] : (uint8_t)2;  // 2: past the end or preserved
       }
-      if (!m) {
-        ++cnt_t;
-        s1_t += v;
-        s2_t = fmaf(v, v, s2_t);
+#pragma unroll
+      for (int u = 0; u < kFlagUnroll; ++u) {
+        if (m[u] == 0 && v[u] > tf) {
+          m[u] = 1;
+          flags[i0 + u * nthr] = 1;
+        }
+        if (m[u] == 0) {
+          ++cnt_t;
+          s1_t += v[u];
+          s2_t = fmaf(v[u], v[u], s2_t);
+        }
       }
     }
     double cnt = (double)cnt_t, s1 = (double)s1_t, s2 = (double)s2_t;
@@ -150,14 +173,26 @@ __global__ void __launch_bounds__(kFlagThreads) flag_kernel(FlagArgs f) {
     prev_count = cnt;
     ++fits;
   }
-  // totals for the report
-  double nflag = 0.0, nnear = 0.0, dummy = 0.0;
-  for (int64_t i = tid; i < f.n_cells; i += nthr) {
-    nflag += f.flags[i];
-    if (f.keep && f.keep[(uint32_t)i % (uint32_t)f.n_chan]) continue;
-    const double v = (double)f.stat[i];
-    if (fabs(v - thresh) <= 2e-4 * v) nnear += 1.0;
+  // totals for the report. "Near" is |s - thresh| <= 2e-4 s, evaluated in
+  // FP32 and redone in FP64 only within 1 % of the boundary: tf is within
+  // one float ulp (1.2e-7 relative) of thresh and the FP32 difference
+  // carries a rounding error of the same order, far inside the 1 % band,
+  // so every decision outside the band is the FP64 one.
+  const float tf = __double2float_rd(thresh);
+  int nflag_t = 0, nnear_t = 0;
+  for (int64_t i = tid; i < n; i += nthr) {
+    nflag_t += flags[i];
+    if (keep && keep[(uint32_t)i % n_chan]) continue;
+    const float v = stat[i];
+    const float a = fabsf(v - tf), b = 2e-4f * v;
+    bool near;
+    if (!(b > 1e-30f) || fabsf(a - b) <= 1e-2f * b)
+      near = fabs((double)v - thresh) <= 2e-4 * (double)v;
+    else
+      near = a < b;
+    nnear_t += near;
   }
+  double nflag = (double)nflag_t, nnear = (double)nnear_t, dummy = 0.0;
   block_sum3(nflag, nnear, dummy, red);
   grid.sync();  // everyone has read this pass's partials before they are reused
   double* part = f.partials;
