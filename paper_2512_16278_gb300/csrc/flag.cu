@@ -37,6 +37,10 @@ struct FlagArgs {
   mraid_flag_info* info;
 };
 
+// Block totals of (a, b, c): a fixed shuffle tree per warp, then the warps'
+// totals in a fixed order. Only thread 0 receives the block totals (it alone
+// publishes them); the other threads skip that FP64 loop, which GB300 would
+// otherwise issue once per warp at a small fraction of the FP32 rate.
 __device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -52,11 +56,13 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c, doub
     red[3 * w + 2] = c;
   }
   __syncthreads();
-  a = b = c = 0.0;
-  for (int i = 0; i < nw; ++i) {  // fixed order
-    a += red[3 * i];
-    b += red[3 * i + 1];
-    c += red[3 * i + 2];
+  if (threadIdx.x == 0) {
+    a = b = c = 0.0;
+    for (int i = 0; i < nw; ++i) {  // fixed order
+      a += red[3 * i];
+      b += red[3 * i + 1];
+      c += red[3 * i + 2];
+    }
   }
 }
 
@@ -99,6 +105,10 @@ __global__ void __launch_bounds__(kFlagThreads) flag_kernel(FlagArgs f) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double red[3 * (kFlagThreads / 32)];
   __shared__ double bcast[3];
+  // the fit's state, kept by thread 0: mu, sigma, cells used, previous count
+  __shared__ double fit_state[4];
+  __shared__ double fit_thresh;
+  __shared__ int fit_stop;
   const float* __restrict__ stat = f.stat;
   uint8_t* __restrict__ flags = f.flags;
   const uint8_t* __restrict__ keep = f.keep;
@@ -108,9 +118,14 @@ __global__ void __launch_bounds__(kFlagThreads) flag_kernel(FlagArgs f) {
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = tid; i < n; i += nthr) flags[i] = 0;
 
-  double thresh = INFINITY, mu = 0.0, sigma = 0.0;
-  double prev_count = -1.0, used = 0.0;
+  double thresh = INFINITY;
   int fits = 0, converged = 0;
+  if (threadIdx.x == 0) {
+    fit_state[0] = 0.0;   // mu
+    fit_state[1] = 0.0;   // sigma
+    fit_state[2] = 0.0;   // cells in the last fit
+    fit_state[3] = -1.0;  // unmasked count of the last fit
+  }
   for (int pass = 0;; ++pass) {
     // The mask test v > thresh for a float v equals v > tf with tf the
     // largest float <= thresh: no float lies in (tf, thresh]. So the cells
@@ -153,38 +168,54 @@ __global__ void __launch_bounds__(kFlagThreads) flag_kernel(FlagArgs f) {
     }
     grid.sync();
     grid_total3(part, gridDim.x, bcast, cnt, s1, s2);
-    if (pass >= 1 && cnt == prev_count) {  // the last threshold masked nothing
-      converged = 1;
-      break;
+    // Thread 0 of every block makes the same decision and fit from the same
+    // totals; its block takes the threshold and the decision from it. The
+    // fit's state (fit_state, fits, converged) is thread 0's, and block 0's
+    // thread 0 writes the report.
+    if (threadIdx.x == 0) {
+      int stop = 0;
+      if (pass >= 1 && cnt == fit_state[3]) {  // the last threshold masked nothing
+        converged = 1;
+        stop = 1;
+      } else if (fits == f.max_iter) {  // mask already holds max_iter markings
+        stop = 1;
+      } else if (cnt == 0.0) {  // nothing left to fit
+        fit_state[0] = fit_state[1] = 0.0;
+        thresh = INFINITY;
+        fit_state[2] = 0.0;
+        ++fits;
+        converged = 1;
+        stop = 1;
+      } else {
+        const double mu = s1 / cnt;
+        const double sigma = sqrt(fmax(s2 / cnt - mu * mu, 0.0));
+        thresh = mu + f.k_sigma * sigma;
+        fit_state[0] = mu;
+        fit_state[1] = sigma;
+        fit_state[2] = cnt;
+        fit_state[3] = cnt;
+        ++fits;
+      }
+      fit_thresh = thresh;
+      fit_stop = stop;
     }
-    if (fits == f.max_iter) break;  // mask already holds max_iter markings
-    if (cnt == 0.0) {               // nothing left to fit
-      mu = sigma = 0.0;
-      thresh = INFINITY;
-      used = 0.0;
-      ++fits;
-      converged = 1;
-      break;
-    }
-    mu = s1 / cnt;
-    sigma = sqrt(fmax(s2 / cnt - mu * mu, 0.0));
-    thresh = mu + f.k_sigma * sigma;
-    used = cnt;
-    prev_count = cnt;
-    ++fits;
+    // the next pass writes these only after its own block barriers
+    __syncthreads();
+    thresh = fit_thresh;
+    if (fit_stop) break;
   }
   // totals for the report. "Near" is |s - thresh| <= 2e-4 s, evaluated in
-  // FP32 and redone in FP64 only within 1 % of the boundary: tf is within
+  // FP32 and redone in FP64 only within 1 % of the boundary: tfin is within
   // one float ulp (1.2e-7 relative) of thresh and the FP32 difference
   // carries a rounding error of the same order, far inside the 1 % band,
   // so every decision outside the band is the FP64 one.
-  const float tf = __double2float_rd(thresh);
+  const float tfin = __double2float_rd(thresh);
   int nflag_t = 0, nnear_t = 0;
   for (int64_t i = tid; i < n; i += nthr) {
     nflag_t += flags[i];
     if (keep && keep[(uint32_t)i % n_chan]) continue;
     const float v = stat[i];
-    const float a = fabsf(v - tf), b = 2e-4f * v;
+    const float a = fabsf(v - tfin), b = 2e-4f * v;
     bool near;
     if (!(b > 1e-30f) || fabsf(a - b) <= 1e-2f * b)
       near = fabs((double)v - thresh) <= 2e-4 * (double)v;
@@ -209,13 +240,13 @@ __global__ void __launch_bounds__(kFlagThreads) flag_kernel(FlagArgs f) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const double tf = bcast[0], tn = bcast[1];
     mraid_flag_info* o = f.info;
-    o->mu = mu;
-    o->sigma = sigma;
+    o->mu = fit_state[0];
+    o->sigma = fit_state[1];
     o->thresh = thresh;
     o->iterations = fits;
     o->converged = converged;
     o->n_flagged = (int64_t)tf;
-    o->n_used = (int64_t)used;
+    o->n_used = (int64_t)fit_state[2];
     o->n_near = (int64_t)tn;
   }
 }
