@@ -5,8 +5,8 @@ Workload (default): 19 beams x 4096 channels x 200 sub-integrations x 1024
 samples of 8-bit data (a 10.07 s block at 49.152 us; 819200 cells of 19x19
 correlation matrices), synthetic (seeded generator, noise + beam-common RFI
 + single-beam pulses). One step = mraid_run on the block resident in HBM:
-Gram sums, correlation, Jacobi eigenvalues, q1, statistic and the
-iterative mask. Inputs (15.9 GB) are far larger than L2 (129 MB).
+Gram sums and correlation, all eigenvalues and q1 (Householder reduction and
+implicit QR by default), the statistic and the iterative mask. Inputs (15.9 GB) are far larger than L2 (129 MB).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mraid|reference]
 
