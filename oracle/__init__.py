@@ -1,7 +1,8 @@
 """ctypes binding of the plain C oracle (mraid_oracle.c).
 
 TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU
-baseline leg may import this; the library's product path never does.
+baseline leg and reference arm (which time it) may import this; the
+library's product path never does.
 
 Method: mRAID (arXiv 2512.16278) Section 3.2 Eq. 1 (cross-correlation
 matrix), Section 3.3 Eq. 2 (eigendecomposition, normalised eigenvalues),

@@ -1,8 +1,9 @@
 /* mraid_oracle.h - plain, slow CPU oracle of the eigenvalue RFI flagger.
  *
- * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the CPU
- * baseline leg of the benchmark may call this code; the library's product
- * path never does. It shares no source with the CUDA path.
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the
+ * benchmark's CPU baseline leg and reference arm (which time it) may call
+ * this code; the library's product path never does. It shares no source
+ * with the CUDA path.
  *
  * Method (mRAID, arXiv 2512.16278):
  *   Section 3.2, Eq. 1: per (channel j, sub-integration k) the N_beam x N_beam
