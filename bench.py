@@ -45,6 +45,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=None,
+                    help="oracle seconds of the reference arm over all its steps "
+                         "(default: 60, and at least 2 per step)")
     ap.add_argument("--n-sub", type=int, default=0,
                     help="shrink the block to this many sub-integrations (profiling runs)")
     ap.add_argument("--f32-subs", type=int, default=20,
@@ -662,7 +665,11 @@ def run_reference(args):
     import synth
     h = torch.empty(cfg.nbytes, dtype=torch.uint8)
     synth.generate(cfg, out_ptr=h.data_ptr())
-    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    n_runs = max(1, args.steps + args.warmup)
+    if args.ref_seconds is None:
+        per_step = max(2.0, 60.0 / n_runs)
+    else:
+        per_step = max(0.1, args.ref_seconds / n_runs)
     vals = []
     for i in range(args.warmup + args.steps):
         r, _ = cpu_baseline(cfg, h.data_ptr(), per_step)
