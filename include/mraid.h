@@ -188,7 +188,7 @@ mraid_status mraid_run(mraid_plan_t plan, const void* d_data, float* d_evals,
 mraid_status mraid_run_host(mraid_plan_t plan, const void* h_data, float* h_stat,
                             uint8_t* h_flags, mraid_flag_info* info);
 
-/* Several timescales in one pass (Section 4.4, Table 1 and Fig. 7 run the
+/* Several timescales in one pass (Section 4.2, Table 1 and Fig. 7 run the
  * method at sub-interval lengths from 0.05 s to 10 s). Level i uses
  * sub-intervals of factors[i] consecutive sub-integrations of the plan
  * (factors[i] * n_samp_sub samples each): the whole path (Eq. 1, Eq. 2,

@@ -1,6 +1,6 @@
 // multires.cu - Gram sums of longer sub-intervals from shorter ones.
 //
-// Section 4.4 (Table 1, Fig. 7) runs the method at sub-interval lengths
+// Section 4.2 (Table 1, Fig. 7) runs the method at sub-interval lengths
 // from 0.05 s to 10 s. The augmented Gram of Eq. 1 over a sub-interval made
 // of m consecutive shorter ones is the sum of their Grams: every entry
 // (sum x_a x_b, sum x_a, n) is a sum over samples, and int64 addition is

@@ -41,7 +41,7 @@ def test_fixture_is_complete_and_self_consistent():
     for k in ("n_beam", "t_samp_us", "n_samp_sub", "n_chan", "bit_depth", "n_pol", "n_sub_file",
               "n_time_file", "eig_k", "vec_t", "timescales_s"):
         assert k in P, k
-    # Sec. 2's sub-integrations of Sec. 2's length are Sec. 5's time samples
+    # Sec. 2's sub-integrations of Sec. 2's length are Sec. 4.4's time samples
     assert P["n_sub_file"] * P["n_samp_sub"] == P["n_time_file"]
 
 

@@ -1,4 +1,4 @@
-"""Several timescales in one pass (mraid_multires, Section 4.4 / Table 1)
+"""Several timescales in one pass (mraid_multires, Section 4.2 / Table 1)
 against the oracle run directly at each longer sub-integration, and
 against mraid_run on a plan with that sub-integration length (needs a GPU).
 
