@@ -437,14 +437,23 @@ def mraid_set_eig_variant(plan: int, variant: int):
     _check(load().mraid_set_eig_variant(plan, variant), "mraid_set_eig_variant")
 
 
+def tune_key(n_beam: int, n_chan: int, n_samp_sub: int, bit_depth: int = 8) -> str:
+    """Key of a shape in the tuning cache: the variants of 8-bit and float32
+    plans differ, so the sample type is part of it."""
+    if bit_depth not in (8, 32):
+        raise ValueError(f"bit_depth {bit_depth}: 8 or 32")
+    return f"{n_beam},{n_chan},{n_samp_sub},{'u8' if bit_depth == 8 else 'f32'}"
+
+
 def tune(plan: int, d_data, n_beam: int, n_chan: int, n_samp_sub: int,
-         cache_path: Optional[str] = None, reps: int = 3):
-    """Pick the Gram and Jacobi variants for this shape: from the JSON tuning
-    cache (keyed by beams, channels, samples per sub-integration, sample type)
-    if it holds the shape, else by mraid_autotune, recording the result.
-    Returns (gram variant, jacobi variant)."""
+         cache_path: Optional[str] = None, reps: int = 3, bit_depth: int = 8):
+    """Pick the Gram and eigensolver variants for this shape: from the JSON
+    tuning cache (keyed by beams, channels, samples per sub-integration and
+    sample type, which must be the plan's bit_depth) if it holds the shape,
+    else by mraid_autotune, recording the result.
+    Returns (gram variant, eigensolver variant)."""
     import json
-    key = f"{n_beam},{n_chan},{n_samp_sub},u8"
+    key = tune_key(n_beam, n_chan, n_samp_sub, bit_depth)
     cache = {}
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as f:

@@ -101,3 +101,12 @@ def test_binding_rejects_non_contiguous_buffers():
     assert m._ptr(None) is None and m._ptr(1234) == 1234
     with pytest.raises(ValueError):
         m._ptr(t.t())
+
+
+def test_tuning_cache_key_separates_sample_types():
+    import paper_2512_16278_gb300 as m
+    assert m.tune_key(19, 4096, 1024) == "19,4096,1024,u8"
+    assert m.tune_key(19, 4096, 1024, 32) == "19,4096,1024,f32"
+    assert m.tune_key(19, 4096, 1024, 8) != m.tune_key(19, 4096, 1024, 32)
+    with pytest.raises(ValueError):
+        m.tune_key(19, 4096, 1024, 16)
