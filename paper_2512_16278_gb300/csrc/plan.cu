@@ -340,6 +340,11 @@ mraid_status mraid_validate(const mraid_params* p) {
     set_error("bit_depth %d: 8-bit and float32 samples are built", p->bit_depth);
     return MRAID_ERR_UNSUPPORTED;
   }
+  if ((int64_t)p->n_sub * p->n_chan > 2147483647ll) {  // before any product with it
+    set_error("n_sub * n_chan exceeds 2^31 - 1 cells");
+    return MRAID_ERR_INVALID_ARG;
+  }
+  // at most 2^31 cells of 2^20 samples: no overflow
   const int64_t dense = (int64_t)p->n_sub * p->n_samp_sub * p->n_chan;
   if (p->beam_stride != 0 && p->beam_stride < dense) {
     set_error("beam_stride %lld smaller than one beam's block (%lld)", (long long)p->beam_stride,
@@ -352,10 +357,6 @@ mraid_status mraid_validate(const mraid_params* p) {
   }
   if (p->max_clip_iter < 1 || p->max_clip_iter > kMaxClipIter) {
     set_error("max_clip_iter %d outside [1, %d]", p->max_clip_iter, kMaxClipIter);
-    return MRAID_ERR_INVALID_ARG;
-  }
-  if ((int64_t)p->n_sub * p->n_chan > 2147483647ll) {
-    set_error("n_sub * n_chan exceeds 2^31 - 1 cells");
     return MRAID_ERR_INVALID_ARG;
   }
   if (p->reserved != 0) {

@@ -110,3 +110,13 @@ def test_tuning_cache_key_separates_sample_types():
     assert m.tune_key(19, 4096, 1024, 8) != m.tune_key(19, 4096, 1024, 32)
     with pytest.raises(ValueError):
         m.tune_key(19, 4096, 1024, 16)
+
+
+def test_validate_rejects_too_many_cells_before_any_size_product(lib):
+    """2^30 sub-integrations x 2^30 channels of 2^20 samples: the cell count
+    is refused first, so no 64-bit block size is ever formed from it."""
+    import paper_2512_16278_gb300 as m
+    p = m.mraid_default_params(19, 1 << 30, 1 << 20, 1 << 30)
+    p.beam_stride = 1
+    assert m.mraid_validate(p) == 1
+    assert "cells" in m.mraid_last_error()
