@@ -240,7 +240,8 @@ typedef struct {
   double ratio;      /* stop when |w_new - w| / |w| < ratio (Euclidean norms), > 0 */
   int32_t itermax;   /* bound on weighted solves, 1..1000 */
   int32_t interval;  /* sub-integrations per bandpass fit interval, >= 1 (the last
-                        interval of a block may be shorter) */
+                        interval of a block may be shorter; one at least as long
+                        as the block makes the block one interval) */
 } mraid_bandpass_params;
 
 /* lam 1e5, ratio 1e-3, itermax 50, interval 20 (about 1 s of 1024-sample

@@ -485,8 +485,15 @@ mraid_status mraid_run_bandpass(mraid_plan_t pl, const void* d_data,
     set_error("mraid_run_bandpass: 8-bit samples and 3 to 2^20 channels");
     return MRAID_ERR_UNSUPPORTED;
   }
-  const int interval = bp->interval;
-  const int n_int = (pl->p.n_sub + interval - 1) / interval;
+  // an interval at least as long as the block is one interval of the
+  // block: the same partition, and no int arithmetic on a huge interval
+  const int interval = bp->interval < pl->p.n_sub ? bp->interval : pl->p.n_sub;
+  const int n_int = (int)(((int64_t)pl->p.n_sub + interval - 1) / interval);
+  if ((int64_t)n_int * pl->p.n_beam > INT32_MAX) {
+    set_error("mraid_run_bandpass: %d intervals x %d beams exceed 2^31 - 1 spectra", n_int,
+              pl->p.n_beam);
+    return MRAID_ERR_UNSUPPORTED;
+  }
   const int n_sys = n_int * pl->p.n_beam;
   const size_t elems = (size_t)n_sys * pl->p.n_chan;
   st = ensure_workspace(pl, (size_t)pl->n_cells);

@@ -96,6 +96,20 @@ def test_bandpass_same_on_both_gram_kernels():
         np.testing.assert_array_equal(outs[0][k], outs[1][k], err_msg=k)
 
 
+def test_interval_beyond_the_block_is_one_interval():
+    """Any interval at least as long as the block, up to the largest int32,
+    fits the whole block once: outputs equal those of interval = n_sub."""
+    import torch
+    m = lib()
+    cfg = synth.SMALL.replace(n_sub=16)
+    d = torch.from_numpy(synth.generate(cfg)).cuda()
+    with m.Plan(19, 64, 128, 16) as plan:
+        a = plan.run_bandpass(d, lam=1e3, interval=16)
+        b = plan.run_bandpass(d, lam=1e3, interval=2**31 - 1)
+    for k in ("bandpass", "evals", "stat", "flags"):
+        np.testing.assert_array_equal(a[k].cpu().numpy(), b[k].cpu().numpy(), err_msg=k)
+
+
 def test_bandpass_rejects_bad_arguments():
     import torch
     m = lib()
