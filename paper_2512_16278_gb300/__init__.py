@@ -26,7 +26,7 @@ __all__ = [
     "mraid_batch_packing",
     "mraid_batch_destroy", "UnitIO", "Batch", "mraid_serve_open", "mraid_serve_submit",
     "mraid_serve_poll", "mraid_serve_drain", "mraid_serve_close", "StreamDesc", "BlockResult",
-    "Server", "mraid_autotune", "mraid_set_variant", "mraid_set_eig_variant", "tune",
+    "Server", "mraid_autotune", "mraid_set_variant", "mraid_set_eig_variant", "tune", "tune_key",
     "mraid_refine", "mraid_multires", "BandpassParams", "mraid_default_bandpass_params",
     "mraid_arpls", "mraid_run_bandpass", "mraid_ccm_pol2", "mraid_run_pol2", "STATUS",
 ]

@@ -211,3 +211,40 @@ def test_fast_block_two_polarisations(fast_block):
     lone = [(k, c) for ev in (ev0, ev1) for (_, c, k, _) in ev["spike"] if (k, c) not in busy]
     assert len(lone) > 100
     assert np.mean([F[k, c] for (k, c) in lone]) < 0.05
+
+
+def test_fast_block_float32_twenty_sub_integrations(fast_block):
+    """Float32 input (bit_depth 32) at the size the benchmark times: the
+    first 20 sub-integrations of the block as (x - 128) / 20 (6.4 GB on the
+    device), through mraid_run on the tensor cores; sampled cells against
+    the oracle's FP64 covariance path, and the masking properties."""
+    import torch
+    m = lib()
+    cfg, h = fast_block
+    N, C, S, K = cfg.n_beam, cfg.n_chan, cfg.n_samp_sub, 20
+    d = h.to("cuda", non_blocking=False)
+    x = d.view(N, cfg.n_time, C)[:, :K * S, :].float().sub_(128.0).div_(20.0).contiguous()
+    del d
+    with m.Plan(N, C, S, K, bit_depth=32) as plan:
+        m.mraid_profile_enable(plan.handle)
+        out = plan.run(x)
+        ran = m.mraid_profile_read(plan.handle)
+    assert "gram_tc_f32" in ran, ran
+    evals = out["evals"].cpu().numpy()
+    stat = out["stat"].cpu().numpy()
+    flags = out["flags"].cpu().numpy().astype(bool)
+    check_mask(stat, flags, out["info"])
+    rng = np.random.default_rng(2514)
+    idx = np.unique(rng.integers(0, K * C, size=96))
+    ev_o = np.zeros((idx.size, N))
+    for j, i in enumerate(idx):
+        k, c = int(i // C), int(i % C)
+        cell = x[:, k * S:(k + 1) * S, c:c + 1].contiguous().cpu().numpy()
+        r, _ = oracle.corr_from_cov(oracle.cell_cov_f32(cell, S, 0, 0))
+        ev_o[j] = oracle.jacobi(r)[0]
+    del x
+    torch.cuda.empty_cache()
+    compare_eig(evals[idx], ev_o, "float32, fast block")
+    st_o = np.array([oracle.stat(e) for e in ev_o])
+    s_err = np.abs(stat[idx] - st_o) / st_o
+    assert s_err.max() <= STAT_TOL, s_err.max()
