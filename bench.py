@@ -220,23 +220,48 @@ def cpu_baseline(cfg, h_ptr, seconds):
     rng = np.random.default_rng(12345)
     shape = (cfg.n_beam, cfg.n_time, cfg.n_chan)
 
-    def run(n):
+    def run(n, n_threads=threads):
         idx = rng.integers(0, cfg.n_cells, size=n)
         subs = (idx // cfg.n_chan).astype(np.int32)
         chans = (idx % cfg.n_chan).astype(np.int32)
         t0 = time.perf_counter()
-        res = oracle.cells(None, cfg.n_samp_sub, subs, chans, n_threads=threads, data_ptr=h_ptr,
-                           shape=shape)
+        res = oracle.cells(None, cfg.n_samp_sub, subs, chans, n_threads=n_threads,
+                           data_ptr=h_ptr, shape=shape)
         return time.perf_counter() - t0, idx, res
 
     n = threads * 4
     t, _, _ = run(n)
     n2 = max(threads, int(n * max(seconds - t, 0.5) / max(t, 1e-6)))
     t2, idx, res = run(n2)
+    # one thread on a quarter of the all-core sample's time: the per-core rate
+    n1 = max(4, n2 // (4 * threads))
+    t1, _, _ = run(n1, 1)
     return {"value": n2 / t2, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "single_thread_value": n1 / t1, "cpu_model": cpu_model(),
             "sample": f"{n2} random cells of the same block (per-cell Gram, FP64 Jacobi, "
-                      f"statistic; {t2:.1f} s on {threads} threads); the mask pass is "
-                      "excluded (it is O(cells) and negligible)"}, (idx, res)
+                      f"statistic; {t2:.1f} s on {threads} threads; {n1} cells on one "
+                      f"thread in {t1:.1f} s); the mask pass is excluded (it is O(cells) "
+                      "and negligible)"}, (idx, res)
+
+
+def cpu_model():
+    """The host CPU's name as the kernel reports it (x86: model name; Arm:
+    implementer and part numbers), else the machine type."""
+    import platform
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                fields.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    if fields.get("model name"):
+        return fields["model name"]
+    if fields.get("CPU part"):
+        return (f"{platform.machine()} (CPU implementer {fields.get('CPU implementer', '?')}, "
+                f"part {fields['CPU part']})")
+    return platform.machine() or "unknown"
 
 
 def sampled_parity(sample, evals, q1, stat):
@@ -683,7 +708,9 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "u8->i64 Gram, f64 Jacobi", "data": "synthetic",
         "config": config_dict(cfg, desc, 1),
         "cpu_baseline": {"kind": "oracle", "cores": r["cores"], "sample": r["sample"],
-                         "value": v, "unit": UNIT},
+                         "value": v, "unit": UNIT,
+                         "single_thread_value": r["single_thread_value"],
+                         "cpu_model": r["cpu_model"]},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
