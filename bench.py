@@ -530,10 +530,26 @@ def bench_pol2(m, torch, h, cfg, stream, steps, peaks):
                     "eigensolver and mask"}
 
 
-def bench_batched(m, torch, stream, steps):
+def batched_fractions(shapes, ms, peaks):
+    """Whole-pass fractions of the batched form: the algorithmic bytes (every
+    block's samples read once; s, flag, eigenvalues and q1 written) against
+    the HBM peak, and the eigensolver's dense floor ((4/3) N^3 flops per
+    cell) against the FP32 peak."""
+    nbytes = sum(c.nbytes + c.n_cells * (5 + 8 * c.n_beam) for c in shapes)
+    flops = sum(c.n_cells * 4.0 * c.n_beam ** 3 / 3.0 for c in shapes)
+    gbs = nbytes / (ms / 1e3) / 1e9
+    tflops = flops / (ms / 1e3) / 1e12
+    return {"hbm": {"bytes_per_pass": nbytes, "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"],
+                    "frac": gbs / peaks["hbm_gbs"]},
+            "alu": {"flops_per_pass": flops, "achieved_tflops": tflops,
+                    "peak_tflops": peaks["fp32_tflops"], "frac": tflops / peaks["fp32_tflops"]}}
+
+
+def bench_batched(m, torch, stream, steps, peaks=None):
     """Four receivers of 5 s each (13/19/36/72 beams) in one graph-captured
     pass, against the plain form (one mraid_run per block, one after the
-    other on one stream) on the same data."""
+    other on one stream) on the same data, with the pass's HBM and ALU
+    fractions."""
     import synth
     shapes = synth.BATCH_SHAPES
     datas = []
@@ -585,6 +601,7 @@ def bench_batched(m, torch, stream, steps):
             "ms_per_pass": ms_b, "cells_per_s": cells / (ms_b / 1000.0),
             "plain_ms_per_pass": ms_p, "plain_cells_per_s": cells / (ms_p / 1000.0),
             "graph_instantiations": inst, "graph_updates": upd,
+            "fractions": batched_fractions(shapes, ms_b, peaks) if peaks else None,
             "packing": {"chosen": "chained" if packing == 1 else "concurrent",
                         "ms_concurrent": ms_conc, "ms_chained": ms_chain},
             "note": "plain = one mraid_run per block, sequential on one stream; default variants "
@@ -887,7 +904,7 @@ def run_mraid(args):
     batched = served = None
     if world == 1 and args.workload == "fast_block" and not args.n_sub:
         if args.batch_steps > 0:
-            batched = bench_batched(m, torch, stream, args.batch_steps)
+            batched = bench_batched(m, torch, stream, args.batch_steps, peaks)
         if args.serve_seconds > 0:
             served = bench_served(m, torch, args.serve_seconds)
 

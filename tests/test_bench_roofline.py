@@ -43,3 +43,18 @@ def test_fp32_peak_is_derived_from_the_unit_counts():
         assert p["hbm_gbs"] == float(d["hbm_gbs"])
         mhz = float(d.get("sm_max_mhz", 2070.0))
     assert p["fp32_tflops"] == pytest.approx(152 * 128 * 2 * mhz * 1e6 / 1e12)
+
+
+def test_batched_fractions():
+    import synth
+    shapes = synth.BATCH_SHAPES
+    peaks = {"hbm_gbs": 6785.9, "source": "measured", "fp32_tflops": 80.54784}
+    f = bench.batched_fractions(shapes, 28.0, peaks)
+    nbytes = sum(c.n_beam * c.n_sub * c.n_samp_sub * c.n_chan
+                 + c.n_sub * c.n_chan * (5 + 8 * c.n_beam) for c in shapes)
+    flops = sum(c.n_sub * c.n_chan * 4.0 * c.n_beam ** 3 / 3.0 for c in shapes)
+    assert f["hbm"]["bytes_per_pass"] == nbytes
+    assert f["hbm"]["frac"] == pytest.approx(nbytes / 28e-3 / 1e9 / 6785.9)
+    assert f["alu"]["flops_per_pass"] == pytest.approx(flops)
+    assert f["alu"]["frac"] == pytest.approx(flops / 28e-3 / 1e12 / 80.54784)
+    assert [c.n_beam for c in shapes] == [13, 19, 36, 72]
