@@ -268,7 +268,8 @@ def sampled_parity(sample, evals, q1, stat):
     """GPU outputs of the timed run against the outputs the cpu_baseline
     leg's oracle sample produced (no further oracle call), at the tests'
     tolerances: eigenvalues 1e-4 of lambda_max, s 2e-4 relative, q1 1e-3
-    where the relative gap is at least 1e-2."""
+    where the relative gap is at least 1e-4 (below it q1 is unpinned), with
+    the q1 error also given per gap band."""
     import numpy as np
     idx, res = sample
     it = torch_index(idx)
@@ -280,13 +281,27 @@ def sampled_parity(sample, evals, q1, stat):
     e_err = (np.abs(ev - eo).max(axis=1) / lmax)
     s_err = np.abs(sv - so) / np.maximum(so, 1e-30)
     gap = (eo[:, 0] - eo[:, 1]) / eo[:, 0]
-    sel = gap >= 1e-2
-    q_err = np.abs(qv[sel] - qo[sel]).max(axis=1) if sel.any() else np.zeros(1)
+    # q1 error per cell; where the two largest magnitudes tie the sign rule
+    # is decided by rounding, so those cells compare up to sign
+    q_same = np.abs(qv - qo).max(axis=1)
+    q_flip = np.abs(qv + qo).max(axis=1)
+    mags = np.sort(np.abs(qo), axis=1)
+    tie = (mags[:, -1] - mags[:, -2]) <= 1e-3
+    q_err = np.where(tie, np.minimum(q_same, q_flip), q_same)
+    sel = gap >= 1e-4
+    bands = {}
+    for name, lo, hi in (("gap>=1e-2", 1e-2, np.inf), ("1e-3<=gap<1e-2", 1e-3, 1e-2),
+                         ("1e-4<=gap<1e-3", 1e-4, 1e-3)):
+        b = (gap >= lo) & (gap < hi)
+        bands[name] = {"cells": int(b.sum()),
+                       "q1_err_max": float(q_err[b].max()) if b.any() else None}
+    bands["gap<1e-4 (unpinned)"] = {"cells": int((gap < 1e-4).sum())}
+    q_max = float(q_err[sel].max()) if sel.any() else 0.0
     return {"cells": int(len(idx)), "eig_err_rel_max": float(e_err.max()),
             "eig_err_rel_p99": float(np.percentile(e_err, 99)),
-            "stat_err_rel_max": float(s_err.max()), "q1_err_max": float(q_err.max()),
-            "q1_cells": int(sel.sum()),
-            "pass": bool(e_err.max() <= 1e-4 and s_err.max() <= 2e-4 and q_err.max() <= 1e-3)}
+            "stat_err_rel_max": float(s_err.max()), "q1_err_max": q_max,
+            "q1_cells": int(sel.sum()), "q1_by_gap": bands,
+            "pass": bool(e_err.max() <= 1e-4 and s_err.max() <= 2e-4 and q_max <= 1e-3)}
 
 
 def torch_index(idx):
@@ -341,13 +356,17 @@ def bench_f32(m, torch, d_u8, cfg, stream, n_sub, peaks):
                "gram_kernel": kern, "gram_launches": n_l}
         if n_l > 0:
             kms = tot / n_l
-            b = in_bytes + cells * 4 * (N * (N + 1) // 2)      # samples in, r out
+            b = in_bytes                                        # samples in
+            x = cells * 4 * (N * (N + 1) // 2)                  # r out (reported apart)
             a = b / (kms / 1e3) / 1e9
             res["gram_roofline"] = {"bound": "hbm", "kernel": kern, "achieved": a,
                                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                     "frac": a / peaks["hbm_gbs"],
                                     "traffic": kernel_traffic(kern),
-                                    "work_per_launch": b, "ms_per_launch": kms}
+                                    "work_per_launch": b, "ms_per_launch": kms,
+                                    "export_bytes": x,
+                                    "frac_incl_export": (b + x) / (kms / 1e3) / 1e9
+                                    / peaks["hbm_gbs"]}
         out[tag] = res
     out["path"] = ("Gram of per-beam shifted samples: tensor cores with bf16 hi/lo products "
                    "(four MMAs per 16 samples) or FP32 CUDA cores; FP32 eigensolver")
@@ -510,12 +529,14 @@ def bench_pol2(m, torch, h, cfg, stream, steps, peaks):
     kt = {k: tot / steps for k, (n, tot) in prof.items() if n > 0}
     gram = None
     if "gram_tc" in kt:
-        b = 2 * nb + cells * 4 * (N * (N + 1) // 2)     # both polarisations in, r out
+        b = 2 * nb                                      # both polarisations in
+        x = cells * 4 * (N * (N + 1) // 2)              # r out (reported apart)
         a = b / (kt["gram_tc"] / 1e3) / 1e9
         gram = {"bound": "hbm", "kernel": "gram_tc (two polarisations)", "achieved": a,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": a / peaks["hbm_gbs"],
                 "traffic": kernel_traffic("gram_tc_pol2"), "work_per_launch": b,
-                "ms_per_launch": kt["gram_tc"]}
+                "ms_per_launch": kt["gram_tc"], "export_bytes": x,
+                "frac_incl_export": (b + x) / (kt["gram_tc"] / 1e3) / 1e9 / peaks["hbm_gbs"]}
     plan.close()
     del d2, h2
     torch.cuda.empty_cache()
@@ -742,7 +763,10 @@ def kernel_rooflines(cfg, kt, peaks):
     np_, psum = N * (N + 1) // 2, (N + 1) * (N + 2) // 2
     in_bytes = N * cfg.n_samp_sub * cells
     hbm = {  # bytes per launch: what the kernel must read and write once
-        "gram_tc": in_bytes + cells * 4 * np_,                 # samples in, r out
+        # the Gram reads every sample once (the per-cell input the path
+        # counts); its correlation export, an intermediate the path would
+        # keep on chip, is reported beside it, not as work
+        "gram_tc": in_bytes,
         "gram_u8": in_bytes + cells * 8 * psum,                # samples in, sums out
         "corr_from_sums": cells * (8 * psum + 4 * np_),
         "flag_clip": cells * 5,                                # stat in, flag out
@@ -766,6 +790,10 @@ def kernel_rooflines(cfg, kt, peaks):
                       "unit": "GB/s", "frac": a / peaks["hbm_gbs"], "traffic": kernel_traffic(k),
                       "peak_source": peaks["source"] + " (burst copy)",
                       "work_per_launch": b, "ms_per_launch": ms}
+            if k == "gram_tc":
+                x = cells * 4 * np_                               # packed r written
+                out[k]["export_bytes"] = x
+                out[k]["frac_incl_export"] = (b + x) / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]
     return out
 
 
@@ -929,6 +957,7 @@ def run_mraid(args):
             "sampled_parity": parity,
             "mask": {"flagged_fraction": info.n_flagged / cells, "iterations": info.iterations,
                      "threshold": info.thresh, "n_near": info.n_near},
+            "q1_fp64_cells": info.q1_refined,
             "variants": {"gram": variants[0], "eig": variants[1],
                          "eig_name": EIG_NAMES.get(variants[1], "?")},
             "eig_iterations": {"per_cell": info.jacobi_sweeps / cells,

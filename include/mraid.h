@@ -87,7 +87,10 @@ typedef struct {
   int64_t jacobi_warp_sweeps; /* the same, as executed: each 32-cell warp counts its slowest
                                  cell (mraid_run) */
   int32_t timed_out;     /* 1 if a bounded device wait expired */
-  int32_t reserved;
+  int32_t q1_refined;    /* cells whose q1 took the FP64 final step: relative gap
+                            (lambda_1 - lambda_2) / lambda_1 in [1e-6, 2e-3), or
+                            [1e-6, 1e-2) behind the one-thread Jacobi variants
+                            (mraid_set_eig_variant 0 and 1, N = 2, 3, 4, 13, 19) */
 } mraid_flag_info;
 
 typedef struct mraid_plan_s* mraid_plan_t;
@@ -138,7 +141,9 @@ mraid_status mraid_ccm(mraid_plan_t plan, const void* d_data, int64_t* d_sums,
  * MRAID_ERR_INVALID_ARG with a message, so split the block over calls.
  * The first call on a device looks up the array's device address with
  * that device current (cudaGetSymbolAddress); make that first call before
- * any stream capture. Every call reuses the same array: calls that can
+ * any stream capture. The address is kept for the life of the process, so
+ * calls after the device's context is destroyed and recreated (e.g. after
+ * cudaDeviceReset) are not supported. Every call reuses the same array: calls that can
  * overlap on the GPU (different streams, or different host threads on one
  * device) race and corrupt each other's sums, so serialise them, e.g. on
  * one stream. */

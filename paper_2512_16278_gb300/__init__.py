@@ -76,11 +76,11 @@ class FlagInfo(ctypes.Structure):
         ("n_flagged", ctypes.c_int64), ("n_used", ctypes.c_int64),
         ("n_near", ctypes.c_int64), ("n_degenerate", ctypes.c_int64),
         ("jacobi_sweeps", ctypes.c_int64), ("jacobi_warp_sweeps", ctypes.c_int64),
-        ("timed_out", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("timed_out", ctypes.c_int32), ("q1_refined", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class UnitIO(ctypes.Structure):

@@ -522,7 +522,7 @@ mraid_status mraid_run_bandpass(mraid_plan_t pl, const void* d_data,
     st = evals_for_q1(pl, (size_t)pl->n_cells, &d_evals);
     if (st != MRAID_OK) return st;
   }
-  e = cudaMemsetAsync(pl->d_sweeps, 0, 2 * sizeof(unsigned long long), pl->stream);
+  e = cudaMemsetAsync(pl->d_sweeps, 0, 3 * sizeof(unsigned long long), pl->stream);
   if (e != cudaSuccess) return cuda_fail(e, "memset");
   bool inter = false;
   st = gram_sums_pass(pl, d_data, nullptr, &inter);
@@ -548,6 +548,9 @@ mraid_status mraid_run_bandpass(mraid_plan_t pl, const void* d_data,
                       cudaMemcpyDeviceToDevice, pl->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&pl->d_info->jacobi_sweeps, pl->d_sweeps, 2 * sizeof(int64_t),
+                        cudaMemcpyDeviceToDevice, pl->stream);
+  if (e == cudaSuccess)  // the FP64 q1 count (low half of the counter)
+    e = cudaMemcpyAsync(&pl->d_info->q1_refined, pl->d_sweeps + 2, sizeof(int32_t),
                         cudaMemcpyDeviceToDevice, pl->stream);
   if (e != cudaSuccess) return cuda_fail(e, "counter copy");
   return enqueue_info_copy(pl, info);

@@ -1119,12 +1119,11 @@ bool eig_needs_tri_workspace(const mraid_plan_s* pl) {
   return !reg && pl->eig_variant >= 2;
 }
 
-bool eig_q1_needs_evals(int n_beam) {
-  return n_beam == 2 || n_beam == 3 || n_beam == 4 || n_beam == 13 || n_beam == 19;
-}
+bool eig_q1_needs_evals(int n_beam) { return n_beam >= 2; }
 
-cudaError_t launch_eig(const mraid_plan_s* pl, const float* d_corr, int64_t n_cells, float* d_evals,
-                       float* d_q1, float* d_stat, cudaStream_t stream) {
+namespace {
+cudaError_t launch_eig_solver(const mraid_plan_s* pl, const float* d_corr, int64_t n_cells,
+                              float* d_evals, float* d_q1, float* d_stat, cudaStream_t stream) {
   const int N = pl->p.n_beam;
   switch (N) {
     case 2: return launch_reg<2>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->d_sweeps, pl->eig_variant, pl->sm_count, stream);
@@ -1150,6 +1149,18 @@ cudaError_t launch_eig(const mraid_plan_s* pl, const float* d_corr, int64_t n_ce
     eig_warp_kernel<<<(unsigned)blocks, 32 * kWarpEigWarps, smem, stream>>>(
         d_corr, n_cells, N, d_evals, d_q1, d_stat, pl->d_sweeps);
   return cudaGetLastError();
+}
+}  // namespace
+
+// The FP32 solver, then the FP64 final step of q1 on the near-degenerate
+// cells (q1_refine.cu) whenever q1 is wanted (callers pass d_evals then).
+cudaError_t launch_eig(const mraid_plan_s* pl, const float* d_corr, int64_t n_cells, float* d_evals,
+                       float* d_q1, float* d_stat, cudaStream_t stream) {
+  cudaError_t e = launch_eig_solver(pl, d_corr, n_cells, d_evals, d_q1, d_stat, stream);
+  if (e != cudaSuccess || !d_q1) return e;
+  if (!d_evals) return cudaErrorInvalidValue;
+  return launch_q1_refine(pl, d_corr, n_cells, d_evals, d_q1,
+                          pl->d_sweeps ? pl->d_sweeps + 2 : nullptr, stream);
 }
 
 cudaError_t launch_eig(const mraid_plan_s* pl, const float* d_corr, int64_t n_cells, float* d_evals,

@@ -49,6 +49,9 @@ struct Workspace {
   size_t evals_cells = 0;
   float* tri = nullptr;     // [cell][tri_workspace_floats(N)]: larger-N eigensolver
   size_t tri_cells = 0;
+  uint32_t* q1_list = nullptr;   // [cell]: cells whose q1 takes the FP64 step
+  size_t q1_list_cells = 0;
+  unsigned* q1_list_n = nullptr;  // entries in q1_list
 };
 
 }  // namespace mraid
@@ -68,7 +71,8 @@ struct mraid_plan_s {
   mraid_flag_info* d_info = nullptr;  // device flag info
   unsigned long long* d_degenerate = nullptr;
   unsigned* d_error = nullptr;        // device error word (bounded waits)
-  unsigned long long* d_sweeps = nullptr;  // Jacobi sweeps: [0] per cell, [1] per warp
+  unsigned long long* d_sweeps = nullptr;  // Jacobi sweeps: [0] per cell, [1] per warp;
+                                           // [2] cells whose q1 took the FP64 step
   mraid_flag_info* h_info = nullptr;  // pinned staging
   mraid_flag_info* pending_info = nullptr;  // user pointer to fill at sync
   mraid::Workspace ws;
@@ -123,7 +127,8 @@ mraid_status check_plan(mraid_plan_t pl);
 mraid_status ensure_tri_workspace(mraid_plan_s* pl, size_t cells);
 // the plan's sums and correlation buffers (and the eigensolver's) for `cells`
 mraid_status ensure_workspace(mraid_plan_s* pl, size_t cells);
-// eigenvalue buffer for the q1 pass when the caller wants q1 but not evals
+// buffers of a q1 request: the FP64 step's cell list, and eigenvalues when
+// the caller wants q1 but not evals (the q1 passes read lambda_1, lambda_2)
 mraid_status evals_for_q1(mraid_plan_s* pl, size_t cells, float** evals);
 // Gram sums + correlation of sub-integrations [sub0, sub0 + n_sub) of d_data
 // (either output may be null; cells relative to sub0)
@@ -194,6 +199,13 @@ cudaError_t launch_eig(const mraid_plan_s* pl, const float* d_corr, int64_t n_ce
 cudaError_t launch_eig(const mraid_plan_s* pl, const float* d_corr, int64_t n_cells,
                        float* d_evals, float* d_q1, float* d_stat, cudaStream_t stream);
 bool eig_supported(int n_beam);
+// q1_refine.cu: FP64 inverse iteration for q1 on cells whose relative gap
+// (lambda_1 - lambda_2) / lambda_1 lies in [1e-6, q1_refine_gap_hi(pl));
+// d_count (or null) counts the refined cells
+float q1_refine_gap_hi(const mraid_plan_s* pl);
+cudaError_t launch_q1_refine(const mraid_plan_s* pl, const float* d_corr, int64_t n_cells,
+                             const float* d_evals, float* d_q1, unsigned long long* d_count,
+                             cudaStream_t stream);
 // eig_large.cu: tridiagonal eigensolver for beam counts without a
 // one-thread kernel; d_work holds tri_workspace_floats(N) floats per cell
 size_t tri_workspace_floats(int n_beam);
@@ -202,7 +214,8 @@ cudaError_t launch_eig_large(const mraid_plan_s* pl, const float* d_corr, int64_
                              cudaStream_t stream);
 // true if the plan's eigensolver needs the tridiagonal workspace
 bool eig_needs_tri_workspace(const mraid_plan_s* pl);
-// true if a q1 request needs d_evals (the q1 pass reads lambda_1 from it)
+// true if a q1 request needs d_evals (the q1 pass reads lambda_1 from it;
+// the FP64 step of q1 reads lambda_1 and lambda_2 for every beam count)
 bool eig_q1_needs_evals(int n_beam);
 // refine.cu
 cudaError_t launch_refine(mraid_plan_s* pl, const float* d_q1, const uint8_t* d_flags,

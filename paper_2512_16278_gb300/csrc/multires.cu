@@ -146,7 +146,7 @@ mraid_status mraid_multires(mraid_plan_t pl, const void* d_data, int32_t n_level
   auto reset_counters = [&]() {
     cudaError_t r = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
     if (r == cudaSuccess)
-      r = cudaMemsetAsync(pl->d_sweeps, 0, 2 * sizeof(unsigned long long), pl->stream);
+      r = cudaMemsetAsync(pl->d_sweeps, 0, 3 * sizeof(unsigned long long), pl->stream);
     return r;
   };
   e = cudaMemsetAsync(pl->d_ml_info, 0, (size_t)n_levels * sizeof(mraid_flag_info), pl->stream);
@@ -191,6 +191,9 @@ mraid_status mraid_multires(mraid_plan_t pl, const void* d_data, int32_t n_level
                         cudaMemcpyDeviceToDevice, pl->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(&pl->d_ml_info[i].jacobi_sweeps, pl->d_sweeps, 2 * sizeof(int64_t),
+                          cudaMemcpyDeviceToDevice, pl->stream);
+    if (e == cudaSuccess)  // the FP64 q1 count (low half of the counter)
+      e = cudaMemcpyAsync(&pl->d_ml_info[i].q1_refined, pl->d_sweeps + 2, sizeof(int32_t),
                           cudaMemcpyDeviceToDevice, pl->stream);
     if (e != cudaSuccess) return cuda_fail(e, "counter copy");
   }

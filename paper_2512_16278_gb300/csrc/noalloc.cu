@@ -24,7 +24,9 @@ constexpr int kNoAllocMaxDevices = 64;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 // Device address of g_noalloc_scratch per device, looked up once with that
-// device current (the host-side symbol is only a stand-in).
+// device current (the host-side symbol is only a stand-in) and kept for the
+// life of the process: a context destroyed and recreated (cudaDeviceReset)
+// may load the module elsewhere, so calls after that are not supported.
 std::atomic<void*> g_noalloc_addr[kNoAllocMaxDevices];
 
 mraid_status scratch_address(int dev, void** out) {
@@ -60,8 +62,8 @@ extern "C" mraid_status mraid_ccm_noalloc(const mraid_params* p, const void* d_d
     return MRAID_ERR_INVALID_ARG;
   }
   if (sub0 < 0 || n_sub < 1 || (int64_t)sub0 + n_sub > p->n_sub) {
-    set_error("mraid_ccm_noalloc: sub-integrations [%d, %d) outside [0, %d)", sub0, sub0 + n_sub,
-              p->n_sub);
+    set_error("mraid_ccm_noalloc: sub-integrations [%d, %lld) outside [0, %d)", sub0,
+              (long long)sub0 + n_sub, p->n_sub);
     return MRAID_ERR_INVALID_ARG;
   }
   const int64_t psum = (int64_t)(p->n_beam + 1) * (p->n_beam + 2) / 2;

@@ -129,8 +129,23 @@ mraid_status ensure_workspace(mraid_plan_s* pl, size_t cells) {
   return MRAID_OK;
 }
 
-// eigenvalue buffer for the q1 pass when the caller wants q1 but not evals
+// buffers of a q1 request: the cell list of the FP64 step, and an
+// eigenvalue buffer when the caller wants q1 but not evals
 mraid_status evals_for_q1(mraid_plan_s* pl, size_t cells, float** evals) {
+  if (pl->ws.q1_list_cells < cells || !pl->ws.q1_list_n) {
+    cudaFree(pl->ws.q1_list);
+    pl->ws.q1_list = nullptr;
+    pl->ws.q1_list_cells = 0;
+    cudaError_t e = cudaMalloc(&pl->ws.q1_list, cells * sizeof(uint32_t));
+    if (e == cudaSuccess && !pl->ws.q1_list_n) e = cudaMalloc(&pl->ws.q1_list_n, sizeof(unsigned));
+    if (e != cudaSuccess) {
+      cudaFree(pl->ws.q1_list);
+      pl->ws.q1_list = nullptr;
+      cudaGetLastError();
+      return cuda_fail(e, "q1 list");
+    }
+    pl->ws.q1_list_cells = cells;
+  }
   if (*evals || !eig_q1_needs_evals(pl->p.n_beam)) return MRAID_OK;
   if (pl->ws.evals_cells < cells) {
     cudaFree(pl->ws.evals);
@@ -397,8 +412,8 @@ mraid_status mraid_plan(const mraid_params* p, void* stream, mraid_plan_t* out) 
   if (e == cudaSuccess) e = cudaMalloc(&pl->d_info, sizeof(mraid_flag_info));
   if (e == cudaSuccess) e = cudaMalloc(&pl->d_degenerate, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&pl->d_error, sizeof(unsigned));
-  if (e == cudaSuccess) e = cudaMalloc(&pl->d_sweeps, 2 * sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_sweeps, 0, 2 * sizeof(unsigned long long), pl->stream);
+  if (e == cudaSuccess) e = cudaMalloc(&pl->d_sweeps, 3 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_sweeps, 0, 3 * sizeof(unsigned long long), pl->stream);
   if (e == cudaSuccess) e = cudaMallocHost(&pl->h_info, sizeof(mraid_flag_info));
   if (e == cudaSuccess && p->keep) {
     e = cudaMalloc(&pl->d_keep, (size_t)p->n_chan);
@@ -492,7 +507,7 @@ mraid_status mraid_run(mraid_plan_t pl, const void* d_data, float* d_evals, floa
   if (st != MRAID_OK) return st;
   cudaError_t e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
   if (e == cudaSuccess)
-    e = cudaMemsetAsync(pl->d_sweeps, 0, 2 * sizeof(unsigned long long), pl->stream);
+    e = cudaMemsetAsync(pl->d_sweeps, 0, 3 * sizeof(unsigned long long), pl->stream);
   if (e != cudaSuccess) return cuda_fail(e, "memset");
   if (d_q1) {
     st = evals_for_q1(pl, (size_t)pl->n_cells, &d_evals);
@@ -508,6 +523,9 @@ mraid_status mraid_run(mraid_plan_t pl, const void* d_data, float* d_evals, floa
                       cudaMemcpyDeviceToDevice, pl->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&pl->d_info->jacobi_sweeps, pl->d_sweeps, 2 * sizeof(int64_t),
+                        cudaMemcpyDeviceToDevice, pl->stream);
+  if (e == cudaSuccess)  // the FP64 q1 count (low half of the counter)
+    e = cudaMemcpyAsync(&pl->d_info->q1_refined, pl->d_sweeps + 2, sizeof(int32_t),
                         cudaMemcpyDeviceToDevice, pl->stream);
   if (e != cudaSuccess) return cuda_fail(e, "counter copy");
   return enqueue_info_copy(pl, info);
@@ -547,7 +565,7 @@ mraid_status mraid_run_host(mraid_plan_t pl, const void* h_data, float* h_stat, 
   if (st != MRAID_OK) return st;
   e = cudaMemsetAsync(pl->d_degenerate, 0, sizeof(unsigned long long), pl->stream);
   if (e == cudaSuccess)
-    e = cudaMemsetAsync(pl->d_sweeps, 0, 2 * sizeof(unsigned long long), pl->stream);
+    e = cudaMemsetAsync(pl->d_sweeps, 0, 3 * sizeof(unsigned long long), pl->stream);
   // The chunk buffer holds [beam][chunk subs * n_samp_sub][chan]; the kernels
   // see it as a block of `chunk` sub-integrations with beam stride
   // chunk * n_samp_sub * n_chan.
@@ -589,6 +607,9 @@ mraid_status mraid_run_host(mraid_plan_t pl, const void* h_data, float* h_stat, 
                         cudaMemcpyDeviceToDevice, pl->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&pl->d_info->jacobi_sweeps, pl->d_sweeps, 2 * sizeof(int64_t),
+                        cudaMemcpyDeviceToDevice, pl->stream);
+  if (e == cudaSuccess)  // the FP64 q1 count (low half of the counter)
+    e = cudaMemcpyAsync(&pl->d_info->q1_refined, pl->d_sweeps + 2, sizeof(int32_t),
                         cudaMemcpyDeviceToDevice, pl->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h_flags, pl->d_flags_full, (size_t)pl->n_cells, cudaMemcpyDeviceToHost, pl->stream);
@@ -816,6 +837,8 @@ void mraid_destroy(mraid_plan_t pl) {
   cudaFree(pl->ws.corr);
   cudaFree(pl->ws.evals);
   cudaFree(pl->ws.tri);
+  cudaFree(pl->ws.q1_list);
+  cudaFree(pl->ws.q1_list_n);
   cudaFree(pl->pol_sums);
   cudaFree(pl->bp_y);
   cudaFree(pl->bp_z);

@@ -198,7 +198,7 @@ mraid_status mraid_run_pol2(mraid_plan_t pl, const void* d_data, float* d_evals,
     st = evals_for_q1(pl, (size_t)pl->n_cells, &d_evals);
     if (st != MRAID_OK) return st;
   }
-  cudaError_t e = cudaMemsetAsync(pl->d_sweeps, 0, 2 * sizeof(unsigned long long), pl->stream);
+  cudaError_t e = cudaMemsetAsync(pl->d_sweeps, 0, 3 * sizeof(unsigned long long), pl->stream);
   if (e != cudaSuccess) return cuda_fail(e, "memset");
   st = pol2_ccm(pl, d_data, nullptr, pl->ws.corr);
   if (st != MRAID_OK) return st;
@@ -210,6 +210,9 @@ mraid_status mraid_run_pol2(mraid_plan_t pl, const void* d_data, float* d_evals,
                       cudaMemcpyDeviceToDevice, pl->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&pl->d_info->jacobi_sweeps, pl->d_sweeps, 2 * sizeof(int64_t),
+                        cudaMemcpyDeviceToDevice, pl->stream);
+  if (e == cudaSuccess)  // the FP64 q1 count (low half of the counter)
+    e = cudaMemcpyAsync(&pl->d_info->q1_refined, pl->d_sweeps + 2, sizeof(int32_t),
                         cudaMemcpyDeviceToDevice, pl->stream);
   if (e != cudaSuccess) return cuda_fail(e, "counter copy");
   return enqueue_info_copy(pl, info);

@@ -1,6 +1,6 @@
 """The benchmark's roofline arithmetic (CPU): algorithmic work per launch
-from the per-cell figures (tensor-core Gram: N n_s bytes of samples in and
-4 N(N+1)/2 bytes of correlation out; eigensolver: the (4/3) N^3 flops of a
+from the per-cell figures (tensor-core Gram: N n_s bytes of samples in, its
+4 N(N+1)/2 bytes of correlation export reported apart; eigensolver: the (4/3) N^3 flops of a
 dense tridiagonal reduction; mask: 5 bytes per cell), achieved = work over
 the launch time, frac = achieved over the peak, and the FP32 peak derived
 from 152 SMs x 128 lanes x 2 flops x the maximum SM clock."""
@@ -19,11 +19,15 @@ def test_fast_block_work_per_launch_and_fractions():
     peaks = {"hbm_gbs": 6785.9, "source": "measured", "fp32_tflops": 80.54784}
     kt = {"gram_tc": (1, 4.5), "eig": (1, 1.5), "flag_clip": (1, 0.1)}
     r = bench.kernel_rooflines(cfg, kt, peaks)
-    gram = cells * (N * S + 4 * N * (N + 1) // 2)
-    assert gram == 16_560_947_200
+    gram = cells * N * S                                  # samples in, read once
+    assert gram == 15_938_355_200
     assert r["gram_tc"]["work_per_launch"] == gram
     assert r["gram_tc"]["achieved"] == pytest.approx(gram / 4.5e-3 / 1e9)
     assert r["gram_tc"]["frac"] == pytest.approx(gram / 4.5e-3 / 1e9 / 6785.9)
+    export = cells * 4 * N * (N + 1) // 2                 # packed r, reported apart
+    assert r["gram_tc"]["export_bytes"] == export
+    assert r["gram_tc"]["frac_incl_export"] == pytest.approx(
+        (gram + export) / 4.5e-3 / 1e9 / 6785.9)
     assert r["gram_tc"]["bound"] == "hbm" and r["gram_tc"]["unit"] == "GB/s"
     flops = cells * 4.0 * N ** 3 / 3.0
     assert r["eig"]["work_per_launch"] == pytest.approx(flops)

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import STAT_TOL, compare_eig, compare_q1, lib
+from gpu_util import Q1_GAP, STAT_TOL, compare_eig, compare_q1, lib
 
 pytestmark = pytest.mark.gpu
 
@@ -47,14 +47,40 @@ def test_fast_block_sampled_parity_and_mask_properties(fast_block):
     idx |= {int(rng.integers(0, cfg.n_sub)) * cfg.n_chan + c for (c, _) in ev["narrow"][:32]}
     for (_, k) in ev["burst"]:
         idx |= {k * cfg.n_chan + int(c) for c in rng.integers(0, cfg.n_chan, size=16)}
+    # every cell whose q1 took the FP64 step (relative gap below 2e-3 in the
+    # FP32 eigenvalues): the count equals the report's, and their q1 is
+    # checked at gaps down to Q1_GAP
+    l1, l2 = evals[:, 0], evals[:, 1]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        gap32 = (l1 - l2) / l1                       # float32, as on the device
+    near = (l1 > 0) & (gap32 >= np.float32(1e-6)) & (gap32 < np.float32(2e-3))
+    assert info["q1_refined"] == int(near.sum()), (info["q1_refined"], int(near.sum()))
+    assert near.sum() > 100, int(near.sum())      # ~0.2 % of noise cells
+    idx |= set(np.flatnonzero(near).tolist())
     idx = np.array(sorted(idx))
     subs, chans = (idx // cfg.n_chan).astype(np.int32), (idx % cfg.n_chan).astype(np.int32)
     o = oracle.cells(None, cfg.n_samp_sub, subs, chans, n_threads=synth.default_threads(),
                      data_ptr=h.data_ptr(), shape=(cfg.n_beam, cfg.n_time, cfg.n_chan))
     compare_eig(evals[idx], o["evals"], "fast block")
-    compare_q1(q1[idx], o["q1"], o["evals"])
+    n_q1, _ = compare_q1(q1[idx], o["q1"], o["evals"])
+    gap = (o["evals"][:, 0] - o["evals"][:, 1]) / o["evals"][:, 0]
+    assert np.sum((gap >= Q1_GAP) & (gap < 1e-3)) > 50   # the band the FP64 step serves
     s_err = np.abs(stat[idx] - o["stat"]) / o["stat"]
     assert s_err.max() <= STAT_TOL, s_err.max()
+
+    # the oracle's own clip iteration on the device's 819 200 statistics:
+    # identical flags away from the threshold and the same fit (the device
+    # sums s and s^2 per thread in FP32 over ~10 cells, then in FP64, so its
+    # mu and sigma carry ~1e-7 relative rounding; the FP64 oracle's far less)
+    f_o, i_o = oracle.flag(stat.astype(np.float64), cfg.n_chan)
+    for key in ("mu", "sigma", "thresh"):
+        assert abs(info[key] - i_o[key]) <= 1e-6 * abs(i_o[key]), (key, info[key], i_o[key])
+    assert info["iterations"] == i_o["iterations"]
+    s64 = stat.astype(np.float64)
+    band = STAT_TOL * s64 + abs(info["thresh"] - i_o["thresh"])
+    at_thresh = np.abs(s64 - i_o["thresh"]) <= band
+    diff = flags != f_o.astype(bool)
+    assert not np.any(diff & ~at_thresh), (int((diff & ~at_thresh).sum()), int(diff.sum()))
 
     # masking properties: the reported fit is the fit of the unmasked cells,
     # every unmasked cell is at or below the final threshold, and the loop

@@ -52,3 +52,37 @@ def test_noalloc_rejects_requests_beyond_its_scratch():
     m.mraid_ccm_noalloc(p, d, 0, 1, out)
     torch.cuda.synchronize()
     assert torch.all(out[:4096, 0] == 1.0)              # r_00 = 1 (zero variance beams)
+
+
+def test_noalloc_capacity_boundary():
+    """The largest request the scratch holds is accepted and equals
+    mraid_ccm; one cell more is refused. With one channel the limit
+    (8 MiB - 256) / (8 * 210) = 4993 cells is a whole number of rows."""
+    import torch
+    m = lib()
+    n_beam, n_chan, n_samp = 19, 1, 16
+    psum = (n_beam + 1) * (n_beam + 2) // 2
+    max_cells = ((8 << 20) - 256) // (8 * psum)
+    assert max_cells == 4993
+    n_sub = max_cells + 1
+    rng = np.random.default_rng(7)
+    data = rng.integers(0, 256, size=(n_beam, n_sub * n_samp, n_chan), dtype=np.uint8)
+    d = torch.from_numpy(data).cuda()
+    np_ = n_beam * (n_beam + 1) // 2
+    with m.Plan(n_beam, n_chan, n_samp, n_sub) as plan:
+        _, ref = plan.ccm(d, sums=False)
+        torch.cuda.synchronize()
+    ref = ref.cpu().numpy()
+    p = m.mraid_default_params(n_beam, n_chan, n_samp, n_sub)
+    stream = torch.cuda.current_stream().cuda_stream
+    for sub0 in (0, 1):
+        out = torch.full((max_cells, np_), float("nan"), device="cuda")
+        m.mraid_ccm_noalloc(p, d, sub0, max_cells, out, stream)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.all(np.isfinite(got)), sub0
+        assert np.abs(got - ref[sub0: sub0 + max_cells]).max() <= CORR_TOL, sub0
+    big = torch.empty((max_cells + 1, np_), device="cuda")
+    with pytest.raises(m.MraidError) as e:
+        m.mraid_ccm_noalloc(p, d, 0, max_cells + 1, big, stream)
+    assert e.value.status == 1 and "scratch" in str(e.value)
