@@ -321,6 +321,8 @@ def bench_f32(m, torch, d_u8, cfg, stream, n_sub, peaks):
     N, C, S = cfg.n_beam, cfg.n_chan, cfg.n_samp_sub
     T = n_sub * S
     x = d_u8.view(N, cfg.n_time, C)[:, :T, :].float().sub_(128.0).div_(20.0).contiguous()
+    # x is made on the current stream; the plan reads it on its own stream
+    stream.wait_stream(torch.cuda.current_stream())
     cells = n_sub * C
     with torch.cuda.stream(stream):
         plan = m.Plan(N, C, S, n_sub, bit_depth=32, stream=stream)
@@ -357,15 +359,15 @@ def bench_f32(m, torch, d_u8, cfg, stream, n_sub, peaks):
         if n_l > 0:
             kms = tot / n_l
             b = in_bytes                                        # samples in
-            x = cells * 4 * (N * (N + 1) // 2)                  # r out (reported apart)
+            xb = cells * 4 * (N * (N + 1) // 2)                 # r out (reported apart)
             a = b / (kms / 1e3) / 1e9
             res["gram_roofline"] = {"bound": "hbm", "kernel": kern, "achieved": a,
                                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                     "frac": a / peaks["hbm_gbs"],
                                     "traffic": kernel_traffic(kern),
                                     "work_per_launch": b, "ms_per_launch": kms,
-                                    "export_bytes": x,
-                                    "frac_incl_export": (b + x) / (kms / 1e3) / 1e9
+                                    "export_bytes": xb,
+                                    "frac_incl_export": (b + xb) / (kms / 1e3) / 1e9
                                     / peaks["hbm_gbs"]}
         out[tag] = res
     out["path"] = ("Gram of per-beam shifted samples: tensor cores with bf16 hi/lo products "
@@ -530,13 +532,13 @@ def bench_pol2(m, torch, h, cfg, stream, steps, peaks):
     gram = None
     if "gram_tc" in kt:
         b = 2 * nb                                      # both polarisations in
-        x = cells * 4 * (N * (N + 1) // 2)              # r out (reported apart)
+        xb = cells * 4 * (N * (N + 1) // 2)             # r out (reported apart)
         a = b / (kt["gram_tc"] / 1e3) / 1e9
         gram = {"bound": "hbm", "kernel": "gram_tc (two polarisations)", "achieved": a,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": a / peaks["hbm_gbs"],
                 "traffic": kernel_traffic("gram_tc_pol2"), "work_per_launch": b,
-                "ms_per_launch": kt["gram_tc"], "export_bytes": x,
-                "frac_incl_export": (b + x) / (kt["gram_tc"] / 1e3) / 1e9 / peaks["hbm_gbs"]}
+                "ms_per_launch": kt["gram_tc"], "export_bytes": xb,
+                "frac_incl_export": (b + xb) / (kt["gram_tc"] / 1e3) / 1e9 / peaks["hbm_gbs"]}
     plan.close()
     del d2, h2
     torch.cuda.empty_cache()

@@ -307,6 +307,32 @@ mraid_status mraid_autotune(mraid_plan_t plan, const void* d_data, int32_t reps,
 mraid_status mraid_set_variant(mraid_plan_t plan, int32_t variant);
 mraid_status mraid_set_eig_variant(mraid_plan_t plan, int32_t variant);
 
+/* Failure detection (no counterpart in the paper). Every wait inside the
+ * tensor-core kernels is bounded: when one runs out the kernel records an
+ * error, waits (with the same bound) for its own bulk copies and MMAs in
+ * flight, frees its tensor memory and returns, so the context stays
+ * usable; mraid_sync then returns MRAID_ERR_TIMEOUT (and the info's
+ * timed_out is 1). Outputs of that call are not valid; later calls are.
+ *   ns: the bound of each wait in nanoseconds, 1e6 .. 6e10 (default 2e9). */
+mraid_status mraid_set_wait_limit(mraid_plan_t plan, int64_t ns);
+
+/* Fault injection for tests of the failure paths, on the host's side of
+ * the launch (no counterpart in the paper; nothing faults the device):
+ *   MRAID_FAULT_NONE:           clear.
+ *   MRAID_FAULT_WITHHOLD_STAGE: in the plan's next tensor-core Gram launch
+ *     (8-bit samples), the first CTA's bulk-copy producer skips its stage
+ *     number arg (counted from 0 over that CTA's stages): the copy is never
+ *     issued, so the consumer's bounded wait for it expires and mraid_sync
+ *     returns MRAID_ERR_TIMEOUT.
+ *   MRAID_FAULT_ALLOC:          the plan's next work-buffer allocation
+ *     fails as out of memory: the call returns MRAID_ERR_OOM (arg unused).
+ * An injection is cleared by the next mraid_sync (MRAID_FAULT_ALLOC also by
+ * the failure it causes). */
+#define MRAID_FAULT_NONE 0
+#define MRAID_FAULT_WITHHOLD_STAGE 1
+#define MRAID_FAULT_ALLOC 2
+mraid_status mraid_inject_fault(mraid_plan_t plan, int32_t kind, int64_t arg);
+
 /* ------------------------------------------------------------------------
  * Batched form: blocks of uneven receiver shapes (different N_beam, N_s,
  * channel counts; e.g. 13-, 19-, 36- and 72-beam systems, Section 5) in one

@@ -27,6 +27,8 @@ __all__ = [
     "mraid_batch_destroy", "UnitIO", "Batch", "mraid_serve_open", "mraid_serve_submit",
     "mraid_serve_poll", "mraid_serve_drain", "mraid_serve_close", "StreamDesc", "BlockResult",
     "Server", "mraid_autotune", "mraid_set_variant", "mraid_set_eig_variant", "tune", "tune_key",
+    "mraid_set_wait_limit", "mraid_inject_fault", "FAULT_NONE", "FAULT_WITHHOLD_STAGE",
+    "FAULT_ALLOC",
     "mraid_refine", "mraid_multires", "BandpassParams", "mraid_default_bandpass_params",
     "mraid_arpls", "mraid_run_bandpass", "mraid_ccm_pol2", "mraid_run_pol2", "STATUS",
 ]
@@ -166,6 +168,8 @@ def load():
                                           ctypes.c_char_p, i32]),
         "mraid_set_variant": (ctypes.c_int, [vp, i32]),
         "mraid_set_eig_variant": (ctypes.c_int, [vp, i32]),
+        "mraid_set_wait_limit": (ctypes.c_int, [vp, ctypes.c_int64]),
+        "mraid_inject_fault": (ctypes.c_int, [vp, i32, ctypes.c_int64]),
         "mraid_refine": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "mraid_multires": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(vp),
                                           ctypes.POINTER(vp), ctypes.POINTER(FlagInfo)]),
@@ -191,6 +195,13 @@ def _ptr(x) -> Optional[int]:
     if x is None:
         return None
     if isinstance(x, int):
+        # 0 is NULL; no buffer lives elsewhere in the first 64 KiB of the
+        # address space: a small count passed by mistake would otherwise
+        # reach a kernel as a pointer
+        if x == 0:
+            return None
+        if 0 < x < (1 << 16):
+            raise ValueError(f"{x} is not a buffer address")
         return x
     if not x.is_contiguous():
         raise ValueError("mraid buffers must be contiguous (row-major) tensors")
@@ -435,6 +446,20 @@ def mraid_set_variant(plan: int, variant: int):
 
 def mraid_set_eig_variant(plan: int, variant: int):
     _check(load().mraid_set_eig_variant(plan, variant), "mraid_set_eig_variant")
+
+
+FAULT_NONE, FAULT_WITHHOLD_STAGE, FAULT_ALLOC = 0, 1, 2
+
+
+def mraid_set_wait_limit(plan: int, ns: int):
+    """Bound (ns) of every wait inside the tensor-core kernels."""
+    _check(load().mraid_set_wait_limit(plan, int(ns)), "mraid_set_wait_limit")
+
+
+def mraid_inject_fault(plan: int, kind: int, arg: int = 0):
+    """Arm a host-side fault for the next launch or allocation (tests of the
+    failure paths; cleared by the next mraid_sync)."""
+    _check(load().mraid_inject_fault(plan, kind, int(arg)), "mraid_inject_fault")
 
 
 def tune_key(n_beam: int, n_chan: int, n_samp_sub: int, bit_depth: int = 8) -> str:

@@ -65,7 +65,6 @@ constexpr int kThreads = 384;
 constexpr int kConvThreads = 128;
 constexpr int kEpiThreads = 128;
 constexpr uint32_t kTmemCols = 512;
-constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 struct TcArgs {
   int n_beam, n_chan, n_samp_sub, sub0, n_sub;
@@ -81,6 +80,8 @@ struct TcArgs {
   float* corr;
   unsigned long long* degenerate;
   unsigned* error;
+  unsigned long long wait_ns;  // bound of every wait (the plan's wait limit)
+  long long withhold;  // fault injection: CTA 0's TMA producer never issues this stage (-1: none)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -125,19 +126,36 @@ __device__ __forceinline__ bool mbar_try_suspend(uint64_t* bar, uint32_t parity)
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase of `parity` to complete; false on timeout or
-// when another role already reported an error.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* error) {
+// Bounded wait for the phase of `parity` to complete; false on timeout
+// (after wait_ns, recorded in the error word) or when another role already
+// reported an error.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* error,
+                                          unsigned long long wait_ns) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = gtimer();
   for (uint32_t i = 0;; ++i) {
     if (mbar_try_suspend(bar, parity)) return true;
     if ((i & 15) == 15) {
       if (*(volatile unsigned*)error) return false;
-      if (gtimer() - t0 > kWaitNs) {
+      if (gtimer() - t0 > wait_ns) {
         atomicOr(error, 1u);
         return false;
       }
+    }
+  }
+}
+// Wait for this CTA's own asynchronous work (bulk copies, MMAs) to land
+// before it exits or frees TMEM: the error word does not cut it short,
+// only the time limit does (and that is recorded).
+__device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity, unsigned* error,
+                                           unsigned long long wait_ns) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try_suspend(bar, parity)) return true;
+    if ((i & 15) == 15 && gtimer() - t0 > wait_ns) {
+      atomicOr(error, 1u);
+      return false;
     }
   }
 }
@@ -199,6 +217,20 @@ __device__ __forceinline__ void tmem_wait_ld() {
 __device__ __forceinline__ void named_sync(int id, int threads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
+// The epilogue warps' wait for the accumulators, decided once for all of
+// them: one thread waits (bounded), the others learn the outcome at a named
+// barrier, so either every epilogue warp goes on to the item or none does.
+// (A warp that gave up alone would leave the others at their next named
+// barrier, which has no time limit.)
+__device__ __forceinline__ bool epi_wait(uint64_t* bar, uint32_t parity, unsigned* error,
+                                         unsigned long long wait_ns, volatile int* go,
+                                         bool leader) {
+  if (leader) *go = mbar_wait(bar, parity, error, wait_ns) ? 1 : 0;
+  named_sync(1, 128);
+  const bool ok = *go != 0;
+  named_sync(1, 128);  // read by all before the leader writes it again
+  return ok;
+}
 
 // Keep the 4 entries of a 32-column chunk whose channel equals c (columns
 // 8u + c, u = 0..3) with compile-time register indices.
@@ -226,6 +258,7 @@ struct Smem {
   uint64_t u8_full[kMaxNU], u8_empty[kMaxNU];
   uint64_t f16_full[kMaxNF], f16_empty[kMaxNF];
   uint64_t acc_full, acc_empty, drain;
+  int epi_go;  // the epilogue leader's wait outcome
   uint32_t tmem_base;
   int32_t s_sum[2][8][kGroupSlots];   // centred row sums G_a per group/channel/slot
   float s_inv[2][8][kGroupSlots];     // 1/sqrt(var_a), 0 if var_a == 0
@@ -323,14 +356,21 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
     // ------------------------------------------------------------ TMA
     if (lane == 0) {
       uint32_t cnt = 0;
+      long long withheld = -1;
       bool ok = true;
       for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
         const int k = (int)(it / chunks), ch0 = (int)(it % chunks) * kBoxCh;
         const int64_t t_item = (int64_t)(g.sub0 + k) * g.n_samp_sub;
         for (int st = 0; st < stages && ok; ++st, ++cnt) {
           const int slot = cnt % kNU;
-          ok = mbar_wait(&s->u8_empty[slot], ((cnt / kNU) & 1) ^ 1, g.error);
+          ok = mbar_wait(&s->u8_empty[slot], ((cnt / kNU) & 1) ^ 1, g.error, g.wait_ns);
           if (!ok) break;
+          if (blockIdx.x == 0 && (long long)cnt == g.withhold) {
+            // injected fault: this stage is never issued, so the converter's
+            // bounded wait for it expires (nothing is in flight for it)
+            withheld = cnt;
+            continue;
+          }
           mbar_expect_tx(&s->u8_full[slot], (uint32_t)u8_stage_bytes);
           tma_load_3d(u8 + (size_t)slot * u8_stage_bytes, &tmap, ch0, (int)(t_item + st * kT), 0,
                       &s->u8_full[slot]);
@@ -338,7 +378,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
       }
       // drain: every issued copy has landed before the CTA may exit
       for (uint32_t d = cnt > kNU ? cnt - kNU : 0; d < cnt; ++d)
-        mbar_wait(&s->u8_full[d % kNU], (d / kNU) & 1, g.error);
+        if ((long long)d != withheld)
+          mbar_drain(&s->u8_full[d % kNU], (d / kNU) & 1, g.error, g.wait_ns);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA
@@ -361,10 +402,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
           int ps = st;
           if constexpr (kPol == 2) ps = st % g.piece_stages;
           const int last = kPol == 2 ? g.piece_stages - 1 : stages - 1;
-          ok = mbar_wait(&s->f16_full[fs], (fcnt / kNF) & 1, g.error);
+          ok = mbar_wait(&s->f16_full[fs], (fcnt / kNF) & 1, g.error, g.wait_ns);
           if (!ok) break;
           if (ps == 0 && pcnt > 0) {
-            ok = mbar_wait(&s->acc_empty, (pcnt - 1) & 1, g.error);
+            ok = mbar_wait(&s->acc_empty, (pcnt - 1) & 1, g.error, g.wait_ns);
             if (!ok) break;
           }
           fence_after();
@@ -388,8 +429,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
           }
         }
       }
-      mma_commit(&s->drain);
-      mbar_wait(&s->drain, 0, g.error);
+      mma_commit(&s->drain);  // every MMA issued has finished before TMEM is freed
+      mbar_drain(&s->drain, 0, g.error, g.wait_ns);
     }
   } else if (warp >= 4 && warp < 8) {
     // ------------------------------------------------------------ convert
@@ -402,8 +443,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
     for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
       for (int st = 0; st < stages && ok; ++st, ++cnt) {
         const int us = cnt % kNU, fs = cnt % kNF;
-        ok = mbar_wait(&s->u8_full[us], (cnt / kNU) & 1, g.error);
-        if (ok) ok = mbar_wait(&s->f16_empty[fs], ((cnt / kNF) & 1) ^ 1, g.error);
+        ok = mbar_wait(&s->u8_full[us], (cnt / kNU) & 1, g.error, g.wait_ns);
+        if (ok) ok = mbar_wait(&s->f16_empty[fs], ((cnt / kNF) & 1) ^ 1, g.error, g.wait_ns);
         if (!ok) break;
         const uint4* src = reinterpret_cast<const uint4*>(u8 + (size_t)us * u8_stage_bytes);
         unsigned char* dst = f16 + (size_t)fs * kF16StageBytes;
@@ -578,7 +619,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
         named_sync(1, kEpiThreads);  // smem tables reused by the next item
       };
       if constexpr (kPol == 1) {
-        ok = mbar_wait(&s->acc_full, pcnt & 1, g.error);
+        ok = epi_wait(&s->acc_full, pcnt & 1, g.error, g.wait_ns, &s->epi_go,
+                      threadIdx.x == 256);
         if (!ok) break;
         ++pcnt;
         fence_after();
@@ -628,7 +670,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
 #pragma unroll
         for (int jb = 0; jb < 16; ++jb) row2[jb] = 0;
         for (int pc = 0; pc < pieces && ok; ++pc, ++pcnt) {
-          ok = mbar_wait(&s->acc_full, pcnt & 1, g.error);
+          ok = epi_wait(&s->acc_full, pcnt & 1, g.error, g.wait_ns, &s->epi_go,
+                        threadIdx.x == 256);
           if (!ok) break;
           fence_after();
 #pragma unroll
@@ -701,6 +744,7 @@ struct SmemF {
   uint64_t bf_full[kF32MaxNF], bf_empty[kF32MaxNF];
   uint64_t shift_full[2];
   uint64_t acc_full, acc_empty, drain;
+  int epi_go;  // the epilogue leader's wait outcome
   uint32_t tmem_base;
   alignas(16) float shift[2][kGroupSlots][kBoxCh];  // by item parity: [beam][channel]
   float s_sum[2][8][kGroupSlots];                   // row sums G_a of the shifted samples
@@ -808,7 +852,7 @@ gram_tc_f32_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
         const int64_t t_item = (int64_t)(g.sub0 + k) * g.n_samp_sub;
         for (int st = 0; st < stages && ok; ++st, ++cnt) {
           const int slot = cnt % kNU;
-          ok = mbar_wait(&s->in_empty[slot], ((cnt / kNU) & 1) ^ 1, g.error);
+          ok = mbar_wait(&s->in_empty[slot], ((cnt / kNU) & 1) ^ 1, g.error, g.wait_ns);
           if (!ok) break;
           mbar_expect_tx(&s->in_full[slot], (uint32_t)in_stage_bytes);
           tma_load_3d(in + (size_t)slot * in_stage_bytes, &tmap, ch0, (int)(t_item + st * kF32T), 0,
@@ -816,7 +860,7 @@ gram_tc_f32_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
         }
       }
       for (uint32_t d = cnt > (uint32_t)kNU ? cnt - kNU : 0; d < cnt; ++d)
-        mbar_wait(&s->in_full[d % kNU], (d / kNU) & 1, g.error);
+        mbar_drain(&s->in_full[d % kNU], (d / kNU) & 1, g.error, g.wait_ns);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA
@@ -832,10 +876,10 @@ gram_tc_f32_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
       for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x, ++item_iter) {
         for (int st = 0; st < stages && ok; ++st, ++fcnt) {
           const int fs = fcnt % NF;
-          ok = mbar_wait(&s->bf_full[fs], (fcnt / NF) & 1, g.error);
+          ok = mbar_wait(&s->bf_full[fs], (fcnt / NF) & 1, g.error, g.wait_ns);
           if (!ok) break;
           if (st == 0 && item_iter > 0) {
-            ok = mbar_wait(&s->acc_empty, (item_iter - 1) & 1, g.error);
+            ok = mbar_wait(&s->acc_empty, (item_iter - 1) & 1, g.error, g.wait_ns);
             if (!ok) break;
           }
           fence_after();
@@ -861,8 +905,8 @@ gram_tc_f32_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
           if (st == stages - 1) mma_commit(&s->acc_full);
         }
       }
-      mma_commit(&s->drain);
-      mbar_wait(&s->drain, 0, g.error);
+      mma_commit(&s->drain);  // every MMA issued has finished before TMEM is freed
+      mbar_drain(&s->drain, 0, g.error, g.wait_ns);
     }
   } else if (warp >= 4 && warp < 8) {
     // ------------------------------------------------------------ convert
@@ -880,8 +924,8 @@ gram_tc_f32_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
       const float4* sh = reinterpret_cast<const float4*>(&s->shift[par][0][0]);
       for (int st = 0; st < stages && ok; ++st, ++cnt) {
         const int us = cnt % kNU, fs = cnt % NF;
-        ok = mbar_wait(&s->in_full[us], (cnt / kNU) & 1, g.error);
-        if (ok) ok = mbar_wait(&s->bf_empty[fs], ((cnt / NF) & 1) ^ 1, g.error);
+        ok = mbar_wait(&s->in_full[us], (cnt / kNU) & 1, g.error, g.wait_ns);
+        if (ok) ok = mbar_wait(&s->bf_empty[fs], ((cnt / NF) & 1) ^ 1, g.error, g.wait_ns);
         if (!ok) break;
         const float4* src = reinterpret_cast<const float4*>(in + (size_t)us * in_stage_bytes);
         if (st == 0) {
@@ -894,7 +938,7 @@ gram_tc_f32_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
             for (int b = 0; b < N; ++b) shw[b * 4 + q] = src[b * kF32T * 4 + q];
             mbar_arrive(&s->shift_full[par]);
           }
-          ok = mbar_wait(&s->shift_full[par], (item_iter >> 1) & 1, g.error);
+          ok = mbar_wait(&s->shift_full[par], (item_iter >> 1) & 1, g.error, g.wait_ns);
           if (!ok) break;
         }
         unsigned char* hi = bf + (size_t)fs * kBfStageBytes;
@@ -932,7 +976,8 @@ gram_tc_f32_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
     uint32_t item_iter = 0;
     bool ok = true;
     for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x, ++item_iter) {
-      ok = mbar_wait(&s->acc_full, item_iter & 1, g.error);
+      ok = epi_wait(&s->acc_full, item_iter & 1, g.error, g.wait_ns, &s->epi_go,
+                    threadIdx.x == 256);
       if (!ok) break;
       fence_after();
       float row[2][kGroupSlots];
@@ -1153,6 +1198,8 @@ cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int su
   a.corr = d_corr;
   a.degenerate = pl->d_degenerate;
   a.error = pl->d_error;
+  a.wait_ns = pl->wait_ns;
+  a.withhold = pl->inject_withhold;
   const int64_t items = (int64_t)n_sub * (p.n_chan / kBoxCh);
   const int grid = (int)(items < pl->sm_count ? items : pl->sm_count);
   cudaError_t e = cudaSuccess;
@@ -1227,6 +1274,8 @@ cudaError_t launch_gram_tc_f32(const mraid_plan_s* pl, const float* d_data, int 
   a.corr = d_corr;
   a.degenerate = pl->d_degenerate;
   a.error = pl->d_error;
+  a.wait_ns = pl->wait_ns;
+  a.withhold = -1;
   const int nf = f32_stages(p.n_beam);
   a.n_u8 = f32_ring_depth(p.n_beam, nf);
   const size_t smem = f32_smem_bytes(p.n_beam, nf, a.n_u8);

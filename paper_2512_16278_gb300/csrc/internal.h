@@ -88,6 +88,9 @@ struct mraid_plan_s {
   mraid::Profiler prof;
   bool force_dp4a = false;  // use the CUDA-core Gram even where tcgen05 fits
   int tc_variant = 0;       // tensor-core Gram variant (tc_default_variant, or autotuned)
+  unsigned long long wait_ns = 2000000000ull;  // bound of every device wait
+  long long inject_withhold = -1;  // MRAID_FAULT_WITHHOLD_STAGE: stage to skip, or -1
+  bool inject_alloc = false;       // MRAID_FAULT_ALLOC armed
   int eig_variant = 3;      // register kernels: 0 = Jacobi, looped rounds; 1 = Jacobi,
                             // unrolled sweep; 2 = Householder + implicit QR, one
                             // step copy per level; 3 = the same, one masked copy

@@ -111,6 +111,11 @@ mraid_status ensure_workspace(mraid_plan_s* pl, size_t cells) {
   mraid_status st = ensure_tri_workspace(pl, cells);
   if (st != MRAID_OK) return st;
   if (pl->ws.cells >= cells) return MRAID_OK;
+  if (pl->inject_alloc) {  // MRAID_FAULT_ALLOC: this allocation fails
+    pl->inject_alloc = false;
+    set_error("workspace allocation: out of memory (injected fault)");
+    return MRAID_ERR_OOM;
+  }
   cudaFree(pl->ws.sums);
   cudaFree(pl->ws.corr);
   pl->ws.sums = nullptr;
@@ -625,6 +630,8 @@ mraid_status mraid_sync(mraid_plan_t pl) {
   if (st != MRAID_OK) return st;
   cudaError_t e = cudaStreamSynchronize(pl->stream);
   if (e != cudaSuccess) return cuda_fail(e, "mraid_sync");
+  pl->inject_withhold = -1;
+  pl->inject_alloc = false;
   prof_fold(pl);
   unsigned dev_err = 0;
   e = cudaMemcpy(&dev_err, pl->d_error, sizeof(unsigned), cudaMemcpyDeviceToHost);
@@ -672,6 +679,41 @@ mraid_status mraid_set_variant(mraid_plan_t pl, int32_t variant) {
   pl->force_dp4a = variant < 0;
   pl->tc_variant = variant < 0 ? 0 : variant;
   return MRAID_OK;
+}
+
+mraid_status mraid_set_wait_limit(mraid_plan_t pl, int64_t ns) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  if (ns < 1000000ll || ns > 60000000000ll) {
+    set_error("mraid_set_wait_limit: %lld ns outside [1e6, 6e10]", (long long)ns);
+    return MRAID_ERR_INVALID_ARG;
+  }
+  pl->wait_ns = (unsigned long long)ns;
+  return MRAID_OK;
+}
+
+mraid_status mraid_inject_fault(mraid_plan_t pl, int32_t kind, int64_t arg) {
+  mraid_status st = check_plan(pl);
+  if (st != MRAID_OK) return st;
+  switch (kind) {
+    case MRAID_FAULT_NONE:
+      pl->inject_withhold = -1;
+      pl->inject_alloc = false;
+      return MRAID_OK;
+    case MRAID_FAULT_WITHHOLD_STAGE:
+      if (arg < 0) {
+        set_error("mraid_inject_fault: stage %lld < 0", (long long)arg);
+        return MRAID_ERR_INVALID_ARG;
+      }
+      pl->inject_withhold = arg;
+      return MRAID_OK;
+    case MRAID_FAULT_ALLOC:
+      pl->inject_alloc = true;
+      return MRAID_OK;
+    default:
+      set_error("mraid_inject_fault: unknown kind %d", kind);
+      return MRAID_ERR_INVALID_ARG;
+  }
 }
 
 mraid_status mraid_set_eig_variant(mraid_plan_t pl, int32_t variant) {

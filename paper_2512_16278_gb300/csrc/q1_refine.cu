@@ -161,7 +161,7 @@ __device__ __forceinline__ void r_times(const float* __restrict__ rp, int N, int
 
 // The cells to refine: lane per cell, warp-aggregated appends to the list.
 __global__ void q1_select_kernel(const float* __restrict__ evals, int64_t n_cells, int N,
-                                 float gap_hi, uint32_t* __restrict__ list,
+                                 float gap_hi, uint32_t* __restrict__ list, int64_t list_cap,
                                  unsigned* __restrict__ count) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -180,14 +180,16 @@ __global__ void q1_select_kernel(const float* __restrict__ evals, int64_t n_cell
     unsigned at = 0;
     if (lane == 0) at = atomicAdd(count, (unsigned)__popc(sel));
     at = __shfl_sync(0xffffffffu, at, 0);
-    if (near) list[at + __popc(sel & ((1u << lane) - 1u))] = (uint32_t)cell;
+    const int64_t slot = (int64_t)at + __popc(sel & ((1u << lane) - 1u));
+    if (near && slot < list_cap) list[slot] = (uint32_t)cell;
   }
 }
 
 // One warp per listed cell.
 __global__ void __launch_bounds__(32 * kRefineMaxWarps)
-q1_refine_kernel(const float* __restrict__ corr, int N, const float* __restrict__ evals,
-                 float* __restrict__ q1, const uint32_t* __restrict__ list,
+q1_refine_kernel(const float* __restrict__ corr, int64_t n_cells, int N,
+                 const float* __restrict__ evals, float* __restrict__ q1,
+                 const uint32_t* __restrict__ list, int64_t list_cap,
                  const unsigned* __restrict__ count, unsigned long long* __restrict__ refined) {
   extern __shared__ double rsm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -216,9 +218,10 @@ q1_refine_kernel(const float* __restrict__ corr, int N, const float* __restrict_
   float* x = dinv + N;
   float* y = x + N;
   const int NP = N * (N + 1) / 2;
-  const unsigned n_list = *count;
-  for (unsigned w = blockIdx.x * warps + wib; w < n_list; w += gridDim.x * warps) {
+  const int64_t n_list = (int64_t)*count < list_cap ? (int64_t)*count : list_cap;
+  for (int64_t w = (int64_t)blockIdx.x * warps + wib; w < n_list; w += (int64_t)gridDim.x * warps) {
     const int64_t cell = list[w];
+    if (cell >= n_cells) continue;
     const float lambda1 = evals[cell * N];
     const float* rp = corr + cell * NP;
     float delta = 1e-5f * fabsf(lambda1);
@@ -371,7 +374,8 @@ cudaError_t launch_q1_refine(const mraid_plan_s* pl, const float* d_corr, int64_
     const int64_t want = (n_cells + 255) / 256;
     const int64_t cap = (int64_t)pl->sm_count * 8;
     q1_select_kernel<<<(unsigned)(want < cap ? want : cap), 256, 0, stream>>>(
-        d_evals, n_cells, N, q1_refine_gap_hi(pl), pl->ws.q1_list, pl->ws.q1_list_n);
+        d_evals, n_cells, N, q1_refine_gap_hi(pl), pl->ws.q1_list,
+        (int64_t)pl->ws.q1_list_cells, pl->ws.q1_list_n);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -386,7 +390,8 @@ cudaError_t launch_q1_refine(const mraid_plan_s* pl, const float* d_corr, int64_
   // get one warp each
   const int64_t blocks = (int64_t)pl->sm_count * (warps >= 4 ? 4 : 8);
   q1_refine_kernel<<<(unsigned)blocks, 32 * warps, smem, stream>>>(
-      d_corr, N, d_evals, d_q1, pl->ws.q1_list, pl->ws.q1_list_n, d_count);
+      d_corr, n_cells, N, d_evals, d_q1, pl->ws.q1_list, (int64_t)pl->ws.q1_list_cells,
+      pl->ws.q1_list_n, d_count);
   return cudaGetLastError();
 }
 

@@ -98,9 +98,12 @@ def test_binding_rejects_non_contiguous_buffers():
     import paper_2512_16278_gb300 as m
     t = torch.zeros(6, 4)
     assert m._ptr(t) == t.data_ptr()
-    assert m._ptr(None) is None and m._ptr(1234) == 1234
+    assert m._ptr(None) is None and m._ptr(0x3abdac00) == 0x3abdac00
     with pytest.raises(ValueError):
         m._ptr(t.t())
+    # a small integer (a count passed where a buffer belongs) is no address
+    with pytest.raises(ValueError):
+        m._ptr(4096)
 
 
 def test_tuning_cache_key_separates_sample_types():
