@@ -166,7 +166,8 @@ def gpu_index(local_rank):
 # ------------------------------------------------------------- peaks
 
 EIG_NAMES = {0: "jacobi (looped rounds)", 1: "jacobi (unrolled sweep)",
-             2: "householder + implicit QR", 3: "householder + implicit QR (compact)"}
+             2: "householder + implicit QR", 3: "householder + implicit QR (compact)",
+             4: "householder + implicit QR, split (reduction and q1 / QR kernels)"}
 SMS, FP32_LANES = 152, 128          # GB300: SMs, FP32 lanes per SM
 
 

@@ -302,8 +302,11 @@ mraid_status mraid_autotune(mraid_plan_t plan, const void* d_data, int32_t reps,
  * looped rounds; 1 = Jacobi, unrolled sweep; 2 = Householder reduction to
  * tridiagonal form, implicit QR with the Wilkinson shift (one unrolled step
  * per deflation level), q1 by inverse iteration on the tridiagonal matrix;
- * 3 = the same with one masked QR step for all levels (smaller code; the
- * default). All give the same outputs to the stated tolerances. */
+ * 3 = the same with one masked QR step for all levels (smaller code);
+ * 4 = the same arithmetic split over two kernels: the reduction, lambda_1
+ * (Newton's method on det(T - x I)) and q1 in one, QR on T for all
+ * eigenvalues in a second with few registers (the default). All give the
+ * same outputs to the stated tolerances. */
 mraid_status mraid_set_variant(mraid_plan_t plan, int32_t variant);
 mraid_status mraid_set_eig_variant(mraid_plan_t plan, int32_t variant);
 

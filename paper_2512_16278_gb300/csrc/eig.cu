@@ -789,6 +789,328 @@ eig_tri_kernel(const float* __restrict__ corr, int64_t n_cells, float* __restric
 }
 
 // ---------------------------------------------------------------------------
+// Split tridiagonal route (variant 4): the same arithmetic as the route
+// above in two kernels. The one-kernel route holds the whole packed matrix
+// in registers during the reduction (255 registers, 8 warps per SM), and the
+// implicit QR steps that follow, two thirds of its time on the FAST block
+// (0.36 ms reduction, 1.03 ms QR, 0.13 ms q1), ran at that occupancy too.
+// Here the reduction kernel writes T (d and e, [2N][cell]) and finds
+// lambda_1 of T itself, by Newton's method on det(T - x I) from Gershgorin's
+// upper bound: above every eigenvalue the pivots of T - x I are all
+// negative, (log det)' = sum_j 1 / (x - lambda_j), and the iterates fall
+// monotonically to lambda_1, so sigma = lambda_1 + delta for the inverse
+// iteration stays above it. It then computes q1 while the reflectors are in
+// its shared memory. A second kernel with a few dozen registers runs QR on
+// T for all eigenvalues at several times the occupancy.
+constexpr int kNewtonMax = 40;
+constexpr int kEigQrThreads = 128;
+
+template <int N>
+__global__ void __launch_bounds__(kEigThreads)
+eig_tri_a_kernel(const float* __restrict__ corr, int64_t n_cells, float* __restrict__ de,
+                 float* __restrict__ q1) {
+  constexpr int NP = Slots<N>::NP;
+  constexpr int STR = Slots<N>::STR;
+  extern __shared__ float sm[];
+  const int64_t cell0 = (int64_t)blockIdx.x * kEigThreads;
+  const int ncell = (int)min((int64_t)kEigThreads, n_cells - cell0);
+  stage_rows<NP, STR>(sm, corr + cell0 * NP, ncell);
+  const bool active = (int)threadIdx.x < ncell;
+  float* row = sm + threadIdx.x * STR;
+  const uint32_t rowa = static_cast<uint32_t>(__cvta_generic_to_shared(row));
+  auto pk = [](int a, int b) { return a * N - a * (a - 1) / 2 + (b - a); };  // a <= b
+  float a[NP];
+  static_for<NP>([&](auto ee) {
+    constexpr int e = decltype(ee)::value;
+    a[e] = active ? row[e] : (Slots<N>::row_of(e) == Slots<N>::col_of(e) ? 1.f : 0.f);
+  });
+  // Reflector k (acting on indices k+1..N-1) is stored at row[voff(k) ..],
+  // its beta at row[NP - 1 - k]; the staged input is already in registers.
+  auto voff = [](int k) { return k * (N - 1) - k * (k - 1) / 2; };
+  float d[N], e[N];
+  static_for<(N > 2 ? N - 2 : 0)>([&](auto kk) {
+    constexpr int k = decltype(kk)::value;
+    constexpr int m = N - k - 1;
+    float v[m], p[m];
+    float s2 = 0.f;
+    static_for<m>([&](auto ii) {
+      constexpr int i = decltype(ii)::value;
+      v[i] = a[pk(k, k + 1 + i)];
+      s2 = fmaf(v[i], v[i], s2);
+    });
+    const float x0 = v[0];
+    const float nx = s2 > 0.f ? s2 * rsqrtf(s2) : 0.f;
+    const float alpha = x0 >= 0.f ? -nx : nx;
+    v[0] = x0 - alpha;                                   // |v0| = |x0| + |x|
+    const float vtv = 2.f * nx * (nx + fabsf(x0));
+    const bool refl = vtv > 1e-30f;
+    const float beta = refl ? __fdividef(2.f, vtv) : 0.f;
+    d[k] = a[pk(k, k)];
+    e[k] = refl ? alpha : x0;
+    static_for<m>([&](auto ii) { sts(rowa + 4 * (voff(k) + decltype(ii)::value), v[decltype(ii)::value]); });
+    sts(rowa + 4 * (NP - 1 - k), beta);
+    // p = beta A' v over the trailing block (packed, each entry used twice)
+    static_for<m>([&](auto ii) { p[decltype(ii)::value] = 0.f; });
+    static_for<m>([&](auto ii) {
+      constexpr int i = decltype(ii)::value;
+      static_for<m - i>([&](auto jj) {
+        constexpr int j = i + decltype(jj)::value;
+        const float aij = a[pk(k + 1 + i, k + 1 + j)];
+        p[i] = fmaf(aij, v[j], p[i]);
+        if constexpr (j != i) p[j] = fmaf(aij, v[i], p[j]);
+      });
+    });
+    float vp = 0.f;
+    static_for<m>([&](auto ii) {
+      constexpr int i = decltype(ii)::value;
+      p[i] *= beta;
+      vp = fmaf(v[i], p[i], vp);
+    });
+    const float kh = 0.5f * beta * vp;
+    static_for<m>([&](auto ii) { p[decltype(ii)::value] = fmaf(-kh, v[decltype(ii)::value], p[decltype(ii)::value]); });
+    // A' -= v w^T + w v^T (w in p)
+    static_for<m>([&](auto ii) {
+      constexpr int i = decltype(ii)::value;
+      static_for<m - i>([&](auto jj) {
+        constexpr int j = i + decltype(jj)::value;
+        float& x = a[pk(k + 1 + i, k + 1 + j)];
+        x = fmaf(-v[i], p[j], fmaf(-p[i], v[j], x));
+      });
+    });
+  });
+  d[N - 2] = a[pk(N - 2, N - 2)];
+  d[N - 1] = a[pk(N - 1, N - 1)];
+  e[N - 2] = a[pk(N - 2, N - 1)];
+  e[N - 1] = 0.f;
+  float td[N], te[N];
+  static_for<N>([&](auto ii) {
+    td[decltype(ii)::value] = d[decltype(ii)::value];
+    te[decltype(ii)::value] = e[decltype(ii)::value];
+  });
+
+  if (!active) return;
+  const int64_t cell = cell0 + threadIdx.x;
+  // T for the QR kernel, d then e, one row of n_cells floats per entry
+  static_for<N>([&](auto ii) {
+    constexpr int i = decltype(ii)::value;
+    de[(int64_t)i * n_cells + cell] = td[i];
+    de[(int64_t)(N + i) * n_cells + cell] = te[i];
+  });
+  if (!q1) return;
+  // lambda_1 of T: Newton on det(T - x I) from Gershgorin's upper bound
+  float lam = -3.0e38f;
+  static_for<N>([&](auto ii) {
+    constexpr int i = decltype(ii)::value;
+    float g = td[i] + fabsf(te[i]);
+    if constexpr (i > 0) g += fabsf(te[i - 1]);
+    lam = fmaxf(lam, g);
+  });
+  for (int it = 0; it < kNewtonMax; ++it) {
+    // pivots q_i of T - lam I, their derivatives q_i' in lam, and
+    // sum q_i' / q_i = (log det)'
+    float q = td[0] - lam, dq = -1.f;
+    bool hit = q == 0.f;
+    float r = __fdividef(1.f, q);
+    float sum = dq * r;
+    static_for<N - 1>([&](auto ii) {
+      constexpr int i = decltype(ii)::value + 1;
+      const float e2 = te[i - 1] * te[i - 1];
+      q = (td[i] - lam) - e2 * r;
+      dq = fmaf(e2 * dq, r * r, -1.f);
+      hit = hit || q == 0.f;
+      r = __fdividef(1.f, q);
+      sum = fmaf(dq, r, sum);
+    });
+    if (hit) break;  // lam is an eigenvalue of T, hence lambda_1
+    const float step = __fdividef(1.f, sum);
+    if (!(step > 0.f)) break;
+    lam -= step;
+    if (!(step > 1e-7f * fabsf(lam))) break;
+  }
+
+  // q1: inverse iteration with sigma I - T = L D L^T (sigma just above
+  // lambda_1, so every pivot is positive), then x = Q y.
+  const float lambda1 = lam;
+  float delta = fmaxf(4e-5f * fabsf(lambda1), 1e-6f);
+  float dinv[N], lo[N];
+  bool ok = false;
+  for (int attempt = 0; attempt < 4 && !ok; ++attempt, delta *= 16.f) {
+    const float sig = lambda1 + delta;
+    ok = true;
+    float piv = sig - td[0];
+    static_for<N>([&](auto ii) {
+      constexpr int i = decltype(ii)::value;
+      if constexpr (i > 0) {
+        const float l = -te[i - 1] * dinv[i - 1];
+        lo[i] = l;
+        piv = fmaf(-l * l, piv, sig - td[i]);
+      }
+      ok = ok && piv > 0.f;
+      dinv[i] = __fdividef(1.f, fmaxf(piv, 1e-30f));
+    });
+  }
+  float y[N];
+  static_for<N>([&](auto ii) {
+    constexpr int i = decltype(ii)::value;
+    y[i] = 1.f + 0.25f * (float)((i * 7) % 5);
+  });
+  for (int it = 0; it < 3; ++it) {
+    static_for<N - 1>([&](auto ii) {
+      constexpr int i = decltype(ii)::value + 1;
+      y[i] = fmaf(-lo[i], y[i - 1], y[i]);
+    });
+    static_for<N>([&](auto ii) { y[decltype(ii)::value] *= dinv[decltype(ii)::value]; });
+    static_for<N - 1>([&](auto ii) {
+      constexpr int i = N - 2 - decltype(ii)::value;
+      y[i] = fmaf(-lo[i + 1], y[i + 1], y[i]);
+    });
+    float nn = 0.f;
+    static_for<N>([&](auto ii) { nn = fmaf(y[decltype(ii)::value], y[decltype(ii)::value], nn); });
+    const float inv = rsqrtf(fmaxf(nn, 1e-37f));
+    static_for<N>([&](auto ii) { y[decltype(ii)::value] *= inv; });
+  }
+  // x = H_0 H_1 ... H_{N-3} y, the last reflector first
+  static_for<(N > 2 ? N - 2 : 0)>([&](auto kk) {
+    constexpr int k = N - 3 - decltype(kk)::value;
+    constexpr int m = N - k - 1;
+    float vk[m];
+    float t = 0.f;
+    static_for<m>([&](auto ii) {
+      constexpr int i = decltype(ii)::value;
+      vk[i] = lds(rowa + 4 * (voff(k) + i));
+      t = fmaf(vk[i], y[k + 1 + i], t);
+    });
+    t *= lds(rowa + 4 * (NP - 1 - k));
+    static_for<m>([&](auto ii) {
+      constexpr int i = decltype(ii)::value;
+      y[k + 1 + i] = fmaf(-t, vk[i], y[k + 1 + i]);
+    });
+  });
+  float best = 0.f, sgn = 1.f;
+  static_for<N>([&](auto kk) {
+    const float v = y[decltype(kk)::value];
+    if (fabsf(v) > best) {
+      best = fabsf(v);
+      sgn = v < 0.f ? -1.f : 1.f;
+    }
+  });
+  if (!ok) sgn = __int_as_float(0x7fc00000);  // NaN marks a failed factor
+  static_for<N>([&](auto kk) { q1[cell * N + decltype(kk)::value] = sgn * y[decltype(kk)::value]; });
+}
+
+
+template <int N, bool kCompact>
+__global__ void __launch_bounds__(kEigQrThreads)
+eig_qr_kernel(const float* __restrict__ de, int64_t n_cells, float* __restrict__ evals,
+              float* __restrict__ stat, unsigned long long* __restrict__ step_count) {
+  const int64_t cell = (int64_t)blockIdx.x * kEigQrThreads + threadIdx.x;
+  const bool active = cell < n_cells;
+  float d[N], e[N];
+  static_for<N>([&](auto ii) {
+    constexpr int i = decltype(ii)::value;
+    d[i] = active ? de[(int64_t)i * n_cells + cell] : 1.f;
+    e[i] = active ? de[(int64_t)(N + i) * n_cells + cell] : 0.f;
+  });
+  // Implicit QR on T. |e| <= 1e-6 ||T||_F counts as zero: by Weyl's
+  // inequality this moves no eigenvalue by more than 1e-6 sqrt(N) lambda_max.
+  float an2 = 0.f;
+  static_for<N>([&](auto ii) {
+    constexpr int i = decltype(ii)::value;
+    an2 = fmaf(d[i], d[i], an2);
+    if constexpr (i < N - 1) an2 = fmaf(2.f * e[i], e[i], an2);
+  });
+  const float thr2 = 1e-12f * an2;
+  int steps = 0;
+  if constexpr (!kCompact) {
+    // one unrolled copy of the QR step per deflation level m: the warp
+    // moves to the next level once every lane has deflated this one
+    static_for<N - 1>([&](auto mm) {
+      constexpr int m = N - 1 - decltype(mm)::value;
+      for (int it = 0; it < kMaxQrIter; ++it) {
+        const bool need = active && e[m - 1] * e[m - 1] > thr2;
+        if (!__any_sync(0xffffffffu, need)) break;
+        if (need) {
+          int l = 0;  // top of the unreduced block that ends at m
+          static_for<m - 1>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            if (e[i] * e[i] <= thr2) l = i + 1;
+          });
+          qr_step<N>(d, e, l, m, d[m - 1], d[m], e[m - 1]);
+          ++steps;
+        }
+      }
+    });
+  } else {
+    // one copy of the step over the whole length, masked to each lane's
+    // unreduced block [l, m]: lanes deflate at their own pace
+    for (int it = 0; it < kMaxQrIter * (N - 1); ++it) {
+      // one pass from the top: m is one past the last non-negligible e
+      // (the bottom of the lowest unreduced block), l one past the last
+      // negligible e above it (its top)
+      int m = 0, l = 0, last_small = 0;
+      float dm1 = 0.f, dm = 0.f, em = 0.f;
+      static_for<N - 1>([&](auto ii) {
+        constexpr int i = decltype(ii)::value;
+        if (e[i] * e[i] > thr2) {
+          m = i + 1;
+          l = last_small;
+          dm1 = d[i];
+          dm = d[i + 1];
+          em = e[i];
+        } else {
+          last_small = i + 1;
+        }
+      });
+      const bool need = active && m > 0;
+      if (!__any_sync(0xffffffffu, need)) break;
+      // The lowest unreduced block moves up as eigenvalues deflate; the
+      // warp's deepest block bounds the positions a step can touch, so
+      // copies of the step over the first third and two thirds of the
+      // positions serve the later steps (same arithmetic, fewer masked
+      // positions issued).
+      const int mw = __reduce_max_sync(0xffffffffu, need ? m : 0);
+      if (need) {
+        if constexpr (N - 1 >= 6) {
+          constexpr int K1 = (N - 1) / 3, K2 = 2 * (N - 1) / 3;
+          if (mw <= K1)
+            qr_step<N, K1>(d, e, l, m, dm1, dm, em);
+          else if (mw <= K2)
+            qr_step<N, K2>(d, e, l, m, dm1, dm, em);
+          else
+            qr_step<N>(d, e, l, m, dm1, dm, em);
+        } else {
+          qr_step<N>(d, e, l, m, dm1, dm, em);
+        }
+        ++steps;
+      }
+    }
+  }
+  if (step_count) {
+    const int wmax = __reduce_max_sync(0xffffffffu, steps);
+    const unsigned wsum = __reduce_add_sync(0xffffffffu, (unsigned)steps);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&step_count[0], (unsigned long long)wsum);
+      atomicAdd(&step_count[1], (unsigned long long)wmax);
+    }
+  }
+  // odd-even transposition sort, descending
+  static_for<N>([&](auto pp) {
+    constexpr int pass = decltype(pp)::value;
+    static_for<(N - (pass & 1)) / 2>([&](auto kk) {
+      constexpr int k = (pass & 1) + 2 * decltype(kk)::value;
+      const float hi = fmaxf(d[k], d[k + 1]), lo = fminf(d[k], d[k + 1]);
+      d[k] = hi;
+      d[k + 1] = lo;
+    });
+  });
+  if (!active) return;
+  float ss = 0.f;
+  static_for<N>([&](auto kk) { ss = fmaf(d[decltype(kk)::value], d[decltype(kk)::value], ss); });
+  stat[cell] = ss > 0.f ? d[0] * d[0] / ss : 0.f;
+  if (evals) static_for<N>([&](auto kk) { evals[cell * N + decltype(kk)::value] = d[decltype(kk)::value]; });
+}
+
+// ---------------------------------------------------------------------------
 // Larger N (PAF-like receivers): one warp per matrix, the packed upper
 // triangle in shared memory, rotated in place. Round r of the circle
 // schedule pairs index M-1 with r and (r+i, r-i) mod (M-1) for i >= 1 (index
@@ -1052,11 +1374,25 @@ eig_warp_kernel(const float* __restrict__ corr, int64_t n_cells, int N, float* _
 template <int N>
 cudaError_t launch_reg(const float* d_corr, int64_t n_cells, float* d_evals, float* d_q1,
                        float* d_stat, unsigned long long* sweep_count, int variant, int sm_count,
-                       cudaStream_t stream) {
+                       float* d_de, cudaStream_t stream) {
   constexpr int STR = Slots<N>::STR;
   const size_t smem = (size_t)kEigThreads * STR * sizeof(float);
   const int64_t blocks = (n_cells + kEigThreads - 1) / kEigThreads;
   cudaError_t e;
+  if (variant == 4 && !d_de) variant = 3;  // no T buffer: the one-kernel route
+  if (variant == 4) {
+    e = cudaFuncSetAttribute(eig_tri_a_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    if (blocks > 0)
+      eig_tri_a_kernel<N><<<(unsigned)blocks, kEigThreads, smem, stream>>>(d_corr, n_cells, d_de,
+                                                                             d_q1);
+    const int64_t qb = (n_cells + kEigQrThreads - 1) / kEigQrThreads;
+    if (qb > 0)
+      eig_qr_kernel<N, true><<<(unsigned)qb, kEigQrThreads, 0, stream>>>(d_de, n_cells, d_evals,
+                                                                           d_stat, sweep_count);
+    return cudaGetLastError();
+  }
   if (variant == 2 || variant == 3) {
     auto kern = variant == 2 ? eig_tri_kernel<N, false> : eig_tri_kernel<N, true>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1126,11 +1462,11 @@ cudaError_t launch_eig_solver(const mraid_plan_s* pl, const float* d_corr, int64
                               float* d_evals, float* d_q1, float* d_stat, cudaStream_t stream) {
   const int N = pl->p.n_beam;
   switch (N) {
-    case 2: return launch_reg<2>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->d_sweeps, pl->eig_variant, pl->sm_count, stream);
-    case 3: return launch_reg<3>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->d_sweeps, pl->eig_variant, pl->sm_count, stream);
-    case 4: return launch_reg<4>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->d_sweeps, pl->eig_variant, pl->sm_count, stream);
-    case 13: return launch_reg<13>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->d_sweeps, pl->eig_variant, pl->sm_count, stream);
-    case 19: return launch_reg<19>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->d_sweeps, pl->eig_variant, pl->sm_count, stream);
+    case 2: return launch_reg<2>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->d_sweeps, pl->eig_variant, pl->sm_count, pl->ws.de_cells >= (size_t)n_cells ? pl->ws.de : nullptr, stream);
+    case 3: return launch_reg<3>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->d_sweeps, pl->eig_variant, pl->sm_count, pl->ws.de_cells >= (size_t)n_cells ? pl->ws.de : nullptr, stream);
+    case 4: return launch_reg<4>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->d_sweeps, pl->eig_variant, pl->sm_count, pl->ws.de_cells >= (size_t)n_cells ? pl->ws.de : nullptr, stream);
+    case 13: return launch_reg<13>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->d_sweeps, pl->eig_variant, pl->sm_count, pl->ws.de_cells >= (size_t)n_cells ? pl->ws.de : nullptr, stream);
+    case 19: return launch_reg<19>(d_corr, n_cells, d_evals, d_q1, d_stat, pl->d_sweeps, pl->eig_variant, pl->sm_count, pl->ws.de_cells >= (size_t)n_cells ? pl->ws.de : nullptr, stream);
     default: break;
   }
   if (eig_needs_tri_workspace(pl)) {

@@ -49,6 +49,8 @@ struct Workspace {
   size_t evals_cells = 0;
   float* tri = nullptr;     // [cell][tri_workspace_floats(N)]: larger-N eigensolver
   size_t tri_cells = 0;
+  float* de = nullptr;      // [2N][cell]: T of the split tridiagonal route (eig variant 4)
+  size_t de_cells = 0;
   uint32_t* q1_list = nullptr;   // [cell]: cells whose q1 takes the FP64 step
   size_t q1_list_cells = 0;
   unsigned* q1_list_n = nullptr;  // entries in q1_list
@@ -91,9 +93,11 @@ struct mraid_plan_s {
   unsigned long long wait_ns = 2000000000ull;  // bound of every device wait
   long long inject_withhold = -1;  // MRAID_FAULT_WITHHOLD_STAGE: stage to skip, or -1
   bool inject_alloc = false;       // MRAID_FAULT_ALLOC armed
-  int eig_variant = 3;      // register kernels: 0 = Jacobi, looped rounds; 1 = Jacobi,
+  int eig_variant = 4;      // register kernels: 0 = Jacobi, looped rounds; 1 = Jacobi,
                             // unrolled sweep; 2 = Householder + implicit QR, one
-                            // step copy per level; 3 = the same, one masked copy
+                            // step copy per level; 3 = the same, one masked copy;
+                            // 4 = the same split over two kernels (reduction and
+                            // q1 / QR), the default
   double* d_refine_part = nullptr;   // eigenvector refinement: [block][N][3]
   float* d_refine_thresh = nullptr;  // [N]
   double* d_refine_ms = nullptr;     // [N][2] when the caller passes none
@@ -181,7 +185,7 @@ bool gram_tc_supported(const mraid_plan_s* pl, const void* d_data, int n_pol = 1
 int tc_variant_samples(int v);
 int tc_default_variant(int n_beam);
 constexpr int kTcVariants = 8;
-constexpr int kEigVariants = 4;  // register eigensolvers (see eig_variant)
+constexpr int kEigVariants = 5;  // register eigensolvers (see eig_variant)
 // d_sums8 (instead of d_sums): the sums in the interleaved layout
 // [cell / 8][P][cell % 8], which the kernel writes in 64-byte runs
 cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int sub0, int n_sub,

@@ -93,7 +93,21 @@ static void prof_fold(mraid_plan_s* pl) {
 mraid_status ensure_tri_workspace(mraid_plan_s* pl, size_t cells) {
   const int N = pl->p.n_beam;
   const bool reg = N == 2 || N == 3 || N == 4 || N == 13 || N == 19;
-  if (reg || pl->ws.tri_cells >= cells) return MRAID_OK;
+  if (reg) {  // T of the split tridiagonal route: 2N floats per cell
+    if (pl->ws.de_cells >= cells) return MRAID_OK;
+    cudaFree(pl->ws.de);
+    pl->ws.de = nullptr;
+    pl->ws.de_cells = 0;
+    cudaError_t e = cudaMalloc(&pl->ws.de, cells * 2 * (size_t)N * sizeof(float));
+    if (e != cudaSuccess) {
+      pl->ws.de = nullptr;
+      cudaGetLastError();
+      return cuda_fail(e, "eigensolver workspace");
+    }
+    pl->ws.de_cells = cells;
+    return MRAID_OK;
+  }
+  if (pl->ws.tri_cells >= cells) return MRAID_OK;
   cudaFree(pl->ws.tri);
   pl->ws.tri = nullptr;
   pl->ws.tri_cells = 0;
@@ -879,6 +893,7 @@ void mraid_destroy(mraid_plan_t pl) {
   cudaFree(pl->ws.corr);
   cudaFree(pl->ws.evals);
   cudaFree(pl->ws.tri);
+  cudaFree(pl->ws.de);
   cudaFree(pl->ws.q1_list);
   cudaFree(pl->ws.q1_list_n);
   cudaFree(pl->pol_sums);
