@@ -239,15 +239,16 @@ def test_fast_block_two_polarisations(fast_block):
     assert np.mean([F[k, c] for (k, c) in lone]) < 0.05
 
 
-def test_fast_block_float32_twenty_sub_integrations(fast_block):
-    """Float32 input (bit_depth 32) at the size the benchmark times: the
-    first 20 sub-integrations of the block as (x - 128) / 20 (6.4 GB on the
-    device), through mraid_run on the tensor cores; sampled cells against
-    the oracle's FP64 covariance path, and the masking properties."""
+def test_fast_block_float32_full_size(fast_block):
+    """Float32 input (bit_depth 32) at its configured size, the size the
+    benchmark times: all 200 sub-integrations (204 800 samples per beam and
+    channel) of the block as (x - 128) / 20, 63.75 GB on the device, through
+    mraid_run on the tensor cores; sampled cells against the oracle's FP64
+    covariance path, and the masking properties."""
     import torch
     m = lib()
     cfg, h = fast_block
-    N, C, S, K = cfg.n_beam, cfg.n_chan, cfg.n_samp_sub, 20
+    N, C, S, K = cfg.n_beam, cfg.n_chan, cfg.n_samp_sub, cfg.n_sub
     d = h.to("cuda", non_blocking=False)
     x = d.view(N, cfg.n_time, C)[:, :K * S, :].float().sub_(128.0).div_(20.0).contiguous()
     del d
@@ -261,7 +262,7 @@ def test_fast_block_float32_twenty_sub_integrations(fast_block):
     flags = out["flags"].cpu().numpy().astype(bool)
     check_mask(stat, flags, out["info"])
     rng = np.random.default_rng(2514)
-    idx = np.unique(rng.integers(0, K * C, size=96))
+    idx = np.unique(rng.integers(0, K * C, size=128))
     ev_o = np.zeros((idx.size, N))
     for j, i in enumerate(idx):
         k, c = int(i // C), int(i % C)
