@@ -41,7 +41,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["mraid", "reference"], default="mraid")
     ap.add_argument("--workload", choices=["fast_block", "small", "paf13", "fast19", "paf36", "paf72"],
                     default="fast_block")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -914,9 +914,12 @@ def run_mraid(args):
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
+        steps_ms = []
         for _ in range(args.e2e_steps):
+            ts = time.perf_counter()
             m.mraid_run_host(plan.handle, h, h_stat, h_flags, hinfo)
             m.mraid_sync(plan.handle)
+            steps_ms.append((time.perf_counter() - ts) * 1000.0)
         te = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dist, "cuda")
         # the box's plain host-to-device copy of the same pinned block, for
         # the copy/compute overlap of the host path
@@ -934,6 +937,7 @@ def run_mraid(args):
                "h2d_gbs_achieved": cfg.nbytes / te / 1e9,
                "copy_only_ms": tcopy * 1000.0, "copy_only_gbs": cfg.nbytes / tcopy / 1e9,
                "compute_hidden_frac": max(0.0, min(1.0, (tcopy * 1000.0 + ms - te * 1000.0) / ms)),
+               "steps_ms": steps_ms,
                "api": "mraid_run_host (pinned host input, stat + flags copied back)",
                "note": "bound by the host-to-device copy; its rate differs between boxes"}
 
