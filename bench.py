@@ -860,6 +860,11 @@ def run_mraid(args):
     # (cached per shape; tuning runs before and outside the timed region)
     tune_cache = os.path.join(ROOT, "paper_2512_16278_gb300", "_build", "tune.json")
     variants = m.tune(plan.handle, d, N, cfg.n_chan, cfg.n_samp_sub, tune_cache)
+    try:  # the tuner's per-variant times for this shape, as recorded in its cache
+        with open(tune_cache) as f:
+            tune_ms = json.load(f)[m.tune_key(N, cfg.n_chan, cfg.n_samp_sub)].get("ms")
+    except (OSError, KeyError, ValueError):
+        tune_ms = None
 
     def step():
         m.mraid_run(plan.handle, d, evals, q1, stat, flags, info)
@@ -1009,7 +1014,7 @@ def run_mraid(args):
                      "threshold": info.thresh, "n_near": info.n_near},
             "q1_fp64_cells": info.q1_refined,
             "variants": {"gram": variants[0], "eig": variants[1],
-                         "eig_name": EIG_NAMES.get(variants[1], "?")},
+                         "eig_name": EIG_NAMES.get(variants[1], "?"), "tune_ms": tune_ms},
             "eig_iterations": {"per_cell": info.jacobi_sweeps / cells,
                                "per_warp": info.jacobi_warp_sweeps / max(1, (cells + 31) // 32),
                                "unit": "QR steps" if variants[1] >= 2 else "Jacobi sweeps"},

@@ -284,19 +284,21 @@ mraid_status mraid_run_bandpass(mraid_plan_t plan, const void* d_data,
 
 /* Autotuner (the paper has no counterpart; it picks among this library's
  * kernel variants). Times, `reps` runs each on d_data, every Gram variant
- * that fits the plan's shape (eight tensor-core variants over samples per
- * stage, f16 stages and converter unrolling, and the CUDA-core Gram) and the register
+ * that fits the plan's shape (ten tensor-core variants: samples per stage,
+ * f16 stages and converter unrolling with both operands in shared memory;
+ * 64 or 32 samples per stage with A in tensor memory, up to 19 beams; and the
+ * CUDA-core Gram) and the register
  * eigensolvers (Jacobi rounds in a loop; the Jacobi sweep unrolled;
  * Householder tridiagonalisation + implicit QR in two code layouts), and
  * keeps the fastest of each for this plan. *gram_choice: -1 = CUDA-core,
- * 0..7 tensor-core variants; *eig_choice: 0..3. report (may be NULL) receives "g<id>:ms;e<id>:ms;...".
+ * 0..9 tensor-core variants; *eig_choice: 0..4. report (may be NULL) receives "g<id>:ms;e<id>:ms;...".
  * Synchronous. */
 mraid_status mraid_autotune(mraid_plan_t plan, const void* d_data, int32_t reps,
                             int32_t* gram_choice, int32_t* eig_choice, char* report,
                             int32_t report_len);
 
 /* Select variants by id (e.g. from a tuning cache). Gram: -1 = CUDA-core,
- * 0..7 tensor-core variants (ignored where the shape does not fit).
+ * 0..9 tensor-core variants (ignored where the shape does not fit).
  * Eigensolver (beam counts with a one-thread-per-matrix kernel: 2, 3, 4, 13,
  * 19; other counts always use the warp-per-matrix Jacobi): 0 = Jacobi,
  * looped rounds; 1 = Jacobi, unrolled sweep; 2 = Householder reduction to

@@ -718,6 +718,553 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
 }
 
 // ---------------------------------------------------------------------------
+// The same Gram with the A operand in tensor memory (variants 8 and 9; one
+// polarisation, N + 1 <= 20 slots). In the kernel above the tensor core
+// reads A (16 beam slots x 8 channels) and B from shared memory: about 96 B
+// of operand reads per channel-sample, which with the TMA writes and the
+// converter's traffic keeps the SM's shared-memory path ~80 % busy at half
+// of HBM. Here the converter writes A straight into TMEM. ldmatrix .trans
+// .b8 turns a 16-sample x 16-channel byte tile of one beam into 4
+// consecutive samples of channel p and of channel p + 8 per lane (p = lane
+// / 4, samples 4 (lane % 4) ..); two beams' registers (slots s, s + 1) fill
+// one tcgen05.st 16x256b store, i.e. 16 TMEM lanes (8 channels x 2 slots,
+// lane = 8 slot + channel) by 16 K values, which is the K-major A layout of
+// kind::f16. The same registers give B in the K-major canonical layout
+// (8-byte stores, a warp's 256 contiguous bytes). Only B is read from
+// shared memory by the MMA, half the operand bytes. Operands go through
+// sub-stages of 16 samples (one K step each): B in shared memory, A in TMEM
+// columns after the accumulators (D1 of group 0 at column 0, of group 1 at
+// 8 rb, D2 at 16 rb; 24 columns per sub-stage for A of group 0, group 1 and
+// D2), as many sub-stages as the 512 columns leave (5 for 19 beams).
+constexpr int kMaxNA = 8;  // A/B sub-stages bound
+constexpr int kASub = 16;  // samples per A/B sub-stage (one K step)
+
+__host__ __device__ constexpr int tca_g1_col(int rb) { return 8 * rb; }
+__host__ __device__ constexpr int tca_d2_col(int rb) { return 16 * rb; }
+__host__ __device__ constexpr int tca_a_col(int rb, int R2) { return 16 * rb + 16 * R2; }
+__host__ __device__ constexpr int tca_sub_stages(int rb, int R2) {
+  return ((int)kTmemCols - tca_a_col(rb, R2)) / 24 < kMaxNA
+             ? ((int)kTmemCols - tca_a_col(rb, R2)) / 24
+             : kMaxNA;
+}
+// bytes of one B sub-stage: every slot of both groups, 16 samples x 8 channels x f16
+__host__ __device__ constexpr int tca_sub_bytes(int n_beam) { return stage_slots(n_beam) * 256; }
+
+struct SmemA {
+  uint64_t u8_full[kMaxNU], u8_empty[kMaxNU];
+  uint64_t f16_full[kMaxNA], f16_empty[kMaxNA];
+  uint64_t acc_full, acc_empty, drain;
+  int epi_go;  // the epilogue leader's wait outcome
+  uint32_t tmem_base;
+  int32_t s_sum[2][8][kGroupSlots];
+  float s_inv[2][8][kGroupSlots];
+};
+template <int T_>
+__host__ __device__ constexpr int tca_u8_depth(int n_beam, int na) {
+  return (int)((kSmemBudget - 1024 - (size_t)na * tca_sub_bytes(n_beam) - sizeof(SmemA)) /
+               ((size_t)n_beam * T_ * kBoxCh)) < kMaxNU
+             ? (int)((kSmemBudget - 1024 - (size_t)na * tca_sub_bytes(n_beam) - sizeof(SmemA)) /
+                     ((size_t)n_beam * T_ * kBoxCh))
+             : kMaxNU;
+}
+template <int T_>
+__host__ __device__ constexpr size_t tca_smem_bytes(int n_beam, int na, int n_u8) {
+  return 1024 + (size_t)na * tca_sub_bytes(n_beam) + (size_t)n_u8 * n_beam * T_ * kBoxCh +
+         sizeof(SmemA);
+}
+__device__ __forceinline__ void mma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b,
+                                           uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
+}
+// kind::f16, f16 A and B, f32 D, A from TMEM (K-major), B K-major
+__host__ __device__ constexpr uint32_t idesc_f16_ta(int m, int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+__device__ __forceinline__ void ldm_trans_b8(uint32_t addr, uint32_t& r0, uint32_t& r1) {
+  asm volatile("ldmatrix.sync.aligned.m16n16.x1.trans.shared.b8 {%0, %1}, [%2];"
+               : "=r"(r0), "=r"(r1)
+               : "r"(addr));
+}
+__device__ __forceinline__ void tmem_st16x256(uint32_t taddr, uint32_t v0, uint32_t v1, uint32_t v2,
+                                              uint32_t v3) {
+  asm volatile("tcgen05.st.sync.aligned.16x256b.x1.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+               "r"(v0), "r"(v1), "r"(v2), "r"(v3)
+               : "memory");
+}
+// 4 bytes (4 samples) -> (x - 128) as two f16x2, exact
+__device__ __forceinline__ void u8x4_to_f16(uint32_t w, uint32_t& lo, uint32_t& hi) {
+  const uint32_t magic = 0x64646464u, bias = 0x64806480u;
+  asm("sub.f16x2 %0, %1, %2;" : "=r"(lo) : "r"(__byte_perm(w, magic, 0x4140)), "r"(bias));
+  asm("sub.f16x2 %0, %1, %2;" : "=r"(hi) : "r"(__byte_perm(w, magic, 0x4342)), "r"(bias));
+}
+
+template <int T_>
+__global__ void __launch_bounds__(kThreads, 1)
+gram_tc_a_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
+  constexpr int kT = T_, kPol = 1;
+  const int kNA = tca_sub_stages(g.rb, g.R2);
+  const int kSubBytes = tca_sub_bytes(g.n_beam);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int kNU = g.n_u8;
+  unsigned char* f16 = base;                                   // kNA B sub-stages
+  unsigned char* u8 = f16 + (size_t)kNA * kSubBytes;           // kNU stages
+  const int u8_stage_bytes = g.n_beam * kT * kBoxCh;
+  SmemA* s = reinterpret_cast<SmemA*>(u8 + (size_t)kNU * u8_stage_bytes);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int N = g.n_beam;
+  const int chunks = g.n_chan / kBoxCh;
+  const int64_t items = (int64_t)g.n_sub * chunks;
+  const int stages = g.n_samp_sub / kT;
+  const int g1c = tca_g1_col(g.rb), d2c = tca_d2_col(g.rb), ac = tca_a_col(g.rb, g.R2);
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kNU; ++i) {
+      mbar_init(&s->u8_full[i], 1);
+      mbar_init(&s->u8_empty[i], kConvThreads);
+    }
+    for (int i = 0; i < kNA; ++i) {
+      mbar_init(&s->f16_full[i], kConvThreads);
+      mbar_init(&s->f16_empty[i], 1);
+    }
+    mbar_init(&s->acc_full, 1);
+    mbar_init(&s->acc_empty, kEpiThreads);
+    mbar_init(&s->drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // B sub-stages: the rows of ones (slot N of each group) and zeros where
+  // the converter does not write (slots past N)
+  const uint32_t one2 = 0x3c003c00u;  // f16x2 (1.0, 1.0)
+  const int p_one0 = slot_pos(0, N, g.R, g.R2), p_one1 = slot_pos(1, N, g.R, g.R2);
+  for (int st = 0; st < kNA; ++st) {
+    uint32_t* w = reinterpret_cast<uint32_t*>(f16 + (size_t)st * kSubBytes);
+    for (int i = threadIdx.x; i < kSubBytes / 4; i += blockDim.x) {
+      const int pos = i / 64;  // 256 B per slot
+      w[i] = (pos == p_one0 || pos == p_one1) ? one2 : 0u;
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s->tmem_base)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = s->tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA
+    if (lane == 0) {
+      uint32_t cnt = 0;
+      long long withheld = -1;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        const int k = (int)(it / chunks), ch0 = (int)(it % chunks) * kBoxCh;
+        const int64_t t_item = (int64_t)(g.sub0 + k) * g.n_samp_sub;
+        for (int st = 0; st < stages && ok; ++st, ++cnt) {
+          const int slot = cnt % kNU;
+          ok = mbar_wait(&s->u8_empty[slot], ((cnt / kNU) & 1) ^ 1, g.error, g.wait_ns);
+          if (!ok) break;
+          if (blockIdx.x == 0 && (long long)cnt == g.withhold) {
+            // injected fault: this stage is never issued, so the converter's
+            // bounded wait for it expires (nothing is in flight for it)
+            withheld = cnt;
+            continue;
+          }
+          mbar_expect_tx(&s->u8_full[slot], (uint32_t)u8_stage_bytes);
+          tma_load_3d(u8 + (size_t)slot * u8_stage_bytes, &tmap, ch0, (int)(t_item + st * kT), 0,
+                      &s->u8_full[slot]);
+        }
+      }
+      // drain: every issued copy has landed before the CTA may exit
+      for (uint32_t d = cnt > kNU ? cnt - kNU : 0; d < cnt; ++d)
+        if ((long long)d != withheld)
+          mbar_drain(&s->u8_full[d % kNU], (d / kNU) & 1, g.error, g.wait_ns);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA
+    if (lane == 0) {
+      const uint32_t f16_base = smem_u32(f16);
+      const uint32_t id1 = idesc_f16_ta(128, 8 * g.rb);
+      const uint32_t id2 = idesc_f16_ta(128, g.R2 > 0 ? 16 * g.R2 : 16);
+      const uint32_t pb1 = (uint32_t)g.R * 256;  // group 1's B: positions R ..
+      const uint32_t pb2 = 16u * 256;            // D2's B: positions 16 ..
+      // K-major canonical layout, no swizzle: core matrices of 8 rows x 16 B,
+      // K-adjacent ones 128 B apart, the next 8 rows (slot) 256 B on
+      const uint32_t lbo = 128, sbo = 256;
+      const int subs = stages * (kT / kASub);
+      uint32_t fcnt = 0, pcnt = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        for (int st = 0; st < subs && ok; ++st, ++fcnt) {
+          const int fs = fcnt % kNA;
+          ok = mbar_wait(&s->f16_full[fs], (fcnt / kNA) & 1, g.error, g.wait_ns);
+          if (!ok) break;
+          if (st == 0 && pcnt > 0) {
+            ok = mbar_wait(&s->acc_empty, (pcnt - 1) & 1, g.error, g.wait_ns);
+            if (!ok) break;
+          }
+          fence_after();
+          const uint32_t b = f16_base + (uint32_t)(fs * kSubBytes);
+          const uint32_t a = tmem + (uint32_t)(ac + 24 * fs);
+          const uint32_t acc = st > 0 ? 1u : 0u;
+          mma_f16_ta(tmem, a, smem_desc(b, lbo, sbo), id1, acc);
+          mma_f16_ta(tmem + g1c, a + 8, smem_desc(b + pb1, lbo, sbo), id1, acc);
+          if (g.R2 > 0) mma_f16_ta(tmem + d2c, a + 16, smem_desc(b + pb2, lbo, sbo), id2, acc);
+          mma_commit(&s->f16_empty[fs]);  // sub-stage free once these MMAs finish
+          if (st == subs - 1) {
+            mma_commit(&s->acc_full);
+            ++pcnt;
+          }
+        }
+      }
+      mma_commit(&s->drain);  // every MMA issued has finished before TMEM is freed
+      mbar_drain(&s->drain, 0, g.error, g.wait_ns);
+    }
+  } else if (warp >= 4 && warp < 8) {
+    // ------------------------------------------------------------ convert
+    // Warp w4 = warp - 4 writes TMEM lanes 32 w4 .. 32 w4 + 31: the A rows of
+    // slots 4 w4 .. 4 w4 + 3 for both groups, and of D2 positions 4 w4 ..
+    // 4 w4 + 3; it writes the B rows of the beams it loads.
+    const int w4 = warp - 4;
+    const int p = lane / 4, q = lane % 4;
+    const uint32_t u8_base = smem_u32(u8);
+    const uint32_t f16_base_c = smem_u32(f16);
+    // this lane's 8 bytes in a slot's 16 samples: K block q / 2, row p
+    const uint32_t bq = (uint32_t)((q / 2) * 128 + p * 16 + (q % 2) * 8);
+    const int ksub = kT / kASub;
+    // The slots this warp converts, fixed for the launch: entries 0..3 are
+    // D1 slots 4 w4 + k (both groups), entries 4..7 D2 positions 2u + h for
+    // u = 2 w4 + j (j = 0, 1), of group grp. kind 0: a beam (loaded), 1: the
+    // row of ones, 2: zeros (or nothing to write). src: the ldmatrix row
+    // address of this lane in the slot's u8 tile; b0 / b1: this lane's B
+    // bytes in a sub-stage for group 0 / 1 (entries 4..7: of their group).
+    int kind[8], grp2[4];
+    uint32_t src[8], b0[8], b1[4];
+    bool d2_on[2];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      int slot, grp = 0;
+      bool on = true;
+      if (k < 4) {
+        slot = 4 * w4 + k;
+      } else {
+        const int j = (k - 4) / 2, h = (k - 4) % 2, u = 2 * w4 + j;
+        on = u < g.R2;
+        if (h == 0) d2_on[j] = on;
+        const int i = 2 * u + h;
+        grp = i < g.R2 ? 0 : 1;
+        slot = 16 + (grp ? i - g.R2 : i);
+        grp2[k - 4] = grp;
+      }
+      kind[k] = !on ? 2 : (slot < N ? 0 : (slot == N ? 1 : 2));
+      src[k] = (uint32_t)((slot < N ? slot : 0) * kT * kBoxCh + (lane & 15) * kBoxCh);
+      b0[k] = (uint32_t)slot_pos(grp, slot, g.R, g.R2) * 256 + bq;
+      if (k < 4) b1[k] = (uint32_t)slot_pos(1, slot, g.R, g.R2) * 256 + bq;
+    }
+    auto st_b = [&](uint32_t addr, uint32_t x, uint32_t y) {
+      asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(x), "r"(y) : "memory");
+    };
+    uint32_t cnt = 0, fcnt = 0;
+    bool ok = true;
+    for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
+      for (int st = 0; st < stages && ok; ++st, ++cnt) {
+        const int us = cnt % kNU;
+        ok = mbar_wait(&s->u8_full[us], (cnt / kNU) & 1, g.error, g.wait_ns);
+        if (!ok) break;
+        const uint32_t u8_stage = u8_base + (uint32_t)us * (uint32_t)u8_stage_bytes;
+        for (int ks = 0; ks < ksub && ok; ++ks, ++fcnt) {
+          const int fs = fcnt % kNA;
+          ok = mbar_wait(&s->f16_empty[fs], ((fcnt / kNA) & 1) ^ 1, g.error, g.wait_ns);
+          if (!ok) break;
+          fence_after();  // the MMAs that read this sub-stage's A columns have finished
+          const uint32_t bsub = f16_base_c + (uint32_t)(fs * kSubBytes);
+          const uint32_t acol = tmem + ((uint32_t)(32 * w4) << 16) + (uint32_t)(ac + 24 * fs);
+          const uint32_t rows = u8_stage + (uint32_t)(ks * kASub * kBoxCh);
+          // every load first (one latency for all), then the conversions,
+          // then the B and A stores. Thread (p, q) gets samples 4q..4q+3 of
+          // channels p and p + 8: f16x2 registers v[k][0..1] and v[k][2..3].
+          uint32_t raw[8][2], v[8][4];
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            if (kind[k] == 0) ldm_trans_b8(rows + src[k], raw[k][0], raw[k][1]);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            if (kind[k] == 0) {
+              u8x4_to_f16(raw[k][0], v[k][0], v[k][1]);
+              u8x4_to_f16(raw[k][1], v[k][2], v[k][3]);
+            } else {
+              const uint32_t c1 = kind[k] == 1 ? one2 : 0u;
+              v[k][0] = v[k][1] = v[k][2] = v[k][3] = c1;
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (kind[k] == 0) {
+              st_b(bsub + b0[k], v[k][0], v[k][1]);
+              st_b(bsub + b1[k], v[k][2], v[k][3]);
+            }
+#pragma unroll
+          for (int k = 4; k < 8; ++k)
+            if (kind[k] == 0) {
+              const bool g1 = grp2[k - 4] != 0;
+              st_b(bsub + b0[k], g1 ? v[k][2] : v[k][0], g1 ? v[k][3] : v[k][1]);
+            }
+          // D1 A: slots 4 w4 + 2j, + 1 -> lanes 32 w4 + 16 j ..; group 1 eight columns on
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const uint32_t lanes = (uint32_t)(16 * j) << 16;
+            const int k = 2 * j;
+            tmem_st16x256(acol + lanes, v[k][0], v[k][1], v[k + 1][0], v[k + 1][1]);
+            tmem_st16x256(acol + lanes + 8, v[k][2], v[k][3], v[k + 1][2], v[k + 1][3]);
+          }
+          // D2 A: positions 2u, 2u + 1 -> lanes 16 u .., sixteen columns on
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            if (!d2_on[j]) continue;
+            const int k = 4 + 2 * j;
+            const bool ga = grp2[2 * j] != 0, gb = grp2[2 * j + 1] != 0;
+            tmem_st16x256(acol + ((uint32_t)(16 * j) << 16) + 16, ga ? v[k][2] : v[k][0],
+                          ga ? v[k][3] : v[k][1], gb ? v[k + 1][2] : v[k + 1][0],
+                          gb ? v[k + 1][3] : v[k + 1][1]);
+          }
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          fence_before();
+          mbar_arrive(&s->f16_full[fs]);
+        }
+        if (!ok) break;
+        mbar_arrive(&s->u8_empty[us]);
+      }
+    }
+  } else if (warp >= 8) {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp - 8;              // TMEM lane quarter (warp % 4)
+    const int c = lane % 8;              // channel within the group
+    const int slot = 4 * q + lane / 8;   // D1 row slot (beam a, 0..15), both groups
+    // D2 row of this lane: stage position 16 + 4q + lane/8, which holds
+    // slot 16.. of group 0, then slot 16.. of group 1, then nothing useful
+    const int p2 = 4 * q + lane / 8;     // position - 16
+    const int g2 = p2 < g.R2 ? 0 : (p2 < 2 * g.R2 ? 1 : -1);
+    const int slot2 = 16 + (g2 == 1 ? p2 - g.R2 : p2);
+    const int64_t n = g.n_samp_sub;
+    const int R = g.R, R2 = g.R2;
+    uint32_t pcnt = 0;
+    bool ok = true;
+    for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
+      // the rest of the item from the rows D1 `slot` of each group and D2
+      // `slot2` (by column block): floats of exact integers (one
+      // polarisation) or int32 sums of the pieces (two)
+      auto finish = [&](auto& row, auto& row2) {
+        // G[a][N] (row sum) and G[a][a] from each row, picked with
+        // compile-time register indices and runtime block -> slot maps
+        using V = std::remove_reference_t<decltype(row[0][0])>;
+        V sumN[2], diag[2], sumN2 = 0, diag2 = 0;
+  #pragma unroll
+        for (int grp = 0; grp < 2; ++grp) {
+          sumN[grp] = diag[grp] = 0;
+  #pragma unroll
+          for (int jb = 0; jb < kGroupSlots; ++jb) {
+            const int b = d1_slot(grp, jb, R2);
+            if (jb < R && b == N) sumN[grp] = row[grp][jb];
+            if (jb < R && b == slot) diag[grp] = row[grp][jb];
+          }
+        }
+        // D2 columns: blocks 0..R2-1 are group 0 slots 16.., then group 1's
+        const int jb2 = g2 == 1 ? R2 : 0;
+  #pragma unroll
+        for (int jb = 0; jb < 16; ++jb) {
+          if (jb - jb2 == N - 16) sumN2 = row2[jb];
+          if (jb - jb2 == slot2 - 16) diag2 = row2[jb];
+        }
+
+        const int k = (int)(it / chunks), ch0 = (int)(it % chunks) * kBoxCh;
+        // row sums and inverse standard deviations, shared through smem
+        auto table = [&](int grp, int a, V sum_a, V diag_a) {
+          const int64_t sa = (int64_t)sum_a;
+          const int64_t var = n * (int64_t)diag_a - sa * sa;
+          s->s_sum[grp][c][a] = (int32_t)sa;
+          float inv = 0.f;
+          if (a < N) {
+            if (var > 0) {
+              const float vf = (float)var;
+              inv = rsqrtf(vf);
+              inv = inv * (1.5f - 0.5f * vf * inv * inv);
+            } else {
+              atomicAdd(g.degenerate, 1ull);
+            }
+          }
+          s->s_inv[grp][c][a] = inv;
+        };
+  #pragma unroll
+        for (int grp = 0; grp < 2; ++grp)
+          if (slot < N + 1) table(grp, slot, sumN[grp], diag[grp]);
+        if (g2 >= 0 && slot2 < N + 1) table(g2, slot2, sumN2, diag2);
+        named_sync(1, kEpiThreads);
+        // one packed output row: a, its group, its values by column block and
+        // the slot of each block (b < 0: not this group's)
+        auto emit = [&](int grp, int a, const V* rv, auto nb_c, auto slot_of) {
+          constexpr int NB = decltype(nb_c)::value;
+          const int64_t cell = (int64_t)k * g.n_chan + ch0 + grp * 8 + c;
+          const int64_t sa = s->s_sum[grp][c][a];
+          const float inva = s->s_inv[grp][c][a];
+          if (g.corr && a < N) {
+            float* dst = g.corr + cell * (int64_t)(N * (N + 1) / 2) + (a * N - a * (a - 1) / 2);
+  #pragma unroll
+            for (int jb = 0; jb < NB; ++jb) {
+              const int b = slot_of(jb);
+              if (b < a || b >= N) continue;
+              float r;
+              if (b == a) {
+                r = 1.f;
+              } else {
+                const int64_t cov = n * (int64_t)rv[jb] - sa * (int64_t)s->s_sum[grp][c][b];
+                r = (float)cov * inva * s->s_inv[grp][c][b];
+              }
+              dst[b - a] = r;
+            }
+          }
+          if (g.sums || g.sums8) {
+            const int N1 = N + 1;
+            const int64_t P = N1 * (N1 + 1) / 2;
+            const int row = a * N1 - a * (a - 1) / 2;
+            // public layout: one cell's entries contiguous; interleaved: the
+            // 8 channels of a group side by side, so a warp's 8-byte stores
+            // fill 64-byte runs
+            int64_t* dst = g.sums8 ? g.sums8 + ((cell >> 3) * P + row) * 8 + (cell & 7)
+                                   : g.sums + cell * P + row;
+            const int step = g.sums8 ? 8 : 1;
+  #pragma unroll
+            for (int jb = 0; jb < NB; ++jb) {
+              const int b = slot_of(jb);
+              if (b < a || b > N) continue;
+              const int64_t gab = (int64_t)rv[jb];
+              int64_t v;
+              const int64_t cc = g.center;
+              if (a == N) v = n;                                  // (N, N): sample count
+              else if (b == N) v = gab + cc * n;                  // S_a
+              else v = gab + cc * (sa + (int64_t)s->s_sum[grp][c][b]) + cc * cc * n;
+              dst[(b - a) * step] = v;
+            }
+          }
+        };
+  #pragma unroll
+        for (int grp = 0; grp < 2; ++grp)
+          if (slot <= N)
+            emit(grp, slot, row[grp], std::integral_constant<int, kGroupSlots>{},
+                 [&](int jb) { return jb < R ? d1_slot(grp, jb, R2) : -1; });
+        if (g2 >= 0 && slot2 <= N)
+          emit(g2, slot2, row2, std::integral_constant<int, 16>{},
+               [&](int jb) { return (jb >= jb2 && jb < jb2 + R2) ? 16 + jb - jb2 : -1; });
+        named_sync(1, kEpiThreads);  // smem tables reused by the next item
+      };
+      if constexpr (kPol == 1) {
+        ok = epi_wait(&s->acc_full, pcnt & 1, g.error, g.wait_ns, &s->epi_go,
+                      threadIdx.x == 256);
+        if (!ok) break;
+        ++pcnt;
+        fence_after();
+        float row[2][kGroupSlots];   // D1 row `slot` of each group, by column block
+        float row2[16];              // D2 row `slot2`, by column block
+#pragma unroll
+        for (int grp = 0; grp < 2; ++grp) {
+          // chunks of 32 columns (4 blocks x 8 channels), one load in flight
+#pragma unroll
+          for (int ch = 0; ch < kGroupSlots / 4; ++ch) {
+            if (ch * 4 < g.rb) {
+              uint32_t v[32];
+              tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + grp * g1c + ch * 32, v);
+              tmem_wait_ld();
+              pick4(v, c, &row[grp][4 * ch]);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) row[grp][4 * ch + u] = 0.f;
+            }
+          }
+        }
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+          if (2 * R2 > 4 * ch) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + d2c + ch * 32, v);
+            tmem_wait_ld();
+            pick4(v, c, &row2[4 * ch]);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) row2[4 * ch + u] = 0.f;
+          }
+        }
+        fence_before();
+        mbar_arrive(&s->acc_empty);  // accumulators may be overwritten now
+        finish(row, row2);
+      } else {
+        // exact integer sums over the accumulation pieces (each piece's
+        // sums are integers below 2^24, so exact in FP32; the total fits int32)
+        const int pieces = stages / g.piece_stages;
+        int32_t row[2][kGroupSlots];
+        int32_t row2[16];
+#pragma unroll
+        for (int grp = 0; grp < 2; ++grp)
+#pragma unroll
+          for (int jb = 0; jb < kGroupSlots; ++jb) row[grp][jb] = 0;
+#pragma unroll
+        for (int jb = 0; jb < 16; ++jb) row2[jb] = 0;
+        for (int pc = 0; pc < pieces && ok; ++pc, ++pcnt) {
+          ok = epi_wait(&s->acc_full, pcnt & 1, g.error, g.wait_ns, &s->epi_go,
+                        threadIdx.x == 256);
+          if (!ok) break;
+          fence_after();
+#pragma unroll
+          for (int grp = 0; grp < 2; ++grp) {
+#pragma unroll
+            for (int ch = 0; ch < kGroupSlots / 4; ++ch) {
+              if (ch * 4 < g.rb) {
+                uint32_t v[32];
+                float f4[4];
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + grp * g1c + ch * 32, v);
+                tmem_wait_ld();
+                pick4(v, c, f4);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) row[grp][4 * ch + u] += __float2int_rn(f4[u]);
+              }
+            }
+          }
+#pragma unroll
+          for (int ch = 0; ch < 4; ++ch) {
+            if (2 * R2 > 4 * ch) {
+              uint32_t v[32];
+              float f4[4];
+              tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + d2c + ch * 32, v);
+              tmem_wait_ld();
+              pick4(v, c, f4);
+#pragma unroll
+              for (int u = 0; u < 4; ++u) row2[4 * ch + u] += __float2int_rn(f4[u]);
+            }
+          }
+          fence_before();
+          mbar_arrive(&s->acc_empty);
+        }
+        if (!ok) break;
+        finish(row, row2);
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 2) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols));
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Float32 samples (beamformer output) on the same tensor cores. Each sample,
 // shifted by its cell's first sample of the same beam and channel (the
 // covariance does not depend on a per-beam shift, and the shift keeps the
@@ -1108,8 +1655,9 @@ EncodeTiledFn encode_fn() {
 
 // Tensor-core Gram variants {samples per stage, f16 stages, converter
 // unrolling}: 0 = {64, 2, 1}, 1 = {32, 4, 1}, 2 = {32, 2, 1}, 3 = {64, 3, 1},
-// 4 = {64, 2, 2}, 5 = {64, 3, 2}, 6 = {64, 4, 1}, 7 = {64, 4, 2}.
-int tc_variant_samples(int v) { return (v == 1 || v == 2) ? 32 : 64; }
+// 4 = {64, 2, 2}, 5 = {64, 3, 2}, 6 = {64, 4, 1}, 7 = {64, 4, 2}; with A in
+// TMEM (gram_tc_a_kernel, up to 19 beams): 8 = 64-sample TMA stages, 9 = 32.
+int tc_variant_samples(int v) { return (v == 1 || v == 2 || v == 9) ? 32 : 64; }
 
 // Untuned default: four f16 stages of 64 samples where that still leaves
 // an u8 ring of at least three stages (measured fastest for 19 beams),
@@ -1134,11 +1682,26 @@ static int tc_u8_depth(int v, int n_beam, int n_pol) {
   }
 }
 
-// Two polarisations double the u8 stage: they run variant 0 (two f16
-// stages), which leaves the u8 ring at least two stages deep.
-static int tc_variant_for(const mraid_plan_s* pl, int n_pol) {
-  return n_pol == 2 ? 0 : pl->tc_variant;
+// The A-in-TMEM kernel fits where the accumulators leave TMEM room for at
+// least two operand sub-stages and shared memory an u8 ring of two stages.
+static bool tca_fits(int v, int n_beam) {
+  const int R = n_beam + 1, rb = (R + 1) / 2 * 2, R2 = R > 16 ? R - 16 : 0;
+  if (n_beam < 2 || R > 20 || tca_sub_stages(rb, R2) < 2) return false;
+  const int na = tca_sub_stages(rb, R2);
+  return (v == 9 ? tca_u8_depth<32>(n_beam, na) : tca_u8_depth<64>(n_beam, na)) >= 2;
 }
+
+// Two polarisations double the u8 stage: they run variant 0 (two f16
+// stages), which leaves the u8 ring at least two stages deep. Variants 8
+// and 9 where they do not fit the shape run the untuned default.
+static int tc_variant_for(const mraid_plan_s* pl, int n_pol) {
+  if (n_pol == 2) return 0;
+  const int v = pl->tc_variant;
+  if (v >= 8 && !tca_fits(v, pl->p.n_beam)) return tc_default_variant(pl->p.n_beam);
+  return v;
+}
+
+int tc_variant_effective(const mraid_plan_s* pl) { return tc_variant_for(pl, 1); }
 
 bool gram_tc_supported(const mraid_plan_s* pl, const void* d_data, int n_pol) {
   const mraid_params& p = pl->p;
@@ -1215,9 +1778,22 @@ cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int su
       gram_tc_kernel<T, NF, U, P><<<grid, kThreads, smem, pl->stream>>>(map, a);                  \
   } while (0)
 #define MRAID_TC_LAUNCH(T, NF, U) MRAID_TC_LAUNCH_P(T, NF, U, 1)
+#define MRAID_TCA_LAUNCH(T)                                                                       \
+  do {                                                                                           \
+    const int na_ = tca_sub_stages(a.rb, a.R2);                                                  \
+    const int n_u8 = tca_u8_depth<T>(p.n_beam, na_);                                             \
+    a.n_u8 = n_u8;                                                                               \
+    const size_t smem = tca_smem_bytes<T>(p.n_beam, na_, n_u8);                                  \
+    e = cudaFuncSetAttribute(gram_tc_a_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                             (int)smem);                                                        \
+    if (e == cudaSuccess && grid > 0)                                                            \
+      gram_tc_a_kernel<T><<<grid, kThreads, smem, pl->stream>>>(map, a);                          \
+  } while (0)
   if (n_pol == 2) {
     MRAID_TC_LAUNCH_P(64, 2, 1, 2);  // variant 0: two f16 stages leave room for the doubled u8 ring
   } else switch (variant) {
+    case 8: MRAID_TCA_LAUNCH(64); break;
+    case 9: MRAID_TCA_LAUNCH(32); break;
     case 1: MRAID_TC_LAUNCH(32, 4, 1); break;
     case 2: MRAID_TC_LAUNCH(32, 2, 1); break;
     case 3: MRAID_TC_LAUNCH(64, 3, 1); break;
@@ -1229,6 +1805,7 @@ cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int su
   }
 #undef MRAID_TC_LAUNCH
 #undef MRAID_TC_LAUNCH_P
+#undef MRAID_TCA_LAUNCH
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

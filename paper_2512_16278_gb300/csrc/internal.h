@@ -184,7 +184,10 @@ cudaError_t launch_gram_f32(const mraid_plan_s* pl, const float* d_data, int sub
 bool gram_tc_supported(const mraid_plan_s* pl, const void* d_data, int n_pol = 1);
 int tc_variant_samples(int v);
 int tc_default_variant(int n_beam);
-constexpr int kTcVariants = 8;
+constexpr int kTcVariants = 10;
+// the tensor-core variant a plan's launch runs (variants 8 and 9 fall back
+// to the default where their A-in-TMEM kernel does not fit the shape)
+int tc_variant_effective(const mraid_plan_s* pl);
 constexpr int kEigVariants = 5;  // register eigensolvers (see eig_variant)
 // d_sums8 (instead of d_sums): the sums in the interleaved layout
 // [cell / 8][P][cell % 8], which the kernel writes in 64-byte runs

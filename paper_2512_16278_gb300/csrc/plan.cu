@@ -787,7 +787,8 @@ mraid_status mraid_autotune(mraid_plan_t pl, const void* d_data, int32_t reps, i
     pl->tc_variant = v < 0 ? 0 : v;
     // float32 samples have one tensor-core kernel, timed as variant 0
     if (v >= 0 && (pl->p.bit_depth == 32 ? (v > 0 || !gram_tc_f32_supported(pl, d_data))
-                                         : !gram_tc_supported(pl, d_data)))
+                                         : (!gram_tc_supported(pl, d_data) ||
+                                            tc_variant_effective(pl) != v)))
       continue;
     float ms = 0.f;
     st = time_runs(pl, reps, e0, e1,

@@ -76,7 +76,7 @@ def test_tc_gram_exact_at_the_edge_every_variant(n_beam, n_chan):
     r_o = np.stack([oracle.corr_from_gram(G[i])[0] for i in range(G.shape[0])])
     d = torch.from_numpy(data).cuda()
     with m.Plan(n_beam, n_chan, N_S, n_sub) as plan:
-        for v in range(8):
+        for v in range(10):
             m.mraid_set_variant(plan.handle, v)
             m.mraid_profile_enable(plan.handle)
             sums, corr = plan.ccm(d)
