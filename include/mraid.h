@@ -298,7 +298,9 @@ mraid_status mraid_autotune(mraid_plan_t plan, const void* d_data, int32_t reps,
                             int32_t report_len);
 
 /* Select variants by id (e.g. from a tuning cache). Gram: -1 = CUDA-core,
- * 0..9 tensor-core variants (ignored where the shape does not fit).
+ * 0..9 tensor-core variants for up to 23 beams (ignored where the shape does
+ * not fit); for 24..127 beams any id >= 0 selects the one-channel-per-MMA
+ * tensor-core Gram (exact in pieces of <= 1024 samples).
  * Eigensolver (beam counts with a one-thread-per-matrix kernel: 2, 3, 4, 13,
  * 19; other counts always use the warp-per-matrix Jacobi): 0 = Jacobi,
  * looped rounds; 1 = Jacobi, unrolled sweep; 2 = Householder reduction to

@@ -42,6 +42,7 @@
 #include <type_traits>
 
 #include "internal.h"
+#include "tc_ptx.h"
 
 namespace mraid {
 namespace {
@@ -83,154 +84,6 @@ struct TcArgs {
   unsigned long long wait_ns;  // bound of every wait (the plan's wait limit)
   long long withhold;  // fault injection: CTA 0's TMA producer never issues this stage (-1: none)
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// The same with a suspend-time hint: a thread whose phase has not completed
-// sleeps in hardware (woken when it completes, or after about 2 us), so
-// waiting warps do not take issue slots from the working ones.
-__device__ __forceinline__ bool mbar_try_suspend(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(2000u)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait for the phase of `parity` to complete; false on timeout
-// (after wait_ns, recorded in the error word) or when another role already
-// reported an error.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* error,
-                                          unsigned long long wait_ns) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = gtimer();
-  for (uint32_t i = 0;; ++i) {
-    if (mbar_try_suspend(bar, parity)) return true;
-    if ((i & 15) == 15) {
-      if (*(volatile unsigned*)error) return false;
-      if (gtimer() - t0 > wait_ns) {
-        atomicOr(error, 1u);
-        return false;
-      }
-    }
-  }
-}
-// Wait for this CTA's own asynchronous work (bulk copies, MMAs) to land
-// before it exits or frees TMEM: the error word does not cut it short,
-// only the time limit does (and that is recorded).
-__device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity, unsigned* error,
-                                           unsigned long long wait_ns) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = gtimer();
-  for (uint32_t i = 0;; ++i) {
-    if (mbar_try_suspend(bar, parity)) return true;
-    if ((i & 15) == 15 && gtimer() - t0 > wait_ns) {
-      atomicOr(error, 1u);
-      return false;
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// tcgen05 shared-memory descriptor, no swizzle: start address, leading and
-// stride byte offsets (>> 4), descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3fff) | ((uint64_t)((lbo >> 4) & 0x3fff) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3fff) << 32) | (1ull << 46);
-}
-// Instruction descriptor, kind::f16: f16 A/B, f32 D, both operands MN-major.
-__host__ __device__ constexpr uint32_t idesc_f16(int m, int n) {
-  return (1u << 4) | (0u << 7) | (0u << 10) | (1u << 15) | (1u << 16) |
-         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                        uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-// 32 consecutive TMEM columns of this warp's 32 lanes.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void named_sync(int id, int threads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
-}
-// The epilogue warps' wait for the accumulators, decided once for all of
-// them: one thread waits (bounded), the others learn the outcome at a named
-// barrier, so either every epilogue warp goes on to the item or none does.
-// (A warp that gave up alone would leave the others at their next named
-// barrier, which has no time limit.)
-__device__ __forceinline__ bool epi_wait(uint64_t* bar, uint32_t parity, unsigned* error,
-                                         unsigned long long wait_ns, volatile int* go,
-                                         bool leader) {
-  if (leader) *go = mbar_wait(bar, parity, error, wait_ns) ? 1 : 0;
-  named_sync(1, 128);
-  const bool ok = *go != 0;
-  named_sync(1, 128);  // read by all before the leader writes it again
-  return ok;
-}
 
 // Keep the 4 entries of a 32-column chunk whose channel equals c (columns
 // 8u + c, u = 0..3) with compile-time register indices.
@@ -779,28 +632,12 @@ __device__ __forceinline__ void mma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uin
       " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
       "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
 }
-// kind::f16, f16 A and B, f32 D, A from TMEM (K-major), B K-major
-__host__ __device__ constexpr uint32_t idesc_f16_ta(int m, int n) {
-  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-__device__ __forceinline__ void ldm_trans_b8(uint32_t addr, uint32_t& r0, uint32_t& r1) {
-  asm volatile("ldmatrix.sync.aligned.m16n16.x1.trans.shared.b8 {%0, %1}, [%2];"
-               : "=r"(r0), "=r"(r1)
-               : "r"(addr));
-}
 __device__ __forceinline__ void tmem_st16x256(uint32_t taddr, uint32_t v0, uint32_t v1, uint32_t v2,
                                               uint32_t v3) {
   asm volatile("tcgen05.st.sync.aligned.16x256b.x1.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
                "r"(v0), "r"(v1), "r"(v2), "r"(v3)
                : "memory");
 }
-// 4 bytes (4 samples) -> (x - 128) as two f16x2, exact
-__device__ __forceinline__ void u8x4_to_f16(uint32_t w, uint32_t& lo, uint32_t& hi) {
-  const uint32_t magic = 0x64646464u, bias = 0x64806480u;
-  asm("sub.f16x2 %0, %1, %2;" : "=r"(lo) : "r"(__byte_perm(w, magic, 0x4140)), "r"(bias));
-  asm("sub.f16x2 %0, %1, %2;" : "=r"(hi) : "r"(__byte_perm(w, magic, 0x4342)), "r"(bias));
-}
-
 template <int T_>
 __global__ void __launch_bounds__(kThreads, 1)
 gram_tc_a_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
@@ -892,8 +729,8 @@ gram_tc_a_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
     // ------------------------------------------------------------ MMA
     if (lane == 0) {
       const uint32_t f16_base = smem_u32(f16);
-      const uint32_t id1 = idesc_f16_ta(128, 8 * g.rb);
-      const uint32_t id2 = idesc_f16_ta(128, g.R2 > 0 ? 16 * g.R2 : 16);
+      const uint32_t id1 = idesc_f16_k(128, 8 * g.rb);
+      const uint32_t id2 = idesc_f16_k(128, g.R2 > 0 ? 16 * g.R2 : 16);
       const uint32_t pb1 = (uint32_t)g.R * 256;  // group 1's B: positions R ..
       const uint32_t pb2 = 16u * 256;            // D2's B: positions 16 ..
       // K-major canonical layout, no swizzle: core matrices of 8 rows x 16 B,
@@ -1632,24 +1469,6 @@ gram_tc_f32_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
   }
 }
 
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
-}
 
 }  // namespace
 

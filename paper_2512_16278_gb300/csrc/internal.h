@@ -25,7 +25,7 @@ struct FlagDev {  // device image of mraid_flag_info
 
 enum KernelId {
   K_GRAM = 0, K_CORR, K_EIG, K_FLAG, K_GRAM_TC, K_GRAM_F32, K_GRAM_TC_F32, K_AGG,
-  K_BP_INPUT, K_ARPLS, K_CCM_BP, K_POL2_FOLD, K_COUNT
+  K_BP_INPUT, K_ARPLS, K_CCM_BP, K_POL2_FOLD, K_GRAM_TCL, K_COUNT
 };
 const char* kernel_name(int id);
 
@@ -196,6 +196,12 @@ cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int su
                            int n_pol = 1);
 // float32 samples on the tensor cores (split-bf16 products, gram_tc.cu):
 // correlation only, d_corr relative to sub0
+// Tensor-core Gram for 24..127 beams, one channel per MMA (gram_tcl.cu):
+// int64 sums [cell][P] of sub-integrations [sub0, sub0 + n_sub), cells
+// relative to sub0.
+bool gram_tcl_supported(const mraid_plan_s* pl, const void* d_data);
+cudaError_t launch_gram_tcl(const mraid_plan_s* pl, const uint8_t* d_data, int sub0, int n_sub,
+                            int64_t* d_sums);
 bool gram_tc_f32_supported(const mraid_plan_s* pl, const void* d_data);
 cudaError_t launch_gram_tc_f32(const mraid_plan_s* pl, const float* d_data, int sub0, int n_sub,
                                float* d_corr);

@@ -41,6 +41,7 @@ const char* kernel_name(int id) {
     case K_ARPLS: return "arpls";
     case K_CCM_BP: return "ccm_bandpass";
     case K_POL2_FOLD: return "pol2_fold";
+    case K_GRAM_TCL: return "gram_tcl";
   }
   return "unknown";
 }
@@ -235,12 +236,19 @@ mraid_status ccm_range(mraid_plan_s* pl, const void* d_data, int sub0, int n_sub
     if (st != MRAID_OK) return st;
     sums = pl->ws.sums;
   }
-  for (int s = 0; s < n_sub; s += kMaxSubPerLaunch) {
-    const int ns = (n_sub - s) < kMaxSubPerLaunch ? (n_sub - s) : kMaxSubPerLaunch;
-    cudaError_t e = MRAID_PROF(pl, K_GRAM,
-                               launch_gram_u8(pl, static_cast<const uint8_t*>(d_data), sub0 + s, ns,
-                                              sums + (int64_t)s * pl->p.n_chan * pl->psum));
-    if (e != cudaSuccess) return cuda_fail(e, "gram launch");
+  if (!pl->force_dp4a && gram_tcl_supported(pl, d_data)) {
+    cudaError_t e = MRAID_PROF(pl, K_GRAM_TCL,
+                               launch_gram_tcl(pl, static_cast<const uint8_t*>(d_data), sub0, n_sub,
+                                               sums));
+    if (e != cudaSuccess) return cuda_fail(e, "gram_tcl launch");
+  } else {
+    for (int s = 0; s < n_sub; s += kMaxSubPerLaunch) {
+      const int ns = (n_sub - s) < kMaxSubPerLaunch ? (n_sub - s) : kMaxSubPerLaunch;
+      cudaError_t e = MRAID_PROF(pl, K_GRAM,
+                                 launch_gram_u8(pl, static_cast<const uint8_t*>(d_data), sub0 + s,
+                                                ns, sums + (int64_t)s * pl->p.n_chan * pl->psum));
+      if (e != cudaSuccess) return cuda_fail(e, "gram launch");
+    }
   }
   if (d_corr) {
     cudaError_t e = MRAID_PROF(pl, K_CORR, launch_corr_from_sums(pl, sums, cells, d_corr));
@@ -785,10 +793,12 @@ mraid_status mraid_autotune(mraid_plan_t pl, const void* d_data, int32_t reps, i
   for (int v = -1; v < kTcVariants && st == MRAID_OK; ++v) {
     pl->force_dp4a = v < 0;
     pl->tc_variant = v < 0 ? 0 : v;
-    // float32 samples have one tensor-core kernel, timed as variant 0
+    // float32 samples, and 24..127 beams, have one tensor-core kernel each,
+    // timed as variant 0
     if (v >= 0 && (pl->p.bit_depth == 32 ? (v > 0 || !gram_tc_f32_supported(pl, d_data))
-                                         : (!gram_tc_supported(pl, d_data) ||
-                                            tc_variant_effective(pl) != v)))
+                   : gram_tcl_supported(pl, d_data) ? v > 0
+                                                    : (!gram_tc_supported(pl, d_data) ||
+                                                       tc_variant_effective(pl) != v)))
       continue;
     float ms = 0.f;
     st = time_runs(pl, reps, e0, e1,

@@ -114,3 +114,39 @@ def compare_flags(flags_gpu, flags_orc, stat_orc, info_gpu, info_orc, keep=None,
         kc = np.tile(np.asarray(keep, bool), flags_gpu.shape[0] // n_chan)
         assert not np.any(flags_gpu.astype(bool) & kc)
     return int(near.sum()), int(diff.sum())
+
+
+def edge_block(n_beam, n_chan, n_sub, seed, n_s=1024):
+    """uint8 block [beam][n_sub * n_s][chan] with one of eight saturated or
+    extreme patterns per cell: every beam 0; every beam 255; 0/255
+    alternation in phase; half the beams in anti-phase; one all-0 beam
+    beside noise; 255 and 0 beams beside random 0/255; uniform bytes;
+    random 0/255."""
+    rng = np.random.default_rng(seed)
+    x = np.empty((n_beam, n_sub * n_s, n_chan), dtype=np.uint8)
+    alt = (np.arange(n_s) % 2).astype(np.uint8) * 255               # 0, 255, 0, ...
+    for k in range(n_sub):
+        for c in range(n_chan):
+            t = slice(k * n_s, (k + 1) * n_s)
+            kind = (k * n_chan + c) % 8
+            if kind == 0:                                          # every beam 0
+                x[:, t, c] = 0
+            elif kind == 1:                                        # every beam 255
+                x[:, t, c] = 255
+            elif kind == 2:                                        # in-phase alternation
+                x[:, t, c] = alt[None, :]
+            elif kind == 3:                                        # half the beams anti-phase
+                x[:, t, c] = alt[None, :]
+                x[::2, t, c] = 255 - alt[None, :]
+            elif kind == 4:                                        # one all-0 beam beside noise
+                x[:, t, c] = rng.integers(0, 256, size=(n_beam, n_s), dtype=np.uint8)
+                x[int(rng.integers(0, n_beam)), t, c] = 0
+            elif kind == 5:                                        # 255 and 0 beams, random 0/255
+                x[:, t, c] = rng.integers(0, 2, size=(n_beam, n_s), dtype=np.uint8) * 255
+                x[0, t, c] = 255
+                x[n_beam - 1, t, c] = 0
+            elif kind == 6:                                        # uniform bytes
+                x[:, t, c] = rng.integers(0, 256, size=(n_beam, n_s), dtype=np.uint8)
+            else:                                                  # random 0/255
+                x[:, t, c] = rng.integers(0, 2, size=(n_beam, n_s), dtype=np.uint8) * 255
+    return x

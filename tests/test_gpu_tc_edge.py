@@ -14,43 +14,11 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import CORR_TOL, lib, unpack_corr
+from gpu_util import CORR_TOL, edge_block, lib, unpack_corr
 
 pytestmark = pytest.mark.gpu
 
 N_S = 1024
-
-
-def edge_block(n_beam, n_chan, n_sub, seed):
-    """One of eight saturated or extreme patterns per cell."""
-    rng = np.random.default_rng(seed)
-    x = np.empty((n_beam, n_sub * N_S, n_chan), dtype=np.uint8)
-    alt = (np.arange(N_S) % 2).astype(np.uint8) * 255               # 0, 255, 0, ...
-    for k in range(n_sub):
-        for c in range(n_chan):
-            t = slice(k * N_S, (k + 1) * N_S)
-            kind = (k * n_chan + c) % 8
-            if kind == 0:                                          # every beam 0
-                x[:, t, c] = 0
-            elif kind == 1:                                        # every beam 255
-                x[:, t, c] = 255
-            elif kind == 2:                                        # in-phase alternation
-                x[:, t, c] = alt[None, :]
-            elif kind == 3:                                        # half the beams anti-phase
-                x[:, t, c] = alt[None, :]
-                x[::2, t, c] = 255 - alt[None, :]
-            elif kind == 4:                                        # one all-0 beam beside noise
-                x[:, t, c] = rng.integers(0, 256, size=(n_beam, N_S), dtype=np.uint8)
-                x[int(rng.integers(0, n_beam)), t, c] = 0
-            elif kind == 5:                                        # 255 and 0 beams, random 0/255
-                x[:, t, c] = rng.integers(0, 2, size=(n_beam, N_S), dtype=np.uint8) * 255
-                x[0, t, c] = 255
-                x[n_beam - 1, t, c] = 0
-            elif kind == 6:                                        # uniform bytes
-                x[:, t, c] = rng.integers(0, 256, size=(n_beam, N_S), dtype=np.uint8)
-            else:                                                  # random 0/255
-                x[:, t, c] = rng.integers(0, 2, size=(n_beam, N_S), dtype=np.uint8) * 255
-    return x
 
 
 def oracle_packed(data, n_sub, n_chan, pol2=False):
