@@ -601,16 +601,16 @@ def bench_batched(m, torch, stream, steps, peaks=None):
     torch.cuda.synchronize()
     ms_b = e0.elapsed_time(e1) / steps
     infos = [m.FlagInfo() for _ in plans]
-    o2 = [plan._empty(plan.n_cells, dtype=torch.float32) for plan in plans]
-    f2 = [plan._empty(plan.n_cells, dtype=torch.uint8) for plan in plans]
+    # the plain form writes the same outputs as the batch: evals, q1, stat, flags
+    po = [{k: torch.empty_like(o[k]) for k in ("evals", "q1", "stat", "flags")} for o in outs]
     for _ in range(2):
-        for plan, d, st, fl, inf in zip(plans, datas, o2, f2, infos):
-            m.mraid_run(plan.handle, d, None, None, st, fl, inf)
+        for plan, d, o, inf in zip(plans, datas, po, infos):
+            m.mraid_run(plan.handle, d, o["evals"], o["q1"], o["stat"], o["flags"], inf)
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(steps):
-        for plan, d, st, fl, inf in zip(plans, datas, o2, f2, infos):
-            m.mraid_run(plan.handle, d, None, None, st, fl, inf)
+        for plan, d, o, inf in zip(plans, datas, po, infos):
+            m.mraid_run(plan.handle, d, o["evals"], o["q1"], o["stat"], o["flags"], inf)
     e1.record(stream)
     torch.cuda.synchronize()
     ms_p = e0.elapsed_time(e1) / steps
@@ -619,7 +619,7 @@ def bench_batched(m, torch, stream, steps, peaks=None):
     for plan in plans:
         plan.close()
     batch.close()
-    del datas, outs
+    del datas, outs, po
     torch.cuda.empty_cache()
     return {"workload": "13b/1024ch/512, 19b/4096ch/1024, 36b/2048ch/2048, 72b/1024ch/4096; "
                         "5 s each, uint8", "cells": cells, "bytes": nbytes,
@@ -629,8 +629,9 @@ def bench_batched(m, torch, stream, steps, peaks=None):
             "fractions": batched_fractions(shapes, ms_b, peaks) if peaks else None,
             "packing": {"chosen": "chained" if packing == 1 else "concurrent",
                         "ms_concurrent": ms_conc, "ms_chained": ms_chain},
-            "note": "plain = one mraid_run per block, sequential on one stream; default variants "
-                    "in both; the batch's first run timed both packings"}
+            "note": "plain = one mraid_run per block, sequential on one stream, writing the same "
+                    "outputs (evals, q1, stat, flags); default variants in both; the batch's "
+                    "first run timed both packings"}
 
 
 def bench_served(m, torch, seconds, rates=(1.0, 2.0, 4.0)):
