@@ -7,10 +7,10 @@ of at most 1024 samples, so the saturated patterns (constant 0 or 255,
 every piece. The int64 sums must equal the oracle's bit for bit, the
 correlation must match the oracle's to CORR_TOL, and the CUDA-core Gram
 (variant -1) must give the same sums. The shapes cover one, two and four
-passes over a 16-channel box (24, 36 and 72 beams), M = 64 MMAs (up to 63
-beams) and M = 128 (64 and more), 127 beams (the largest that fits M = 128
-rows with the row of ones), pieces of 768 samples (1536-sample
-sub-integrations) and more work items than SMs."""
+passes over a 16-channel box (24, 36 and 72 beams), the three tile shapes
+(four channels per MMA up to 31 beams, two up to 63, one from 64), 127 beams
+(the largest that fits 128 rows with the row of ones), pieces of 768
+samples (1536-sample sub-integrations) and more work items than SMs."""
 import numpy as np
 import pytest
 
@@ -37,8 +37,9 @@ def oracle_sums(data, n_s, n_sub, n_chan):
     (72, 16, 4096, 2),     # 4 channels per pass, four pieces
     (127, 16, 512, 2),     # the largest beam count
     (40, 48, 1536, 2),     # pieces of 768 samples, three 16-channel boxes
-    (63, 16, 1024, 2),     # N + 1 = 64: the largest M = 64 MMA
-    (64, 16, 1024, 2),     # N + 1 = 65: M = 128
+    (63, 16, 1024, 2),     # N + 1 = 64: the largest two-channel tile
+    (64, 16, 1024, 2),     # N + 1 = 65: one channel per tile
+    (31, 16, 1024, 2),     # N + 1 = 32: the largest four-channel tile
 ])
 def test_tcl_gram_exact(n_beam, n_chan, n_s, n_sub):
     import torch
