@@ -167,7 +167,8 @@ def gpu_index(local_rank):
 
 EIG_NAMES = {0: "jacobi (looped rounds)", 1: "jacobi (unrolled sweep)",
              2: "householder + implicit QR", 3: "householder + implicit QR (compact)",
-             4: "householder + implicit QR, split (reduction and q1 / QR kernels)"}
+             4: "householder + implicit QR, split (reduction and q1 / QR kernels)",
+             5: "householder + root-free QR, split (reduction and q1 / QR kernels)"}
 SMS, FP32_LANES = 152, 128          # GB300: SMs, FP32 lanes per SM
 
 

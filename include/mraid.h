@@ -291,7 +291,7 @@ mraid_status mraid_run_bandpass(mraid_plan_t plan, const void* d_data,
  * eigensolvers (Jacobi rounds in a loop; the Jacobi sweep unrolled;
  * Householder tridiagonalisation + implicit QR in two code layouts), and
  * keeps the fastest of each for this plan. *gram_choice: -1 = CUDA-core,
- * 0..9 tensor-core variants; *eig_choice: 0..4. report (may be NULL) receives "g<id>:ms;e<id>:ms;...".
+ * 0..9 tensor-core variants; *eig_choice: 0..5. report (may be NULL) receives "g<id>:ms;e<id>:ms;...".
  * Synchronous. */
 mraid_status mraid_autotune(mraid_plan_t plan, const void* d_data, int32_t reps,
                             int32_t* gram_choice, int32_t* eig_choice, char* report,
@@ -309,8 +309,10 @@ mraid_status mraid_autotune(mraid_plan_t plan, const void* d_data, int32_t reps,
  * 3 = the same with one masked QR step for all levels (smaller code);
  * 4 = the same arithmetic split over two kernels: the reduction, lambda_1
  * (Newton's method on det(T - x I)) and q1 in one, QR on T for all
- * eigenvalues in a second with few registers (the default). All give the
- * same outputs to the stated tolerances. */
+ * eigenvalues in a second with few registers (the default); 5 = variant 4
+ * with the root-free (Pal-Walker-Kahan) QR step on the squared
+ * off-diagonals in the second kernel. All give the same outputs to the
+ * stated tolerances. */
 mraid_status mraid_set_variant(mraid_plan_t plan, int32_t variant);
 mraid_status mraid_set_eig_variant(mraid_plan_t plan, int32_t variant);
 

@@ -19,6 +19,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
 #include <utility>
 
 #include "internal.h"
@@ -534,6 +535,48 @@ __device__ __forceinline__ void qr_step(float (&d)[N], float (&e)[N], int l, int
   });
 }
 
+// The same implicit QR step in root-free form for eigenvalues only (the
+// Pal-Walker-Kahan variant, Parlett, The Symmetric Eigenvalue Problem,
+// section 8-15): it carries the squared off-diagonals e2 = e^2 and the
+// quantities gamma = c (d - mu) - s gamma' and p = gamma^2 / c of the
+// rotation chase, so a rotation costs one division and no square root. The
+// chase runs from the top of the unreduced block [l, m] down, deflating at
+// its bottom, with the Wilkinson shift of the trailing 2x2 block.
+template <int N, int K = N - 1>
+__device__ __forceinline__ void qr_step_pwk(float (&d)[N], float (&e2)[N], int l, int m, float dm1,
+                                            float dm, float e2m) {
+  static_assert(K >= 1 && K <= N - 1, "rotation positions");
+  const float dl = 0.5f * (dm1 - dm);
+  const float r2s = fmaf(dl, dl, e2m);
+  const float rr = r2s * rsqrtf(r2s);  // e2m > 0 here, so r2s > 0
+  const float mu = dm - __fdividef(e2m, dl + (dl >= 0.f ? rr : -rr));
+  float c = 1.f, s = 0.f, gamma = 0.f, p = 0.f;
+  static_for<K>([&](auto kk) {
+    constexpr int k = decltype(kk)::value;
+    if (k >= l && k < m) {
+      if (k == l) {
+        gamma = d[k] - mu;
+        p = gamma * gamma;
+      }
+      const float bb = e2[k];
+      const float r = p + bb;
+      if (k > l) e2[k - 1] = s * r;
+      const float oldc = c;
+      const float ri = r > 1e-37f ? __frcp_rn(r) : 0.f;
+      c = r > 1e-37f ? p * ri : 1.f;
+      s = bb * ri;
+      const float oldgam = gamma, alpha = d[k + 1];
+      gamma = fmaf(c, alpha - mu, -s * oldgam);
+      d[k] = oldgam + (alpha - gamma);
+      p = c != 0.f ? __fdividef(gamma * gamma, c) : oldc * bb;
+      if (k == m - 1) {
+        e2[k] = s * p;
+        d[k + 1] = mu + gamma;
+      }
+    }
+  });
+}
+
 template <int N, bool kCompact>
 __global__ void __launch_bounds__(kEigThreads)
 eig_tri_kernel(const float* __restrict__ corr, int64_t n_cells, float* __restrict__ evals,
@@ -999,7 +1042,8 @@ eig_tri_a_kernel(const float* __restrict__ corr, int64_t n_cells, float* __restr
 }
 
 
-template <int N, bool kCompact>
+// kRootFree: the root-free step on the squared off-diagonals (e holds e^2)
+template <int N, bool kCompact, bool kRootFree = false>
 __global__ void __launch_bounds__(kEigQrThreads)
 eig_qr_kernel(const float* __restrict__ de, int64_t n_cells, float* __restrict__ evals,
               float* __restrict__ stat, unsigned long long* __restrict__ step_count) {
@@ -1010,14 +1054,17 @@ eig_qr_kernel(const float* __restrict__ de, int64_t n_cells, float* __restrict__
     constexpr int i = decltype(ii)::value;
     d[i] = active ? de[(int64_t)i * n_cells + cell] : 1.f;
     e[i] = active ? de[(int64_t)(N + i) * n_cells + cell] : 0.f;
+    if constexpr (kRootFree) e[i] *= e[i];
   });
+  // |e| as compared below: e itself, or its square already
+  auto esq = [&](float x) { return kRootFree ? x : x * x; };
   // Implicit QR on T. |e| <= 1e-6 ||T||_F counts as zero: by Weyl's
   // inequality this moves no eigenvalue by more than 1e-6 sqrt(N) lambda_max.
   float an2 = 0.f;
   static_for<N>([&](auto ii) {
     constexpr int i = decltype(ii)::value;
     an2 = fmaf(d[i], d[i], an2);
-    if constexpr (i < N - 1) an2 = fmaf(2.f * e[i], e[i], an2);
+    if constexpr (i < N - 1) an2 = fmaf(2.f, esq(e[i]), an2);
   });
   const float thr2 = 1e-12f * an2;
   int steps = 0;
@@ -1027,15 +1074,18 @@ eig_qr_kernel(const float* __restrict__ de, int64_t n_cells, float* __restrict__
     static_for<N - 1>([&](auto mm) {
       constexpr int m = N - 1 - decltype(mm)::value;
       for (int it = 0; it < kMaxQrIter; ++it) {
-        const bool need = active && e[m - 1] * e[m - 1] > thr2;
+        const bool need = active && esq(e[m - 1]) > thr2;
         if (!__any_sync(0xffffffffu, need)) break;
         if (need) {
           int l = 0;  // top of the unreduced block that ends at m
           static_for<m - 1>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
-            if (e[i] * e[i] <= thr2) l = i + 1;
+            if (esq(e[i]) <= thr2) l = i + 1;
           });
-          qr_step<N>(d, e, l, m, d[m - 1], d[m], e[m - 1]);
+          if constexpr (kRootFree)
+            qr_step_pwk<N>(d, e, l, m, d[m - 1], d[m], e[m - 1]);
+          else
+            qr_step<N>(d, e, l, m, d[m - 1], d[m], e[m - 1]);
           ++steps;
         }
       }
@@ -1051,7 +1101,7 @@ eig_qr_kernel(const float* __restrict__ de, int64_t n_cells, float* __restrict__
       float dm1 = 0.f, dm = 0.f, em = 0.f;
       static_for<N - 1>([&](auto ii) {
         constexpr int i = decltype(ii)::value;
-        if (e[i] * e[i] > thr2) {
+        if (esq(e[i]) > thr2) {
           m = i + 1;
           l = last_small;
           dm1 = d[i];
@@ -1070,16 +1120,23 @@ eig_qr_kernel(const float* __restrict__ de, int64_t n_cells, float* __restrict__
       // positions issued).
       const int mw = __reduce_max_sync(0xffffffffu, need ? m : 0);
       if (need) {
+        auto step = [&](auto kc) {
+          constexpr int KK = decltype(kc)::value;
+          if constexpr (kRootFree)
+            qr_step_pwk<N, KK>(d, e, l, m, dm1, dm, em);
+          else
+            qr_step<N, KK>(d, e, l, m, dm1, dm, em);
+        };
         if constexpr (N - 1 >= 6) {
           constexpr int K1 = (N - 1) / 3, K2 = 2 * (N - 1) / 3;
           if (mw <= K1)
-            qr_step<N, K1>(d, e, l, m, dm1, dm, em);
+            step(std::integral_constant<int, K1>{});
           else if (mw <= K2)
-            qr_step<N, K2>(d, e, l, m, dm1, dm, em);
+            step(std::integral_constant<int, K2>{});
           else
-            qr_step<N>(d, e, l, m, dm1, dm, em);
+            step(std::integral_constant<int, N - 1>{});
         } else {
-          qr_step<N>(d, e, l, m, dm1, dm, em);
+          step(std::integral_constant<int, N - 1>{});
         }
         ++steps;
       }
@@ -1379,8 +1436,8 @@ cudaError_t launch_reg(const float* d_corr, int64_t n_cells, float* d_evals, flo
   const size_t smem = (size_t)kEigThreads * STR * sizeof(float);
   const int64_t blocks = (n_cells + kEigThreads - 1) / kEigThreads;
   cudaError_t e;
-  if (variant == 4 && !d_de) variant = 3;  // no T buffer: the one-kernel route
-  if (variant == 4) {
+  if (variant >= 4 && !d_de) variant = 3;  // no T buffer: the one-kernel route
+  if (variant >= 4) {
     e = cudaFuncSetAttribute(eig_tri_a_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
@@ -1388,9 +1445,14 @@ cudaError_t launch_reg(const float* d_corr, int64_t n_cells, float* d_evals, flo
       eig_tri_a_kernel<N><<<(unsigned)blocks, kEigThreads, smem, stream>>>(d_corr, n_cells, d_de,
                                                                              d_q1);
     const int64_t qb = (n_cells + kEigQrThreads - 1) / kEigQrThreads;
-    if (qb > 0)
-      eig_qr_kernel<N, true><<<(unsigned)qb, kEigQrThreads, 0, stream>>>(d_de, n_cells, d_evals,
-                                                                           d_stat, sweep_count);
+    if (qb > 0) {
+      if (variant == 5)
+        eig_qr_kernel<N, true, true><<<(unsigned)qb, kEigQrThreads, 0, stream>>>(
+            d_de, n_cells, d_evals, d_stat, sweep_count);
+      else
+        eig_qr_kernel<N, true><<<(unsigned)qb, kEigQrThreads, 0, stream>>>(d_de, n_cells, d_evals,
+                                                                             d_stat, sweep_count);
+    }
     return cudaGetLastError();
   }
   if (variant == 2 || variant == 3) {

@@ -188,7 +188,7 @@ constexpr int kTcVariants = 10;
 // the tensor-core variant a plan's launch runs (variants 8 and 9 fall back
 // to the default where their A-in-TMEM kernel does not fit the shape)
 int tc_variant_effective(const mraid_plan_s* pl);
-constexpr int kEigVariants = 5;  // register eigensolvers (see eig_variant)
+constexpr int kEigVariants = 6;  // register eigensolvers (see eig_variant)
 // d_sums8 (instead of d_sums): the sums in the interleaved layout
 // [cell / 8][P][cell % 8], which the kernel writes in 64-byte runs
 cudaError_t launch_gram_tc(const mraid_plan_s* pl, const uint8_t* d_data, int sub0, int n_sub,

@@ -39,7 +39,7 @@ def structured_corrs(N, n_cells, seed):
 
 
 @pytest.mark.parametrize("N", [2, 3, 4, 13, 19])
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_eig_variant_matches_oracle(N, variant):
     import torch
     m = lib()

@@ -112,5 +112,5 @@ def test_f32_autotune_times_both_gram_kernels():
     d = torch.from_numpy(x).cuda()
     with m.Plan(19, 64, 256, 4, bit_depth=32) as plan:
         (g, e), times = m.mraid_autotune(plan.handle, d, reps=2)
-    assert g in (-1, 0) and e in (0, 1, 2, 3, 4)
+    assert g in (-1, 0) and e in (0, 1, 2, 3, 4, 5)
     assert sorted(k for k in times if k.startswith("g")) == ["g-1", "g0"], times

@@ -51,7 +51,7 @@ def two_signal_block(n_beam, n_chan, n_sub, n_samp, seed):
     return np.clip(np.rint(x), 0, 255).astype(np.uint8)
 
 
-@pytest.mark.parametrize("n_beam,n_chan,variants", [(19, 64, (0, 1, 2, 3, 4)), (36, 32, (0, 3))])
+@pytest.mark.parametrize("n_beam,n_chan,variants", [(19, 64, (0, 1, 2, 3, 4, 5)), (36, 32, (0, 3))])
 def test_q1_near_degenerate_matches_oracle(n_beam, n_chan, variants):
     import torch
     m = lib()

@@ -27,16 +27,16 @@ def test_variants_agree_and_cache(tmp_path):
             assert np.abs(outs[v][1] - outs[-1][1]).max() <= 2e-6
         # every eigensolver variant gives the same eigenvalues to rounding
         evs = {}
-        for v in (0, 1, 2, 3, 4):
+        for v in (0, 1, 2, 3, 4, 5):
             m.mraid_set_eig_variant(plan.handle, v)
             evs[v] = plan.eig(c)[0].cpu().numpy()
-        for v in (1, 2, 3, 4):
+        for v in (1, 2, 3, 4, 5):
             assert np.abs(evs[0] - evs[v]).max() <= 1e-5 * np.abs(evs[0]).max()
         cache = tmp_path / "tune.json"
         choice = m.tune(plan.handle, d, cfg.n_beam, cfg.n_chan, cfg.n_samp_sub, str(cache), reps=2)
-        assert -1 <= choice[0] < 10 and choice[1] in (0, 1, 2, 3, 4)
+        assert -1 <= choice[0] < 10 and choice[1] in (0, 1, 2, 3, 4, 5)
         rec = json.loads(cache.read_text())
         key = f"{cfg.n_beam},{cfg.n_chan},{cfg.n_samp_sub},u8"
-        assert (rec[key]["gram"], rec[key]["jacobi"]) == choice and len(rec[key]["ms"]) == 16
+        assert (rec[key]["gram"], rec[key]["jacobi"]) == choice and len(rec[key]["ms"]) == 17
         # a second call reads the cache
         assert m.tune(plan.handle, d, cfg.n_beam, cfg.n_chan, cfg.n_samp_sub, str(cache)) == choice
