@@ -111,21 +111,27 @@ def test_multires_rejects_bad_arguments(block):
 
 
 def test_levels_on_the_cuda_core_gram():
-    """40 channels (not a multiple of 16) and 36 beams: the CUDA-core Gram
-    writes the sums cell by cell; every level still equals mraid_run at
-    its longer sub-integration, bit for bit."""
+    """40 channels (not a multiple of 16), and 36 beams with the CUDA-core
+    Gram selected: it writes the sums cell by cell; 36 beams by default:
+    the tensor-core Gram for more than 23 beams writes them too. Every
+    level still equals mraid_run at its longer sub-integration, bit for
+    bit."""
     import torch
     m = lib()
-    for (nb, nc, ns, nk) in ((13, 40, 64, 12), (36, 16, 64, 8)):
+    for (nb, nc, ns, nk, variant, gram) in ((13, 40, 64, 12, None, "gram_u8"),
+                                            (36, 16, 64, 8, -1, "gram_u8"),
+                                            (36, 16, 64, 8, None, "gram_tcl")):
         cfg = synth.SMALL.replace(n_beam=nb, n_chan=nc, n_samp_sub=ns, n_sub=nk, n_burst=1)
         data = synth.generate(cfg)
         d = torch.from_numpy(data).cuda()
         factors = [1, 2, 3, nk] if nk % 3 == 0 else [1, 2, 4, nk]
         with m.Plan(nb, nc, ns, nk) as plan:
+            if variant is not None:
+                m.mraid_set_variant(plan.handle, variant)
             m.mraid_profile_enable(plan.handle)
             levels = plan.multires(d, factors)
             ran = m.mraid_profile_read(plan.handle)
-        assert "gram_tc" not in ran and "gram_u8" in ran, ran
+        assert "gram_tc" not in ran and gram in ran, ran
         for lv in levels:
             f = lv["factor"]
             n_f = nk // f
