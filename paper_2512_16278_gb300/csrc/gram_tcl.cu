@@ -70,7 +70,7 @@ struct LArgs {
   int R;             // tile rows per channel (128 / G; np for G = 1)
   int gcols;         // D columns per MMA (128; np for G = 1)
   int nc;            // channels per CTA pass (a multiple of G)
-  int passes;        // 16 / nc
+  int passes;        // ceil(16 / nc); the last pass takes the remaining channels
   int piece_stages;  // stages per TMEM accumulation piece
   int n_u8;          // u8 ring depth
   int psum;          // (N + 1)(N + 2) / 2
@@ -115,6 +115,10 @@ __host__ __device__ constexpr uint32_t l_acc_bytes(int n_beam, int nc) {
 // the f16 stages, rounded up so that the u8 ring starts 1024-byte aligned
 __host__ __device__ constexpr size_t l_f16_region(uint32_t f16_stage) {
   return ((size_t)kLNF * f16_stage + 1023) & ~(size_t)1023;
+}
+// channels in pass `pass` of a 16-channel box (the last pass may hold fewer)
+__host__ __device__ __forceinline__ int l_pass_channels(int pass, int nc) {
+  return 16 - pass * nc < nc ? 16 - pass * nc : nc;
 }
 // start of row a in the packed upper triangle of an (N+1)^2 matrix
 __host__ __device__ __forceinline__ int l_row_off(int a, int n1) { return a * n1 - a * (a - 1) / 2; }
@@ -169,7 +173,6 @@ gram_tcl_kernel(const __grid_constant__ CUtensorMap tmap, LArgs g) {
   const int64_t items = (int64_t)g.n_sub * chunks * g.passes;
   const int stages = g.n_samp_sub / kLT;
   const int nc = g.nc, G = g.G, R = g.R;
-  const int n_groups = nc / G;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < kNU; ++i) {
@@ -243,6 +246,7 @@ gram_tcl_kernel(const __grid_constant__ CUtensorMap tmap, LArgs g) {
       uint32_t fcnt = 0, pcnt = 0;
       bool ok = true;
       for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        const int ng = l_pass_channels((int)(it % g.passes), nc) / G;  // this pass's MMAs per K step
         for (int st = 0; st < stages && ok; ++st, ++fcnt) {
           const int fs = fcnt % kLNF;
           const int ps = st % g.piece_stages;
@@ -255,7 +259,7 @@ gram_tcl_kernel(const __grid_constant__ CUtensorMap tmap, LArgs g) {
           fence_after();
           const uint32_t stage = f16_base + (uint32_t)fs * g.f16_stage;
           for (int ks = 0; ks < kLKs; ++ks)
-            for (int gi = 0; gi < n_groups; ++gi) {
+            for (int gi = 0; gi < ng; ++gi) {
               const uint32_t t = stage + (uint32_t)ks * g.ks_stride + (uint32_t)gi * g.gstride;
               const uint64_t d = smem_desc(t, lbo, sbo);
               mma_f16(tmem + (uint32_t)(gi * g.gcols), d, d, idesc, (ps > 0 || ks > 0) ? 1u : 0u);
@@ -303,8 +307,9 @@ gram_tcl_kernel(const __grid_constant__ CUtensorMap tmap, LArgs g) {
     bool ok = true;
     for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
       const int c0 = (int)(it % g.passes) * nc;
-      const int ci0 = p - c0, ci1 = p + 8 - c0;  // channel p / p + 8 in the pass (valid in [0, nc))
-      const bool use0 = ci0 >= 0 && ci0 < nc, use1 = ci1 >= 0 && ci1 < nc;
+      const int ncp = l_pass_channels((int)(it % g.passes), nc);
+      const int ci0 = p - c0, ci1 = p + 8 - c0;  // channel p / p + 8 in the pass (valid in [0, ncp))
+      const bool use0 = ci0 >= 0 && ci0 < ncp, use1 = ci1 >= 0 && ci1 < ncp;
       // first store: channel p if it is the pass's, else p + 8; second
       // (nc = 16 only): channel p + 8
       const uint32_t ta = chan_off(use0 ? ci0 : (use1 ? ci1 : 0)) + lane_off;
@@ -382,13 +387,14 @@ gram_tcl_kernel(const __grid_constant__ CUtensorMap tmap, LArgs g) {
       const int64_t rest = it / g.passes;
       const int k = (int)(rest / chunks), ch0 = (int)(rest % chunks) * 16;
       const int c0 = (int)(it % g.passes) * nc;
+      const int ncp = l_pass_channels((int)(it % g.passes), nc);
       for (int pc = 0; pc < n_pieces && ok; ++pc) {
         ok = epi_wait(&s->acc_full, pcnt & 1, g.error, g.wait_ns, &s->epi_go, et == 0, kLEpi);
         if (!ok) break;
         ++pcnt;
         fence_after();
         if (slot < G) {
-          for (int gi = h; gi < n_groups; gi += 2) {
+          for (int gi = h; gi < ncp / G; gi += 2) {
             const int ci = gi * G + slot;
             // this row's entries b >= a: tab[row_off(a) + b - a]
             int32_t* row = acc + ci * psum + (mine ? l_row_off(a, N1) : 0);
@@ -416,7 +422,7 @@ gram_tcl_kernel(const __grid_constant__ CUtensorMap tmap, LArgs g) {
       }
       if (!ok) break;
       named_sync(1, kLEpi);  // every table and row sum complete
-      for (int ci = 0; ci < nc; ++ci) {
+      for (int ci = 0; ci < ncp; ++ci) {
         const int32_t* tab = acc + ci * psum;
         const int32_t* gs = rowsum + ci * 128;
         const int64_t cell = (int64_t)k * g.n_chan + ch0 + c0 + ci;
@@ -456,13 +462,15 @@ gram_tcl_kernel(const __grid_constant__ CUtensorMap tmap, LArgs g) {
   }
 }
 
-// Channels per pass: the largest power of two that is a multiple of G,
-// whose accumulators fit TMEM ((nc / G) x gcols <= 512 columns) and whose
-// tables, two f16 stages and an u8 ring of two stages fit shared memory;
-// 0 if none does.
+// Channels per pass: the most whose accumulators fit TMEM ((nc / G) x gcols
+// <= 512 columns) and whose tables, two f16 stages and an u8 ring of two
+// stages fit shared memory: 16 or 8 for the four- and two-channel tiles
+// (a divisor of 16 that is a multiple of G), any count for one channel per
+// tile (the box's last pass then takes the remaining channels); 0 if none
+// fits.
 int l_channels(int n_beam, int* n_u8_out) {
   const LShape sh = l_shape(n_beam);
-  for (int nc = 16; nc >= sh.G; nc /= 2) {
+  for (int nc = 16; nc >= sh.G; nc = sh.G > 1 ? nc / 2 : nc - 1) {
     if ((nc / sh.G) * sh.gcols > (int)kLTmemCols) continue;
     const size_t fixed = 1024 + l_f16_region(l_f16_stage(sh, nc)) + l_acc_bytes(n_beam, nc) +
                          sizeof(SmemL);
@@ -513,7 +521,7 @@ cudaError_t launch_gram_tcl(const mraid_plan_s* pl, const uint8_t* d_data, int s
   a.R = sh.R;
   a.gcols = sh.gcols;
   a.nc = l_channels(p.n_beam, &a.n_u8);
-  a.passes = 16 / a.nc;
+  a.passes = (16 + a.nc - 1) / a.nc;
   {
     const int stages = p.n_samp_sub / kLT;
     int d = stages;
