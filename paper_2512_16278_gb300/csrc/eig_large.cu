@@ -361,7 +361,6 @@ cudaError_t launch_eig_large(const mraid_plan_s* pl, const float* d_corr, int64_
   float* de = d_work;
   float* refl = de + (size_t)n_cells * 2 * N;
   float* y = refl + (size_t)n_cells * refl_floats(N);
-  const int64_t cap = (int64_t)pl->sm_count * 16;
   // pass 1: as many warps per block (up to 4) as 200 KB of shared memory holds
   const size_t per_warp = sizeof(float) * ((size_t)N * row_stride(N) + 2 * row_stride(N));
   int nw = (int)((200u << 10) / per_warp);
@@ -370,8 +369,14 @@ cudaError_t launch_eig_large(const mraid_plan_s* pl, const float* d_corr, int64_
   cudaError_t e = cudaFuncSetAttribute(tri_reduce_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
   if (e != cudaSuccess) return e;
+  // one wave of resident blocks (they loop over the cells): a grid larger
+  // than the GPU holds leaves a partial second wave
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_reduce_kernel, 32 * nw, smem1);
+  if (e != cudaSuccess) return e;
+  const int64_t wave1 = (int64_t)(per_sm > 0 ? per_sm : 1) * pl->sm_count;
   int64_t blocks = (n_cells + nw - 1) / nw;
-  if (blocks > cap) blocks = cap;
+  if (blocks > wave1) blocks = wave1;
   tri_reduce_kernel<<<(unsigned)blocks, 32 * nw, smem1, stream>>>(d_corr, n_cells, N, de, refl);
   const size_t smem2 = sizeof(float) * (size_t)kQrThreads * (4 * N + 1);
   e = cudaFuncSetAttribute(tri_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
@@ -381,8 +386,13 @@ cudaError_t launch_eig_large(const mraid_plan_s* pl, const float* d_corr, int64_
       de, n_cells, N, d_evals, d_stat, d_q1 ? y : nullptr, pl->d_sweeps);
   if (d_q1) {
     const size_t smem3 = sizeof(float) * (size_t)kRedWarps * N;
+    int per_sm3 = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3, tri_back_kernel, 32 * kRedWarps,
+                                                      smem3);
+    if (e != cudaSuccess) return e;
+    const int64_t wave3 = (int64_t)(per_sm3 > 0 ? per_sm3 : 1) * pl->sm_count;
     int64_t blocks3 = (n_cells + kRedWarps - 1) / kRedWarps;
-    if (blocks3 > cap) blocks3 = cap;
+    if (blocks3 > wave3) blocks3 = wave3;
     tri_back_kernel<<<(unsigned)blocks3, 32 * kRedWarps, smem3, stream>>>(refl, y, n_cells, N,
                                                                           d_q1);
   }
