@@ -34,6 +34,13 @@ __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// sum over the LPM lanes of one matrix's group (LPM a power of two <= 32)
+template <int LPM>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = LPM / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 __device__ __forceinline__ void cp_async4(uint32_t dst, const float* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
 }
@@ -60,29 +67,38 @@ __host__ __device__ __forceinline__ int row_stride(int N) {
 }
 
 // ---------------------------------------------------------------- pass 1
+// LPM lanes per matrix: 32, or 16 (two matrices per warp) where the
+// trailing block has at most ~48 rows, so that fewer lanes sit idle in the
+// row loops as the block shrinks.
+template <int LPM>
 __global__ void tri_reduce_kernel(const float* __restrict__ corr, int64_t n_cells, int N,
                                   float* __restrict__ de, float* __restrict__ refl) {
   extern __shared__ __align__(16) float rsm[];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  constexpr int MPW = 32 / LPM;  // matrices per warp
+  const int lane32 = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int sub = lane32 / LPM, lane = lane32 % LPM;
   const int LD = row_stride(N);
   const int NP = N * (N + 1) / 2;
-  float* A = rsm + (size_t)w * ((size_t)N * LD + 2 * LD);
+  float* A = rsm + ((size_t)w * MPW + sub) * ((size_t)N * LD + 2 * LD);
   float* V = A + (size_t)N * LD;   // current reflector, by absolute column (0 outside it)
   float* W = V + LD;               // p, then w = p - K v, by absolute column
   const uint32_t abase = static_cast<uint32_t>(__cvta_generic_to_shared(A));
   const int64_t RF = refl_floats(N);
-  for (int64_t cell = (int64_t)blockIdx.x * nw + w; cell < n_cells;
-       cell += (int64_t)gridDim.x * nw) {
+  for (int64_t c0 = ((int64_t)blockIdx.x * nw + w) * MPW; c0 < n_cells;
+       c0 += (int64_t)gridDim.x * nw * MPW) {
+    // past the last cell a group repeats the warp's first matrix and writes nothing
+    const bool valid = c0 + sub < n_cells;
+    const int64_t cell = valid ? c0 + sub : c0;
     const float* src = corr + cell * NP;
     // packed upper triangle -> full symmetric matrix; padding columns zero
     for (int a = 0, off = 0; a < N; off += N - a, ++a)
-      for (int b = a + lane; b < N; b += 32) {
+      for (int b = a + lane; b < N; b += LPM) {
         cp_async4(abase + 4u * (uint32_t)(a * LD + b), src + off + (b - a));
         if (b != a) cp_async4(abase + 4u * (uint32_t)(b * LD + a), src + off + (b - a));
       }
     for (int a = 0; a < N; ++a)
-      for (int b = N + lane; b < LD; b += 32) A[a * LD + b] = 0.f;
-    for (int j = lane; j < LD; j += 32) V[j] = W[j] = 0.f;
+      for (int b = N + lane; b < LD; b += LPM) A[a * LD + b] = 0.f;
+    for (int j = lane; j < LD; j += LPM) V[j] = W[j] = 0.f;
     cp_async_wait_all();
     __syncwarp();
     float* dcell = de + cell * 2 * N;
@@ -91,11 +107,11 @@ __global__ void tri_reduce_kernel(const float* __restrict__ corr, int64_t n_cell
       const int m = N - 1 - k;
       const int j0 = (k + 1) & ~3;  // aligned start; V = W = 0 below column k + 1
       float s2 = 0.f;
-      for (int i = lane; i < m; i += 32) {
+      for (int i = lane; i < m; i += LPM) {
         const float x = A[(size_t)(k + 1 + i) * LD + k];
         s2 = fmaf(x, x, s2);
       }
-      s2 = warp_sum(s2);
+      s2 = group_sum<LPM>(s2);
       const float x0 = A[(size_t)(k + 1) * LD + k];
       const float nx = sqrtf(s2);
       const float alpha = x0 >= 0.f ? -nx : nx;
@@ -103,19 +119,19 @@ __global__ void tri_reduce_kernel(const float* __restrict__ corr, int64_t n_cell
       const bool reflect = vtv > 1e-30f;
       const float beta = reflect ? 2.f / vtv : 0.f;
       if (lane == 0) V[k] = 0.f;  // column k leaves the trailing block
-      for (int i = lane; i < m; i += 32) {
+      for (int i = lane; i < m; i += LPM) {
         const float v = i == 0 ? x0 - alpha : A[(size_t)(k + 1 + i) * LD + k];
         V[k + 1 + i] = v;
-        rcell[refl_off(k, N) + i] = v;
+        if (valid) rcell[refl_off(k, N) + i] = v;
       }
-      if (lane == 0) {
+      if (lane == 0 && valid) {
         rcell[refl_off(N - 2, N) + k] = beta;
         dcell[k] = A[(size_t)k * LD + k];
         dcell[N + k] = reflect ? alpha : x0;
       }
       __syncwarp();
       // p = beta A' v, one row per lane, 16-byte accesses
-      for (int i = lane; i < m; i += 32) {
+      for (int i = lane; i < m; i += LPM) {
         const float4* row = reinterpret_cast<const float4*>(A + (size_t)(k + 1 + i) * LD);
         const float4* v4 = reinterpret_cast<const float4*>(V);
         float a0 = 0.f, a1 = 0.f;
@@ -131,12 +147,12 @@ __global__ void tri_reduce_kernel(const float* __restrict__ corr, int64_t n_cell
       }
       __syncwarp();
       float vp = 0.f;
-      for (int i = lane; i < m; i += 32) vp = fmaf(V[k + 1 + i], W[k + 1 + i], vp);
-      const float kh = 0.5f * beta * warp_sum(vp);
-      for (int i = lane; i < m; i += 32) W[k + 1 + i] = fmaf(-kh, V[k + 1 + i], W[k + 1 + i]);
+      for (int i = lane; i < m; i += LPM) vp = fmaf(V[k + 1 + i], W[k + 1 + i], vp);
+      const float kh = 0.5f * beta * group_sum<LPM>(vp);
+      for (int i = lane; i < m; i += LPM) W[k + 1 + i] = fmaf(-kh, V[k + 1 + i], W[k + 1 + i]);
       __syncwarp();
       // A' -= v w^T + w v^T (columns below k + 1 see v = w = 0)
-      for (int i = lane; i < m; i += 32) {
+      for (int i = lane; i < m; i += LPM) {
         float4* row = reinterpret_cast<float4*>(A + (size_t)(k + 1 + i) * LD);
         const float4* v4 = reinterpret_cast<const float4*>(V);
         const float4* w4 = reinterpret_cast<const float4*>(W);
@@ -155,7 +171,7 @@ __global__ void tri_reduce_kernel(const float* __restrict__ corr, int64_t n_cell
       __syncwarp();
       if (lane == 0) W[k] = 0.f;
     }
-    if (lane == 0) {
+    if (lane == 0 && valid) {
       dcell[N - 2] = A[(size_t)(N - 2) * LD + (N - 2)];
       dcell[N - 1] = A[(size_t)(N - 1) * LD + (N - 1)];
       dcell[N + N - 2] = A[(size_t)(N - 2) * LD + (N - 1)];
@@ -361,23 +377,26 @@ cudaError_t launch_eig_large(const mraid_plan_s* pl, const float* d_corr, int64_
   float* de = d_work;
   float* refl = de + (size_t)n_cells * 2 * N;
   float* y = refl + (size_t)n_cells * refl_floats(N);
-  // pass 1: as many warps per block (up to 4) as 200 KB of shared memory holds
-  const size_t per_warp = sizeof(float) * ((size_t)N * row_stride(N) + 2 * row_stride(N));
+  // pass 1: two matrices per warp up to 48 beams, else one; as many warps
+  // per block (up to 4) as 200 KB of shared memory holds
+  const int mpw = N <= 48 ? 2 : 1;
+  const auto red = mpw == 2 ? tri_reduce_kernel<16> : tri_reduce_kernel<32>;
+  const size_t per_warp =
+      sizeof(float) * mpw * ((size_t)N * row_stride(N) + 2 * row_stride(N));
   int nw = (int)((200u << 10) / per_warp);
   nw = nw < 1 ? 1 : (nw > kRedWarps ? kRedWarps : nw);
   const size_t smem1 = per_warp * nw;
-  cudaError_t e = cudaFuncSetAttribute(tri_reduce_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+  cudaError_t e = cudaFuncSetAttribute(red, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
   if (e != cudaSuccess) return e;
   // one wave of resident blocks (they loop over the cells): a grid larger
   // than the GPU holds leaves a partial second wave
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_reduce_kernel, 32 * nw, smem1);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, red, 32 * nw, smem1);
   if (e != cudaSuccess) return e;
   const int64_t wave1 = (int64_t)(per_sm > 0 ? per_sm : 1) * pl->sm_count;
-  int64_t blocks = (n_cells + nw - 1) / nw;
+  int64_t blocks = (n_cells + (int64_t)nw * mpw - 1) / ((int64_t)nw * mpw);
   if (blocks > wave1) blocks = wave1;
-  tri_reduce_kernel<<<(unsigned)blocks, 32 * nw, smem1, stream>>>(d_corr, n_cells, N, de, refl);
+  red<<<(unsigned)blocks, 32 * nw, smem1, stream>>>(d_corr, n_cells, N, de, refl);
   const size_t smem2 = sizeof(float) * (size_t)kQrThreads * (4 * N + 1);
   e = cudaFuncSetAttribute(tri_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
   if (e != cudaSuccess) return e;
