@@ -329,7 +329,7 @@ mraid_status mraid_set_wait_limit(mraid_plan_t plan, int64_t ns);
  * the launch (no counterpart in the paper; nothing faults the device):
  *   MRAID_FAULT_NONE:           clear.
  *   MRAID_FAULT_WITHHOLD_STAGE: in the plan's next tensor-core Gram launch
- *     (8-bit samples), the first CTA's bulk-copy producer skips its stage
+ *     (8-bit samples, any beam count), the first CTA's bulk-copy producer skips its stage
  *     number arg (counted from 0 over that CTA's stages): the copy is never
  *     issued, so the consumer's bounded wait for it expires and mraid_sync
  *     returns MRAID_ERR_TIMEOUT.

@@ -81,6 +81,7 @@ struct LArgs {
   int64_t* sums;       // [cell][psum], cells relative to sub0
   unsigned* error;
   unsigned long long wait_ns;
+  long long withhold;  // fault injection: CTA 0's TMA producer never issues this stage (-1: none)
 };
 
 struct SmemL {
@@ -218,6 +219,7 @@ gram_tcl_kernel(const __grid_constant__ CUtensorMap tmap, LArgs g) {
     // ------------------------------------------------------------ TMA
     if (lane == 0) {
       uint32_t cnt = 0;
+      long long withheld = -1;
       bool ok = true;
       for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
         const int64_t rest = it / g.passes;
@@ -227,13 +229,21 @@ gram_tcl_kernel(const __grid_constant__ CUtensorMap tmap, LArgs g) {
           const int slot = cnt % kNU;
           ok = mbar_wait(&s->u8_empty[slot], ((cnt / kNU) & 1) ^ 1, g.error, g.wait_ns);
           if (!ok) break;
+          if (blockIdx.x == 0 && (long long)cnt == g.withhold) {
+            // injected fault: this stage is never issued, so the converters'
+            // bounded wait for it expires (nothing is in flight for it)
+            withheld = cnt;
+            continue;
+          }
           mbar_expect_tx(&s->u8_full[slot], u8_stage_bytes);
           tma_load_3d(u8 + (size_t)slot * u8_stage_bytes, &tmap, ch0, (int)(t_item + st * kLT), 0,
                       &s->u8_full[slot]);
         }
       }
+      // every issued copy has landed before the CTA may exit
       for (uint32_t d = cnt > (uint32_t)kNU ? cnt - kNU : 0; d < cnt; ++d)
-        mbar_drain(&s->u8_full[d % kNU], (d / kNU) & 1, g.error, g.wait_ns);
+        if ((long long)d != withheld)
+          mbar_drain(&s->u8_full[d % kNU], (d / kNU) & 1, g.error, g.wait_ns);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA
@@ -536,6 +546,7 @@ cudaError_t launch_gram_tcl(const mraid_plan_s* pl, const uint8_t* d_data, int s
   a.sums = d_sums;
   a.error = pl->d_error;
   a.wait_ns = pl->wait_ns;
+  a.withhold = pl->inject_withhold;
   const size_t smem = 1024 + l_f16_region(a.f16_stage) + (size_t)a.n_u8 * p.n_beam * kLT * 16 +
                       a.acc_bytes + sizeof(SmemL);
   const int64_t items = (int64_t)n_sub * (p.n_chan / 16) * a.passes;

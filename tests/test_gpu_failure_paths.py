@@ -2,8 +2,9 @@
 the device).
 
 A bounded wait that runs out: the host arms MRAID_FAULT_WITHHOLD_STAGE, so
-the first CTA of the next tensor-core Gram launch never issues one of its
-bulk copies. Nothing is then in flight for that stage; the converter's wait
+the first CTA of the next tensor-core Gram launch (the block-diagonal kernel
+at 19 beams, the large-beam kernel at 36) never issues one of its bulk
+copies. Nothing is then in flight for that stage; the converter's wait
 for it expires after the plan's wait limit (50 ms here), the kernel records
 the error, every role returns, its own copies and MMAs are drained and its
 tensor memory freed. mraid_sync must report MRAID_ERR_TIMEOUT with the
@@ -21,26 +22,28 @@ from gpu_util import lib
 pytestmark = pytest.mark.gpu
 
 N_BEAM, N_CHAN, N_S, N_SUB = 19, 32, 1024, 4     # tensor-core Gram shape
+SHAPES = [(19, 32, 1024, 4, "gram_tc"), (36, 32, 2048, 2, "gram_tcl")]
 TIMEOUT, OOM = 5, 3
 
 
-def block(seed):
+def block(seed, n_beam=N_BEAM, n_chan=N_CHAN, n_s=N_S, n_sub=N_SUB):
     rng = np.random.default_rng(seed)
-    return rng.integers(0, 256, size=(N_BEAM, N_SUB * N_S, N_CHAN), dtype=np.uint8)
+    return rng.integers(0, 256, size=(n_beam, n_sub * n_s, n_chan), dtype=np.uint8)
 
 
 def outputs(out):
     return {k: out[k].cpu().numpy() for k in ("evals", "q1", "stat", "flags")}
 
 
-def test_expired_wait_is_reported_and_the_plan_recovers():
+@pytest.mark.parametrize("n_beam,n_chan,n_s,n_sub,gram", SHAPES)
+def test_expired_wait_is_reported_and_the_plan_recovers(n_beam, n_chan, n_s, n_sub, gram):
     import torch
     m = lib()
-    d = torch.from_numpy(block(11)).cuda()
-    with m.Plan(N_BEAM, N_CHAN, N_S, N_SUB) as plan:
+    d = torch.from_numpy(block(11, n_beam, n_chan, n_s, n_sub)).cuda()
+    with m.Plan(n_beam, n_chan, n_s, n_sub) as plan:
         m.mraid_profile_enable(plan.handle)
         ref = outputs(plan.run(d))
-        assert "gram_tc" in m.mraid_profile_read(plan.handle)
+        assert gram in m.mraid_profile_read(plan.handle)
         m.mraid_set_wait_limit(plan.handle, 50_000_000)
         for stage in (0, 5):
             m.mraid_inject_fault(plan.handle, m.FAULT_WITHHOLD_STAGE, stage)
