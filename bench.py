@@ -944,7 +944,7 @@ def run_mraid(args):
                "h2d_gbs_achieved": cfg.nbytes / te / 1e9,
                "copy_only_ms": tcopy * 1000.0, "copy_only_gbs": cfg.nbytes / tcopy / 1e9,
                "compute_hidden_frac": max(0.0, min(1.0, (tcopy * 1000.0 + ms - te * 1000.0) / ms)),
-               "steps_ms": steps_ms,
+               "steps_ms": steps_ms, "steps_median_ms": statistics.median(steps_ms),
                "api": "mraid_run_host (pinned host input, stat + flags copied back)",
                "note": "bound by the host-to-device copy; its rate differs between boxes"}
 
